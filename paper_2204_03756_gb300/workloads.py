@@ -1,0 +1,108 @@
+"""Seeded synthetic inputs (initial particle states) for the MTPT step.
+
+This module holds no part of the method's arithmetic: it only draws initial
+positions and assigns initial masses, the inputs that the CUDA path and the
+CPU oracle both consume.  Positions are uniform in the box (Sec. 2.1: "randomly
+scattered"), drawn with numpy's Philox bit generator under the workload seed;
+masses follow the initial conditions of each workload.
+
+Workloads (sizes and parameters of the paper's test problem family, Sec. 2):
+
+* ``heaviside_2d``   N = 10,000 in [0,100]^2, mass 1 where x < 50 else 0,
+  D = 1, kappa = 0.5, dt = 0.1, 100 steps.
+* ``gaussian_2d``    N = 4,000,000 in [0,2000]^2 (density 1), mass
+  exp(-|x - c|^2 / (2 * 5^2)) with c the box centre, D = 1, dt = 0.1,
+  1,000 steps.
+* ``heaviside_3d``   N = 2,000,000 in [0,126]^3 (density ~1), mass 1 where
+  x < 63 else 0, D = 1, dt = 0.05, 500 steps.
+* ``uniform_mass_2d`` N = 250,000 in [0,500]^2, mass U(0,1), D = 0.5,
+  dt = 0.1, 200 steps.
+
+Every workload takes kappa = 0.5, beta = 1 and lambda = 3 (cutoff
+psi = 3 sqrt(4 D_MT dt)), and may be scaled down (``n`` with the box scaled
+to keep the density) for tests.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+SEED_BASE = 2204037560
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n: int
+    lo: tuple
+    hi: tuple
+    D: float
+    kappa: float
+    dt: float
+    steps: int
+    mass_kind: str           # "heaviside_left", "gaussian_centre", "uniform01", "ones"
+    beta: float = 1.0
+    lam: float = 3.0
+    seed: int = SEED_BASE
+    mass_param: float = 0.0  # Heaviside split x, or Gaussian sigma
+
+    def scaled(self, n: int) -> "Workload":
+        """Same density and parameters with ``n`` particles: every box edge
+        is scaled by (n / N)^(1/d) about the lower corner."""
+        f = (n / self.n) ** (1.0 / self.dim)
+        lo = tuple(self.lo[a] for a in range(self.dim))
+        hi = tuple(self.lo[a] + (self.hi[a] - self.lo[a]) * f for a in range(self.dim))
+        mp = self.mass_param * f if self.mass_kind == "heaviside_left" else self.mass_param
+        return replace(self, n=n, lo=lo, hi=hi, mass_param=mp)
+
+
+WORKLOADS = {
+    "heaviside_2d": Workload("heaviside_2d", 2, 10_000, (0.0, 0.0), (100.0, 100.0),
+                             1.0, 0.5, 0.1, 100, "heaviside_left", seed=SEED_BASE + 1,
+                             mass_param=50.0),
+    "gaussian_2d": Workload("gaussian_2d", 2, 4_000_000, (0.0, 0.0), (2000.0, 2000.0),
+                            1.0, 0.5, 0.1, 1000, "gaussian_centre", seed=SEED_BASE + 2,
+                            mass_param=5.0),
+    "heaviside_3d": Workload("heaviside_3d", 3, 2_000_000, (0.0, 0.0, 0.0),
+                             (126.0, 126.0, 126.0), 1.0, 0.5, 0.05, 500, "heaviside_left",
+                             seed=SEED_BASE + 3, mass_param=63.0),
+    "uniform_mass_2d": Workload("uniform_mass_2d", 2, 250_000, (0.0, 0.0), (500.0, 500.0),
+                                0.5, 0.5, 0.1, 200, "uniform01", seed=SEED_BASE + 5),
+}
+
+
+def positions(w: Workload) -> np.ndarray:
+    """Uniform positions in the box, shape (dim, n), float64."""
+    rng = np.random.Generator(np.random.Philox(w.seed))
+    pos = np.empty((w.dim, w.n), dtype=np.float64)
+    for a in range(w.dim):
+        pos[a] = rng.uniform(w.lo[a], w.hi[a], size=w.n)
+    return pos
+
+
+def masses(w: Workload, pos: np.ndarray) -> np.ndarray:
+    """Initial masses of the workload's initial condition, float64."""
+    if w.mass_kind == "heaviside_left":
+        return (pos[0] < w.mass_param).astype(np.float64)
+    if w.mass_kind == "gaussian_centre":
+        c = [0.5 * (w.lo[a] + w.hi[a]) for a in range(w.dim)]
+        r2 = sum((pos[a] - c[a]) ** 2 for a in range(w.dim))
+        return np.exp(-r2 / (2.0 * w.mass_param ** 2))
+    if w.mass_kind == "uniform01":
+        rng = np.random.Generator(np.random.Philox(w.seed + 1_000_003))
+        return rng.uniform(0.0, 1.0, size=pos.shape[1])
+    if w.mass_kind == "ones":
+        return np.ones(pos.shape[1], dtype=np.float64)
+    raise ValueError(f"unknown mass kind {w.mass_kind!r}")
+
+
+def initial_state(w: Workload):
+    pos = positions(w)
+    return pos, masses(w, pos)
+
+
+def get(name: str, n: int | None = None) -> Workload:
+    w = WORKLOADS[name]
+    return w if n is None or n == w.n else w.scaled(n)
