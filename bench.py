@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Throughput of the MTPT time step on GB300: particle-steps/s and
+pair-interactions/s, binary64 form and precision form.
+
+Workload (default): the 2-d diffusion at scale -- N = 4,000,000 particles
+uniform in [0,2000]^2 (density 1), Gaussian point-source mass (sigma 5 at the
+centre), D = 1, kappa = 0.5, dt = 0.1, lambda = 3.  A "step" is one full time
+step of the hot path (walk, cell-list build, row sums, exchange) over every
+particle.  Inputs are resident in HBM when the timed region starts; the
+per-step working set (state double buffer, cell list, row sums) is several
+times the 129 MB L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent realisation (seed + rank) on its
+own GPU: no data-path collective ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2204_03756_gb300 import mtpt, workloads  # noqa: E402
+
+FORMS = {"fp64": mtpt.MTPT_FP64, "fp32w": mtpt.MTPT_FP32W}
+DTYPE = {"fp64": "f64", "fp32w": "f32+f64acc"}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
+    """Bytes the kernel's own arithmetic must read and write once per particle
+    (its inputs and outputs; cell-list traffic excluded)."""
+    x = 8 * dim
+    r = 8 if form == "fp64" else 4
+    table = {
+        "walk_key": 2 * x,                 # positions read + written
+        "rowsum_f64": x + r, "rowsum_f32": x + r,          # positions in, r out
+        "exchange_f64": x + 8 + r + 8, "exchange_f32": x + 8 + r + 8,  # X, M, r in; M out
+        "gather": 2 * (x + 8 + 4),         # state copied into cell order
+        "scatter": 8, "scan_tile_sums": 0, "scan_tile_offsets": 0, "scan_apply": 0,
+    }
+    return float(table.get(kernel, 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _params(w, form: str, rank: int) -> mtpt.Params:
+    return mtpt.Params(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
+                       lo=w.lo, hi=w.hi, seed=w.seed + rank, precision=FORMS[form])
+
+
+def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
+    import torch
+    p = _params(w, form, rank)
+    stream = torch.cuda.Stream()
+    h = mtpt.mtpt_create(p)
+    try:
+        mtpt.mtpt_set_stream(h, stream.cuda_stream)
+        mtpt.mtpt_set_particles(h, w.dim, pos, mass)
+        mtpt.mtpt_step(h, warmup)
+        mtpt.mtpt_sync(h)
+        m_before = float(mtpt.mtpt_get_masses(h, w.n).sum())
+        pairs0 = mtpt.mtpt_get_info(h)["pair_count"]
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.3)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mtpt.mtpt_step(h, steps)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        info = mtpt.mtpt_get_info(h)
+        pairs = info["pair_count"] - pairs0
+        m_after = float(mtpt.mtpt_get_masses(h, w.n).sum())
+        # second pass with per-kernel events (same stream, same workload)
+        mtpt.mtpt_timing_reset(h)
+        mtpt.mtpt_timing_enable(h, True)
+        mtpt.mtpt_step(h, steps)
+        kstats = mtpt.mtpt_timing_read(h)
+        mtpt.mtpt_timing_enable(h, False)
+    finally:
+        mtpt.mtpt_destroy(h)
+    max_ms = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+        pt = torch.tensor([float(pairs)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
+        pairs = pt.item()
+    sec = max_ms / 1e3
+    return {
+        "form": form, "ms": max_ms, "ms_per_step": max_ms / steps,
+        "particle_steps_per_s": w.n * steps * world / sec,
+        "pair_interactions_per_s": pairs / sec,
+        "pairs_per_particle_step": pairs / (w.n * steps * world),
+        "mass_drift_rel": abs(m_after - m_before) / abs(m_before),
+        "clocks": clocks, "kernels": kstats, "launches_per_step":
+            sum(v[0] for v in kstats.values()) / steps,
+    }
+
+
+def roofline(w, res, peaks):
+    kst = res["kernels"]
+    name, (launches, total_ms) = max(kst.items(), key=lambda kv: kv[1][1])
+    per_launch_s = total_ms / launches / 1e3
+    algo = _algo_bytes_per_particle(name, w.dim, res["form"]) * w.n
+    achieved = algo / per_launch_s / 1e9
+    share = total_ms / sum(v[1] for v in kst.values())
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "algorithmic_bytes_per_launch": algo, "launch_ms": per_launch_s * 1e3,
+            "share_of_step": share, "peak_source": peaks["source"]}
+
+
+def e2e_form(w, pos, mass, form, steps, rank):
+    """Through the C ABI with HOST buffers: each step uploads the state from
+    pinned host memory, advances one time step and reads the masses back."""
+    import torch
+    p = _params(w, form, rank)
+    pin_pos = torch.from_numpy(np.ascontiguousarray(pos)).pin_memory()
+    pin_mass = torch.from_numpy(np.ascontiguousarray(mass)).pin_memory()
+    out = torch.empty(w.n, dtype=torch.float64).pin_memory()
+    h = mtpt.mtpt_create(p)
+    lib = mtpt.load()
+    try:
+        def one():
+            rc = lib.mtpt_set_particles(h, w.n, pin_pos.data_ptr(), pin_mass.data_ptr())
+            rc = rc or lib.mtpt_step(h, 1)
+            rc = rc or lib.mtpt_get_masses(h, out.data_ptr())
+            if rc:
+                raise mtpt.MtptError(rc, "e2e step")
+        one()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+    finally:
+        mtpt.mtpt_destroy(h)
+    return {"value": w.n * steps / sec, "unit": "particle-steps/s",
+            "h2d_bytes_per_step": int(pos.nbytes + mass.nbytes),
+            "d2h_bytes_per_step": int(w.n * 8), "steps": steps}
+
+
+def cpu_baseline(w, pos, mass, form):
+    """The CPU oracle timed on one core over one full time step of the whole
+    workload; the same step on the GPU is compared with it element by element."""
+    import oracle as O
+    p = _params(w, form, 0)
+    op = O.OracleParams(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
+                        lo=tuple(w.lo) + (0.0,) * (3 - w.dim),
+                        hi=tuple(w.hi) + (0.0,) * (3 - w.dim), seed=w.seed)
+    t0 = time.perf_counter()
+    x_ref, m_ref, npairs = O.run(op, pos, mass, 1)
+    sec = time.perf_counter() - t0
+    with mtpt.Simulation(p, pos, mass) as sim:
+        sim.step(1)
+        x_gpu, m_gpu, info = sim.positions(), sim.masses(), sim.info()
+    err = float(np.abs(m_gpu - m_ref).max() / np.abs(m_ref).max())
+    return {"value": w.n / sec, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full time step of all {w.n} particles (serial C oracle, K-D tree)",
+            "seconds": sec, "pair_interactions_per_s": npairs / sec,
+            "parity": {"form": form, "max_rel_err_vs_oracle": err,
+                       "positions_bit_exact": bool(np.array_equal(x_gpu, x_ref)),
+                       "pair_count_equal": bool(info["pair_count"] == npairs)}}
+
+
+def reference_arm(args, w, pos, mass):
+    """The oracle as the reference implementation: each step is one oracle
+    time step of a bounded sample of the workload (a corner sub-box at the same
+    density)."""
+    import oracle as O
+    n_sample = int(args.ref_sample)
+    ws = w.scaled(n_sample)
+    ps, ms = workloads.initial_state(ws)
+    op = O.OracleParams(dim=ws.dim, D=ws.D, kappa=ws.kappa, dt=ws.dt, beta=ws.beta, lam=ws.lam,
+                        lo=tuple(ws.lo) + (0.0,) * (3 - ws.dim),
+                        hi=tuple(ws.hi) + (0.0,) * (3 - ws.dim), seed=ws.seed)
+    x, m = ps, ms
+    for s in range(args.warmup):
+        x, m, _ = O.run(op, x, m, 1, step0=s)
+    t0 = time.perf_counter()
+    pairs = 0
+    for s in range(args.steps):
+        x, m, np_ = O.run(op, x, m, 1, step0=args.warmup + s)
+        pairs += np_
+    sec = time.perf_counter() - t0
+    value = n_sample * args.steps / sec
+    sample = (f"{n_sample} particles of the workload at its density (box "
+              f"{ws.hi[0] - ws.lo[0]:.1f}^{ws.dim}), one oracle step per bench step")
+    return {"impl": "reference", "metric": "particle-steps/s", "value": value,
+            "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "dim": w.dim, "steps_in_config": w.steps},
+            "pair_interactions_per_s": pairs / sec,
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--forms", default="fp64,fp32w",
+                    help="comma list; the first is the headline value")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=200_000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world, rank, local = _dist()
+    w = workloads.get(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        pos, mass = workloads.initial_state(w)
+        print(json.dumps(reference_arm(args, w, pos, mass)))
+        return 0
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    mtpt.load()
+    pos, mass = workloads.initial_state(w)
+    forms = [f for f in args.forms.split(",") if f]
+    results = {f: time_form(w, pos, mass, f, args.steps, args.warmup, rank, world, dist)
+               for f in forms}
+    head = results[forms[0]]
+    peaks = _peaks()
+    e2e = e2e_form(w, pos, mass, forms[0], args.e2e_steps, rank)
+    line = {
+        "metric": "particle-steps/s", "value": head["particle_steps_per_s"],
+        "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[forms[0]], "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "dim": w.dim, "box": list(w.hi),
+                   "D": w.D, "kappa": w.kappa, "dt": w.dt, "lambda": w.lam,
+                   "form": forms[0], "steps_in_config": w.steps,
+                   "l2": "inputs larger than L2 (per-step working set > 300 MB)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "pair_interactions_per_s": head["pair_interactions_per_s"],
+        "pairs_per_particle_step": head["pairs_per_particle_step"],
+        "mass_drift_rel": head["mass_drift_rel"],
+        "gpu_launches": int(round(head["launches_per_step"] * args.steps)),
+        "clocks": head["clocks"],
+        "roofline": roofline(w, head, peaks),
+        "e2e": e2e,
+        "forms": {f: {k: v for k, v in r.items() if k not in ("clocks",)}
+                  for f, r in results.items()},
+    }
+    for f, r in results.items():
+        line["forms"][f]["roofline"] = roofline(w, r, peaks)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, pos, mass, forms[0])
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,207 @@
+/*
+ * mtpt.h -- C ABI of the GB300 mass-transfer particle-tracking (MTPT) step.
+ *
+ * One time step of the method of Schauer et al., "Parallelized Domain
+ * Decomposition for Multi-Dimensional Lagrangian Random Walk, Mass-Transfer
+ * Particle Tracking Schemes" (arXiv:2204.03756), Sec. 3:
+ *   1. random walk  X_i <- X_i + xi_i sqrt(2 D_RW dt), D_RW = kappa D, with
+ *      elastic reflection at the walls of the box (zero-flux boundary);
+ *   2. every pair with ||x_i - x_j|| <= psi, psi = lambda sqrt(4 D_MT dt / beta)
+ *      (Eq. "cutoff"), D_MT = (1 - kappa) D;
+ *   3. Gaussian kernel K_ij of variance h^2 = 2 D_MT dt / beta per axis
+ *      (simplified Eq. "kernel");
+ *   4. W_ij = K_ij / (1/2 (sum_i K_ij + sum_j K_ij)) = 2 K_ij / (r_i + r_j),
+ *      r the row sums of K including the self term;
+ *   5. M_i <- M_i + sum_j beta (M_j - M_i) W_ij  (Eq. "changemass", explicit).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: an mtpt_status code; 0 is success.  No call aborts or
+ *     exits the process; no C++ exception crosses the ABI.
+ *   - Ownership: the library copies caller buffers in and out; the caller
+ *     keeps ownership of its own memory.  The handle owns every device
+ *     allocation it makes until mtpt_destroy.
+ *   - Positions are structure-of-arrays float64: pos[a * n + i] is axis a of
+ *     particle i, a < dim.  Masses are float64, length n.  Particle i of the
+ *     last mtpt_set_particles* call keeps index i in every output.
+ *   - Stream: all device work of a handle is ordered on the handle's stream
+ *     (the legacy default stream unless mtpt_set_stream was called).  Calls
+ *     with host buffers synchronise that stream before returning; *_device
+ *     calls only enqueue work.
+ *   - Device errors found inside kernels (non-finite positions) are latched
+ *     in a device status word and reported by the next synchronising call.
+ */
+#ifndef MTPT_H
+#define MTPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum mtpt_status {
+    MTPT_OK = 0,
+    MTPT_ERR_INVALID_ARG = 1,     /* null pointer, bad dimension, bad parameter */
+    MTPT_ERR_OUT_OF_DOMAIN = 2,   /* a particle outside [lo, hi] or not finite */
+    MTPT_ERR_CUDA = 3,            /* a CUDA runtime call failed */
+    MTPT_ERR_NO_MEMORY = 4,       /* device or host allocation failed */
+    MTPT_ERR_STATE = 5,           /* call not valid in the handle's state */
+    MTPT_ERR_CAPACITY = 6         /* a caller buffer is too small */
+} mtpt_status;
+
+/* Precision forms of the pair arithmetic. */
+typedef enum mtpt_precision {
+    /* Every pair weight, sum and flux in binary64 (the paper's method). */
+    MTPT_FP64 = 0,
+    /* Pair kernel and weights in binary32 with the hardware exp; row sums and
+     * per-particle mass accumulation in compensated binary32, the mass update
+     * itself in binary64.  The neighbour test stays exact binary64, so the pair
+     * set equals MTPT_FP64's, and W_ij = W_ji bit for bit, so every pair flux is
+     * exactly antisymmetric. */
+    MTPT_FP32W = 1
+} mtpt_precision;
+
+/* Flags of mtpt_step_ex. */
+enum {
+    MTPT_DO_WALK = 1,       /* step 1 (random walk + reflection) */
+    MTPT_DO_TRANSFER = 2    /* steps 2-5 (search, kernel, normalise, exchange) */
+};
+
+/* Parameters of Sec. 2-3.  dim in {1, 2, 3}; D >= 0; 0 <= kappa <= 1;
+ * dt > 0; beta > 0 (the paper takes 1); lambda > 0 (the paper's Eq. "cutoff"
+ * prints 6, its cost analysis uses 3 in this notation; see the design notes);
+ * lo[a] < hi[a] for a < dim (entries a >= dim are ignored); seed keys the
+ * counter-based generator of the walk. */
+typedef struct mtpt_params {
+    int32_t dim;
+    int32_t precision;      /* an mtpt_precision */
+    double D;
+    double kappa;
+    double dt;
+    double beta;
+    double lambda;
+    double lo[3];
+    double hi[3];
+    uint64_t seed;
+} mtpt_params;
+
+/* Derived quantities and counters of a handle. */
+typedef struct mtpt_info {
+    int64_t n;                /* particles */
+    uint64_t step;            /* walk steps taken so far (the generator's step counter) */
+    uint64_t pair_count;      /* ordered neighbour pairs (i != j) summed over transfer steps */
+    double D_RW, D_MT;        /* kappa D, (1 - kappa) D */
+    double sigma;             /* sqrt(2 D_RW dt) */
+    double h2;                /* 2 D_MT dt / beta */
+    double psi, psi2;         /* cutoff and its square (as used by the pair test) */
+    double kernel_norm;       /* (2 pi h^2)^(-d/2) */
+    int32_t cells[3];         /* cell-list grid (1 on unused axes) */
+    double cell_width[3];
+} mtpt_info;
+
+typedef struct mtpt_handle mtpt_handle;
+
+/* Create a handle on the current CUDA device.  *out receives the handle.
+ * Validates the parameters (MTPT_ERR_INVALID_ARG).  Allocates nothing on the
+ * device until particles are set. */
+int mtpt_create(const mtpt_params* params, mtpt_handle** out);
+
+/* Release every device allocation and the handle.  Synchronises the stream.
+ * Passing NULL is a no-op returning MTPT_OK. */
+int mtpt_destroy(mtpt_handle* h);
+
+/* Order all later device work of the handle on `stream` (a cudaStream_t;
+ * NULL selects the legacy default stream). */
+int mtpt_set_stream(mtpt_handle* h, void* stream);
+
+/* Load n particles from HOST buffers: pos (dim x n, SoA float64) and mass (n
+ * float64).  Every coordinate must be finite and inside [lo, hi] of its axis
+ * (MTPT_ERR_OUT_OF_DOMAIN otherwise, and the handle keeps its old state).
+ * Particle ids are 0..n-1 in input order; they key the walk's generator.
+ * Resets the step counter and pair counter to 0.  n = 0 is allowed. */
+int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass);
+
+/* As mtpt_set_particles with DEVICE buffers, enqueued on the stream.
+ * The domain check runs on the device; a violation is reported by the next
+ * synchronising call. */
+int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
+                              const double* mass_dev);
+
+/* Advance nsteps full time steps (walk, then mass transfer on the moved
+ * positions).  Enqueued on the stream; returns the launch status. */
+int mtpt_step(mtpt_handle* h, int64_t nsteps);
+
+/* As mtpt_step with a subset of the step: flags is a combination of
+ * MTPT_DO_WALK and MTPT_DO_TRANSFER.  The walk's step counter advances only
+ * when MTPT_DO_WALK is set. */
+int mtpt_step_ex(mtpt_handle* h, int64_t nsteps, int32_t flags);
+
+/* Copy the masses, in input order, to a HOST buffer of n doubles.  Syncs and
+ * reports any latched device error. */
+int mtpt_get_masses(mtpt_handle* h, double* out);
+
+/* As mtpt_get_masses into a DEVICE buffer of n doubles (stream-ordered). */
+int mtpt_get_masses_device(mtpt_handle* h, double* out_dev);
+
+/* Copy the positions, in input order, to a HOST buffer of dim x n doubles
+ * (SoA).  Syncs. */
+int mtpt_get_positions(mtpt_handle* h, double* out);
+
+/* As mtpt_get_positions into a DEVICE buffer of dim x n doubles. */
+int mtpt_get_positions_device(mtpt_handle* h, double* out_dev);
+
+/* Row sums r_i = sum_j K_ij (self term included, in the paper's units, i.e.
+ * with the factor (2 pi h^2)^(-d/2)) of the most recent transfer step, in
+ * input order, to a HOST buffer of n doubles.  MTPT_ERR_STATE before the first
+ * transfer step. */
+int mtpt_get_row_sums(mtpt_handle* h, double* out);
+
+/* Neighbour pairs of the CURRENT positions: every ordered pair (i, j), i != j,
+ * with ||x_i - x_j||^2 <= psi^2, as input-order indices, written to the HOST
+ * arrays pair_i / pair_j of capacity `cap` (in no particular order).
+ * *count receives the number of pairs; if it exceeds cap, only cap pairs are
+ * written and MTPT_ERR_CAPACITY is returned.  Syncs.  Intended for tests. */
+int mtpt_get_pairs(mtpt_handle* h, int64_t cap, int64_t* count, uint32_t* pair_i,
+                   uint32_t* pair_j);
+
+/* Derived quantities and counters.  Syncs. */
+int mtpt_get_info(mtpt_handle* h, mtpt_info* out);
+
+/* Overwrite the walk's step counter (checkpoint resume: a run restarted from
+ * saved positions and masses with the saved counter reproduces the
+ * uninterrupted run bit for bit). */
+int mtpt_set_step(mtpt_handle* h, uint64_t step);
+
+/* Wait for the handle's stream and report any latched device error. */
+int mtpt_sync(mtpt_handle* h);
+
+/* Per-kernel timing (tracing).  While enabled, every kernel the handle
+ * launches is bracketed by two CUDA events on the handle's stream; the
+ * elapsed times are summed per kernel name.  Enabling adds two event records
+ * per launch and nothing else. */
+typedef struct mtpt_kernel_stat {
+    char name[40];          /* kernel name, NUL-terminated */
+    int64_t launches;       /* launches timed since the last reset */
+    double total_ms;        /* summed event-to-event time of those launches */
+} mtpt_kernel_stat;
+
+/* Start (on != 0) or stop timing; stopping keeps the collected figures. */
+int mtpt_timing_enable(mtpt_handle* h, int32_t on);
+
+/* Synchronise, fold pending events into the per-kernel sums, and copy up to
+ * `cap` entries into `out`; *count receives the number of distinct kernels. */
+int mtpt_timing_read(mtpt_handle* h, int32_t cap, mtpt_kernel_stat* out, int32_t* count);
+
+/* Clear the per-kernel sums. */
+int mtpt_timing_reset(mtpt_handle* h);
+
+/* Human-readable text of a status code (static storage). */
+const char* mtpt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MTPT_H */

@@ -1,0 +1,82 @@
+"""In-tree build of the CUDA library ``libmtpt.so`` for sm_103a (GB300).
+
+One translation unit (``csrc/mtpt.cu``) compiled by nvcc with
+``-gencode arch=compute_103a,code=sm_103a``; the shared object lands in
+``paper_2204_03756_gb300/_lib/`` next to the package, so the process that
+imports the package loads it from the source tree.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+
+PKG_DIR = os.path.dirname(os.path.abspath(__file__))
+SRC_DIR = os.path.join(PKG_DIR, "csrc")
+INCLUDE_DIR = os.path.join(os.path.dirname(PKG_DIR), "include")
+LIB_DIR = os.path.join(PKG_DIR, "_lib")
+LIB_PATH = os.path.join(LIB_DIR, "libmtpt.so")
+ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _sources():
+    out = [os.path.join(INCLUDE_DIR, "mtpt.h")]
+    for name in sorted(os.listdir(SRC_DIR)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            out.append(os.path.join(SRC_DIR, name))
+    return out
+
+
+def nvcc_path() -> str:
+    home = os.environ.get("CUDA_HOME") or os.environ.get("CUDA_PATH") or "/usr/local/cuda"
+    cand = os.path.join(home, "bin", "nvcc")
+    if os.path.exists(cand):
+        return cand
+    found = shutil.which("nvcc")
+    if not found:
+        raise RuntimeError("nvcc not found: set CUDA_HOME or put nvcc on PATH")
+    return found
+
+
+def build_command(out_path: str = LIB_PATH, extra=()) -> list:
+    return [nvcc_path(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17",
+            "-Xcompiler", "-fPIC", "-shared", "-I", INCLUDE_DIR, *extra,
+            "-o", out_path, os.path.join(SRC_DIR, "mtpt.cu")]
+
+
+def needs_build() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    return any(os.path.getmtime(s) > t for s in _sources())
+
+
+def start_build(force: bool = False):
+    """Launch nvcc in the background; returns the Popen (or None if the
+    library is up to date)."""
+    if not force and not needs_build():
+        return None
+    os.makedirs(LIB_DIR, exist_ok=True)
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    proc = subprocess.Popen(build_command(tmp), stdout=subprocess.PIPE,
+                            stderr=subprocess.STDOUT, text=True)
+    proc._mtpt_tmp = tmp  # type: ignore[attr-defined]
+    return proc
+
+
+def finish_build(proc) -> str:
+    if proc is None:
+        return LIB_PATH
+    out, _ = proc.communicate()
+    if proc.returncode != 0:
+        raise RuntimeError(f"nvcc failed ({proc.returncode}):\n{out}")
+    os.replace(proc._mtpt_tmp, LIB_PATH)
+    return LIB_PATH
+
+
+def build(force: bool = False) -> str:
+    return finish_build(start_build(force))
+
+
+if __name__ == "__main__":
+    print(build(force=True))

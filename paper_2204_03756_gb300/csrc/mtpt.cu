@@ -1,0 +1,741 @@
+// mtpt.cu -- host side of the C ABI declared in include/mtpt.h.
+//
+// A handle owns the particle state on one device in cell order and runs one
+// time step of Sec. 3 as a fixed sequence of kernels on the handle's stream:
+//   walk_key -> scan (3 launches) -> scatter -> gather -> rowsum -> exchange
+// No step goes through the host: the only host<->device traffic is in
+// mtpt_set_particles / mtpt_get_*.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/mtpt.h"
+#include "kernels.cuh"
+
+using namespace mtpt;
+
+namespace {
+
+constexpr int kMaxDim = 3;
+
+#define MTPT_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t err_ = (expr);                            \
+        if (err_ != cudaSuccess) {                            \
+            (void)cudaGetLastError();                         \
+            return MTPT_ERR_CUDA;                             \
+        }                                                     \
+    } while (0)
+
+#define MTPT_TRY(expr)              \
+    do {                            \
+        int rc_ = (expr);           \
+        if (rc_ != MTPT_OK) return rc_; \
+    } while (0)
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t count = 0;
+    int ensure(size_t n) {
+        if (n <= count && p) return MTPT_OK;
+        release();
+        if (n == 0) return MTPT_OK;
+        if (cudaMalloc(reinterpret_cast<void**>(&p), n * sizeof(T)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            p = nullptr;
+            count = 0;
+            return MTPT_ERR_NO_MEMORY;
+        }
+        count = n;
+        return MTPT_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        count = 0;
+    }
+};
+
+int grid_for(int64_t n) { return int((n + kBlock - 1) / kBlock); }
+
+}  // namespace
+
+struct mtpt_handle;
+namespace {
+cudaEvent_t take_event(mtpt_handle* h);
+// Brackets one kernel launch with timing events when timing is enabled.
+struct KernelTimer {
+    mtpt_handle* h;
+    const char* name;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KernelTimer(mtpt_handle* hh, const char* nm);
+    ~KernelTimer();
+};
+}  // namespace
+#define MTPT_CAT_(a, b) a##b
+#define MTPT_CAT(a, b) MTPT_CAT_(a, b)
+#define MTPT_TIMED(h, name) KernelTimer MTPT_CAT(kernel_timer_, __LINE__)((h), (name))
+
+struct mtpt_handle {
+    mtpt_params prm{};
+    cudaStream_t stream = nullptr;
+    // derived (Sec. 3)
+    double D_RW = 0, D_MT = 0, sigma = 0, h2 = 0, psi = 0, psi2 = 0, kernel_norm = 0;
+    bool transfer_enabled = false;
+    Box box{};
+    Grid grid{};
+    PairParams pp{};
+    int64_t n = 0, cap = 0;
+    int64_t n_cells = 0, n_cells_pad = 0;
+    uint64_t step = 0;
+    bool have_row_sums = false;
+    // state, double-buffered (cur = index into the pair)
+    DevBuf<double> pos[2], mass[2];
+    DevBuf<uint32_t> id[2];
+    int cur = 0;
+    // per-step scratch
+    DevBuf<uint32_t> key, perm, cell, count, start, tile_sums;
+    DevBuf<float> xl;
+    DevBuf<double> r64;
+    DevBuf<float> r32;
+    DevBuf<float2> msplit;
+    DevBuf<double> out_tmp;
+    DevBuf<double> exp_table;
+    DevBuf<uint32_t> status;
+    DevBuf<unsigned long long> pair_counter;
+    DevBuf<unsigned long long> emit_counter;
+    DevBuf<uint32_t> emit_i, emit_j;
+    // per-kernel timing
+    bool timing = false;
+    struct PendingEvent { const char* name; cudaEvent_t a, b; };
+    std::vector<PendingEvent> pending;
+    std::vector<cudaEvent_t> spare_events;
+    struct Stat { const char* name; int64_t launches; double total_ms; };
+    std::vector<Stat> stats;
+};
+
+namespace {
+
+cudaEvent_t take_event(mtpt_handle* h) {
+    if (!h->spare_events.empty()) {
+        cudaEvent_t e = h->spare_events.back();
+        h->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+KernelTimer::KernelTimer(mtpt_handle* hh, const char* nm) : h(hh), name(nm) {
+    if (!h->timing) return;
+    a = take_event(h);
+    b = take_event(h);
+    if (a && b) cudaEventRecord(a, h->stream);
+}
+
+KernelTimer::~KernelTimer() {
+    if (!h->timing || !a || !b) return;
+    cudaEventRecord(b, h->stream);
+    h->pending.push_back({name, a, b});
+}
+
+int fold_timing(mtpt_handle* h) {
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (auto& pe : h->pending) {
+        float ms = 0.0f;
+        MTPT_CUDA_TRY(cudaEventElapsedTime(&ms, pe.a, pe.b));
+        bool found = false;
+        for (auto& st : h->stats) {
+            if (std::strcmp(st.name, pe.name) == 0) {
+                st.launches += 1;
+                st.total_ms += ms;
+                found = true;
+                break;
+            }
+        }
+        if (!found) h->stats.push_back({pe.name, 1, double(ms)});
+        h->spare_events.push_back(pe.a);
+        h->spare_events.push_back(pe.b);
+    }
+    h->pending.clear();
+    return MTPT_OK;
+}
+
+int validate_params(const mtpt_params* p) {
+    if (!p) return MTPT_ERR_INVALID_ARG;
+    if (p->dim < 1 || p->dim > kMaxDim) return MTPT_ERR_INVALID_ARG;
+    if (p->precision != MTPT_FP64 && p->precision != MTPT_FP32W) return MTPT_ERR_INVALID_ARG;
+    if (!(p->D >= 0.0) || !std::isfinite(p->D)) return MTPT_ERR_INVALID_ARG;
+    if (!(p->kappa >= 0.0 && p->kappa <= 1.0)) return MTPT_ERR_INVALID_ARG;
+    if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return MTPT_ERR_INVALID_ARG;
+    if (!(p->beta > 0.0) || !std::isfinite(p->beta)) return MTPT_ERR_INVALID_ARG;
+    if (!(p->lambda > 0.0 && p->lambda <= 20.0)) return MTPT_ERR_INVALID_ARG;
+    for (int a = 0; a < p->dim; ++a) {
+        if (!std::isfinite(p->lo[a]) || !std::isfinite(p->hi[a]) || !(p->lo[a] < p->hi[a]))
+            return MTPT_ERR_INVALID_ARG;
+    }
+    return MTPT_OK;
+}
+
+// Sec. 3: D_RW = kappa D, D_MT = (1 - kappa) D, walk scale sqrt(2 D_RW dt),
+// h^2 = 2 D_MT dt / beta, psi = lambda sqrt(4 D_MT dt / beta).
+void derive(mtpt_handle* h) {
+    const mtpt_params& p = h->prm;
+    h->D_RW = p.kappa * p.D;
+    h->D_MT = (1.0 - p.kappa) * p.D;
+    h->sigma = std::sqrt(2.0 * h->D_RW * p.dt);
+    h->h2 = 2.0 * h->D_MT * p.dt / p.beta;
+    h->psi = p.lambda * std::sqrt(4.0 * h->D_MT * p.dt / p.beta);
+    h->psi2 = h->psi * h->psi;
+    h->kernel_norm = h->h2 > 0.0 ? std::pow(2.0 * M_PI * h->h2, -0.5 * p.dim) : 0.0;
+    h->transfer_enabled = h->h2 > 0.0;
+    for (int a = 0; a < 3; ++a) {
+        h->box.lo[a] = a < p.dim ? p.lo[a] : 0.0;
+        h->box.hi[a] = a < p.dim ? p.hi[a] : 0.0;
+    }
+}
+
+// Cell grid: width >= psi on every axis (slightly above, so a pair at
+// distance psi never spans two cell boundaries under rounding), with the
+// total cell count capped near 4 n so sparse boxes do not allocate huge
+// empty grids (cells then just get wider, which stays correct).
+int setup_grid(mtpt_handle* h) {
+    const mtpt_params& p = h->prm;
+    Grid& g = h->grid;
+    const double psi_eff = h->psi * (1.0 + 1e-9);
+    double ncell[3] = {1, 1, 1};
+    for (int a = 0; a < p.dim; ++a) {
+        const double L = p.hi[a] - p.lo[a];
+        double k = h->transfer_enabled ? std::floor(L / psi_eff) : 1.0;
+        ncell[a] = std::max(1.0, std::min(k, double(1 << 30)));
+    }
+    const double cap = std::max(4.0 * double(h->n) + 64.0, 64.0);
+    double total = ncell[0] * ncell[1] * ncell[2];
+    for (int guard = 0; guard < 64 && total > cap; ++guard) {
+        const double f = std::pow(cap / total, 1.0 / p.dim);
+        for (int a = 0; a < p.dim; ++a) ncell[a] = std::max(1.0, std::floor(ncell[a] * f));
+        total = ncell[0] * ncell[1] * ncell[2];
+        if (total > cap) {
+            int amax = 0;
+            for (int a = 1; a < p.dim; ++a)
+                if (ncell[a] > ncell[amax]) amax = a;
+            ncell[amax] = std::max(1.0, ncell[amax] - 1.0);
+            total = ncell[0] * ncell[1] * ncell[2];
+        }
+    }
+    if (total > 2.0e9) return MTPT_ERR_INVALID_ARG;
+    double wmax_over_psi = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = int(ncell[a]);
+        g.lo[a] = a < p.dim ? p.lo[a] : 0.0;
+        g.w[a] = a < p.dim ? (p.hi[a] - p.lo[a]) / ncell[a] : 1.0;
+        g.inv_w[a] = 1.0 / g.w[a];
+        g.wf[a] = float(g.w[a]);
+        if (a < p.dim && h->psi > 0.0) wmax_over_psi += g.w[a] / h->psi;
+    }
+    h->n_cells = int64_t(total);
+    h->n_cells_pad = ((h->n_cells + 1 + kScanTile - 1) / kScanTile) * kScanTile;
+
+    // Pair-test band.  With u = 2^-24, every binary32 coordinate offset is
+    // within u w of its exact value and each of the four roundings in
+    // (xl_j + shift) - xl_i adds at most u (2 w); so the squared distance
+    // evaluated in binary32 is within u (3 + 12 sum_a w_a / psi) psi^2 of the
+    // exact one for any candidate near the cutoff.  Four times that bound is
+    // the band half-width.
+    PairParams& pp = h->pp;
+    const double u = std::ldexp(1.0, -24);
+    const double eta = 4.0 * u * (3.0 + 12.0 * wmax_over_psi);
+    pp.psi2 = h->psi2;
+    pp.band_lo = float(h->psi2 * (1.0 - eta));
+    pp.band_hi = float(h->psi2 * (1.0 + eta));
+    pp.a = h->h2 > 0.0 ? 1.0 / (2.0 * h->h2) : 0.0;
+    pp.a_log2e = float(pp.a * 1.4426950408889634);
+    pp.beta = p.beta;
+    // ln 2 = ln2_hi + ln2_lo (leading and trailing binary64 parts)
+    const double ln2_hi = 6.93147180559945286227e-01, ln2_lo = 2.31904681384629955842e-17;
+    pp.ec.inv_step = 64.0 / ln2_hi;
+    pp.ec.step_hi = ln2_hi / 64.0;
+    pp.ec.step_lo = ln2_lo / 64.0;
+    return MTPT_OK;
+}
+
+int upload_exp_table(mtpt_handle* h) {
+    MTPT_TRY(h->exp_table.ensure(64));
+    double t[64];
+    for (int j = 0; j < 64; ++j) t[j] = double(exp2l(-static_cast<long double>(j) / 64.0L));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h->exp_table.p, t, sizeof(t), cudaMemcpyHostToDevice, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MTPT_OK;
+}
+
+int ensure_capacity(mtpt_handle* h, int64_t n) {
+    const int d = h->prm.dim;
+    const int64_t cap = std::max<int64_t>(n, 1);
+    if (cap > h->cap) {
+        for (int b = 0; b < 2; ++b) {
+            MTPT_TRY(h->pos[b].ensure(size_t(d) * cap));
+            MTPT_TRY(h->mass[b].ensure(cap));
+            MTPT_TRY(h->id[b].ensure(cap));
+        }
+        MTPT_TRY(h->key.ensure(cap));
+        MTPT_TRY(h->perm.ensure(cap));
+        MTPT_TRY(h->cell.ensure(cap));
+        MTPT_TRY(h->xl.ensure(size_t(d) * cap));
+        if (h->prm.precision == MTPT_FP64) {
+            MTPT_TRY(h->r64.ensure(cap));
+        } else {
+            MTPT_TRY(h->r32.ensure(cap));
+            MTPT_TRY(h->msplit.ensure(cap));
+        }
+        h->cap = cap;
+    }
+    MTPT_TRY(h->status.ensure(1));
+    MTPT_TRY(h->pair_counter.ensure(1));
+    return MTPT_OK;
+}
+
+int ensure_cells(mtpt_handle* h) {
+    const size_t padded = size_t(h->n_cells_pad);
+    if (padded > h->count.count) {
+        MTPT_TRY(h->count.ensure(padded));
+        MTPT_TRY(h->start.ensure(padded));
+        MTPT_TRY(h->tile_sums.ensure(padded / kScanTile));
+    }
+    // counts start (and, after each scatter, end) at zero
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->count.p, 0, padded * sizeof(uint32_t), h->stream));
+    return MTPT_OK;
+}
+
+int read_status(mtpt_handle* h) {
+    uint32_t st = 0;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&st, h->status.p, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (st & (kStatusNonFinite | kStatusOutOfDomain)) return MTPT_ERR_OUT_OF_DOMAIN;
+    return MTPT_OK;
+}
+
+template <int DIM>
+int launch_step(mtpt_handle* h, int flags) {
+    const int n = int(h->n);
+    if (n == 0) return MTPT_OK;
+    const int64_t stride = h->cap;
+    const int blocks = grid_for(n);
+    cudaStream_t st = h->stream;
+    const bool walk = (flags & MTPT_DO_WALK) && h->sigma > 0.0;
+    const bool transfer = (flags & MTPT_DO_TRANSFER) && h->transfer_enabled;
+    const int c = h->cur, o = 1 - h->cur;
+    if (walk || transfer) {
+        MTPT_TIMED(h, "walk_key");
+        k_walk_key<DIM><<<blocks, kBlock, 0, st>>>(
+            n, stride, h->pos[c].p, h->id[c].p, h->prm.seed, h->step, h->sigma, walk ? 1 : 0,
+            transfer ? 1 : 0, h->box, h->grid, h->key.p, h->count.p, h->status.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    if (flags & MTPT_DO_WALK) h->step += 1;
+    if (!transfer) return MTPT_OK;
+
+    const int ntiles = int(h->n_cells_pad / kScanTile);
+    const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
+    {
+        MTPT_TIMED(h, "scan_tile_sums");
+        k_scan_tile_sums<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p);
+    }
+    {
+        MTPT_TIMED(h, "scan_tile_offsets");
+        k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(h->tile_sums.p, ntiles);
+    }
+    {
+        MTPT_TIMED(h, "scan_apply");
+        k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p,
+                                                      reinterpret_cast<uint4*>(h->start.p));
+    }
+    {
+        MTPT_TIMED(h, "scatter");
+        k_scatter<<<blocks, kBlock, 0, st>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
+    }
+    const bool split = h->prm.precision == MTPT_FP32W;
+    if (split) {
+        MTPT_TIMED(h, "gather");
+        k_gather<DIM, true><<<blocks, kBlock, 0, st>>>(
+            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, h->msplit.p, h->grid);
+    } else {
+        MTPT_TIMED(h, "gather");
+        k_gather<DIM, false><<<blocks, kBlock, 0, st>>>(
+            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, nullptr, h->grid);
+    }
+    MTPT_CUDA_TRY(cudaGetLastError());
+    // state now lives in buffer o (cell order); masses are updated into c
+    const double* pos_s = h->pos[o].p;
+    if (!split) {
+        {
+        MTPT_TIMED(h, "rowsum_f64");
+        k_rowsum_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
+                                                     h->start.p, h->exp_table.p, h->grid, h->pp,
+                                                     h->r64.p, h->pair_counter.p);
+        }
+        MTPT_TIMED(h, "exchange_f64");
+        k_exchange_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
+                                                       h->start.p, h->exp_table.p, h->grid, h->pp,
+                                                       h->r64.p, h->mass[o].p, h->mass[c].p);
+    } else {
+        {
+        MTPT_TIMED(h, "rowsum_f32");
+        k_rowsum_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
+                                                     h->start.p, h->grid, h->pp, h->r32.p,
+                                                     h->pair_counter.p);
+        }
+        MTPT_TIMED(h, "exchange_f32");
+        k_exchange_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
+                                                       h->start.p, h->grid, h->pp, h->r32.p,
+                                                       h->msplit.p, h->mass[o].p, h->mass[c].p);
+    }
+    MTPT_CUDA_TRY(cudaGetLastError());
+    // positions and ids live in o; the updated masses were written into c's
+    // buffer: swap the mass pair so both sit at index o, then make o current.
+    std::swap(h->mass[c], h->mass[o]);
+    h->cur = o;
+    h->have_row_sums = true;
+    return MTPT_OK;
+}
+
+int dispatch_step(mtpt_handle* h, int flags) {
+    switch (h->prm.dim) {
+        case 1: return launch_step<1>(h, flags);
+        case 2: return launch_step<2>(h, flags);
+        default: return launch_step<3>(h, flags);
+    }
+}
+
+int ensure_out_tmp(mtpt_handle* h) {
+    return h->out_tmp.ensure(size_t(h->prm.dim) * std::max<int64_t>(h->n, 1));
+}
+
+// Copy `naxes` arrays of the current state (stride cap, cell order) into
+// `out_dev` (stride n, input order), multiplied by `scale`.
+template <typename T>
+int unpermute_to(mtpt_handle* h, const T* src, int naxes, double scale, double* out_dev) {
+    if (h->n == 0) return MTPT_OK;
+    k_unpermute<T><<<grid_for(h->n), kBlock, 0, h->stream>>>(int(h->n), h->cap, naxes,
+                                                            h->id[h->cur].p, src, scale, out_dev);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
+}
+
+int copy_out_host(mtpt_handle* h, int naxes, double* out) {
+    const size_t bytes = size_t(naxes) * size_t(h->n) * sizeof(double);
+    if (bytes) MTPT_CUDA_TRY(cudaMemcpyAsync(out, h->out_tmp.p, bytes, cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
+int load_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass,
+                   cudaMemcpyKind kind) {
+    const int d = h->prm.dim;
+    if (n < 0 || n > int64_t(0x7fffffff) - kBlock) return MTPT_ERR_INVALID_ARG;
+    if (n > 0 && (!pos || !mass)) return MTPT_ERR_INVALID_ARG;
+    h->n = n;
+    MTPT_TRY(ensure_capacity(h, n));
+    MTPT_TRY(setup_grid(h));
+    if (h->transfer_enabled) MTPT_TRY(ensure_cells(h));
+    if (!h->exp_table.p) MTPT_TRY(upload_exp_table(h));
+    h->cur = 0;
+    if (n > 0) {
+        MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[0].p, size_t(h->cap) * sizeof(double), pos,
+                                        size_t(n) * sizeof(double), size_t(n) * sizeof(double), d,
+                                        kind, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[0].p, mass, size_t(n) * sizeof(double), kind, h->stream));
+        k_iota<<<grid_for(n), kBlock, 0, h->stream>>>(int(n), h->id[0].p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(uint32_t), h->stream));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->pair_counter.p, 0, sizeof(unsigned long long), h->stream));
+    h->step = 0;
+    h->have_row_sums = false;
+    return MTPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mtpt_create(const mtpt_params* params, mtpt_handle** out) {
+    if (!out) return MTPT_ERR_INVALID_ARG;
+    *out = nullptr;
+    MTPT_TRY(validate_params(params));
+    mtpt_handle* h = new (std::nothrow) mtpt_handle();
+    if (!h) return MTPT_ERR_NO_MEMORY;
+    h->prm = *params;
+    derive(h);
+    *out = h;
+    return MTPT_OK;
+}
+
+int mtpt_destroy(mtpt_handle* h) {
+    if (!h) return MTPT_OK;
+    cudaStreamSynchronize(h->stream);
+    for (int b = 0; b < 2; ++b) {
+        h->pos[b].release();
+        h->mass[b].release();
+        h->id[b].release();
+    }
+    h->key.release(); h->perm.release(); h->cell.release(); h->count.release();
+    h->start.release(); h->tile_sums.release(); h->xl.release(); h->r64.release();
+    h->r32.release(); h->msplit.release(); h->out_tmp.release(); h->exp_table.release();
+    h->status.release(); h->pair_counter.release(); h->emit_counter.release();
+    h->emit_i.release(); h->emit_j.release();
+    for (auto& pe : h->pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (auto e : h->spare_events) cudaEventDestroy(e);
+    delete h;
+    return MTPT_OK;
+}
+
+int mtpt_set_stream(mtpt_handle* h, void* stream) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return MTPT_OK;
+}
+
+int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    if (n < 0) return MTPT_ERR_INVALID_ARG;
+    if (n > 0 && (!pos || !mass)) return MTPT_ERR_INVALID_ARG;
+    const int d = h->prm.dim;
+    for (int a = 0; a < d; ++a) {
+        const double lo = h->prm.lo[a], hi = h->prm.hi[a];
+        const double* x = pos + size_t(a) * size_t(n);
+        for (int64_t i = 0; i < n; ++i)
+            if (!(x[i] >= lo && x[i] <= hi)) return MTPT_ERR_OUT_OF_DOMAIN;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(mass[i])) return MTPT_ERR_INVALID_ARG;
+    MTPT_TRY(load_particles(h, n, pos, mass, cudaMemcpyHostToDevice));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MTPT_OK;
+}
+
+int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
+                              const double* mass_dev) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    MTPT_TRY(load_particles(h, n, pos_dev, mass_dev, cudaMemcpyDeviceToDevice));
+    if (n > 0) {
+        const int blocks = grid_for(n);
+        switch (h->prm.dim) {
+            case 1: k_check_domain<1><<<blocks, kBlock, 0, h->stream>>>(int(n), h->cap, h->pos[0].p, h->box, h->status.p); break;
+            case 2: k_check_domain<2><<<blocks, kBlock, 0, h->stream>>>(int(n), h->cap, h->pos[0].p, h->box, h->status.p); break;
+            default: k_check_domain<3><<<blocks, kBlock, 0, h->stream>>>(int(n), h->cap, h->pos[0].p, h->box, h->status.p); break;
+        }
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    return MTPT_OK;
+}
+
+int mtpt_step_ex(mtpt_handle* h, int64_t nsteps, int32_t flags) {
+    if (!h || nsteps < 0) return MTPT_ERR_INVALID_ARG;
+    if (flags & ~(MTPT_DO_WALK | MTPT_DO_TRANSFER)) return MTPT_ERR_INVALID_ARG;
+    if (!h->status.p) return MTPT_ERR_STATE;
+    for (int64_t s = 0; s < nsteps; ++s) MTPT_TRY(dispatch_step(h, flags));
+    return MTPT_OK;
+}
+
+int mtpt_step(mtpt_handle* h, int64_t nsteps) {
+    return mtpt_step_ex(h, nsteps, MTPT_DO_WALK | MTPT_DO_TRANSFER);
+}
+
+int mtpt_get_masses_device(mtpt_handle* h, double* out_dev) {
+    if (!h || (!out_dev && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->status.p) return MTPT_ERR_STATE;
+    return unpermute_to<double>(h, h->mass[h->cur].p, 1, 1.0, out_dev);
+}
+
+int mtpt_get_masses(mtpt_handle* h, double* out) {
+    if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->status.p) return MTPT_ERR_STATE;
+    MTPT_TRY(ensure_out_tmp(h));
+    MTPT_TRY(unpermute_to<double>(h, h->mass[h->cur].p, 1, 1.0, h->out_tmp.p));
+    return copy_out_host(h, 1, out);
+}
+
+int mtpt_get_positions_device(mtpt_handle* h, double* out_dev) {
+    if (!h || (!out_dev && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->status.p) return MTPT_ERR_STATE;
+    return unpermute_to<double>(h, h->pos[h->cur].p, h->prm.dim, 1.0, out_dev);
+}
+
+int mtpt_get_positions(mtpt_handle* h, double* out) {
+    if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->status.p) return MTPT_ERR_STATE;
+    MTPT_TRY(ensure_out_tmp(h));
+    MTPT_TRY(unpermute_to<double>(h, h->pos[h->cur].p, h->prm.dim, 1.0, h->out_tmp.p));
+    return copy_out_host(h, h->prm.dim, out);
+}
+
+int mtpt_get_row_sums(mtpt_handle* h, double* out) {
+    if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->status.p || !h->have_row_sums) return MTPT_ERR_STATE;
+    MTPT_TRY(ensure_out_tmp(h));
+    if (h->prm.precision == MTPT_FP64)
+        MTPT_TRY(unpermute_to<double>(h, h->r64.p, 1, h->kernel_norm, h->out_tmp.p));
+    else
+        MTPT_TRY(unpermute_to<float>(h, h->r32.p, 1, h->kernel_norm, h->out_tmp.p));
+    return copy_out_host(h, 1, out);
+}
+
+int mtpt_get_pairs(mtpt_handle* h, int64_t cap, int64_t* count, uint32_t* pair_i,
+                   uint32_t* pair_j) {
+    if (!h || !count || cap < 0 || (cap > 0 && (!pair_i || !pair_j))) return MTPT_ERR_INVALID_ARG;
+    if (!h->status.p) return MTPT_ERR_STATE;
+    *count = 0;
+    if (h->n == 0 || !h->transfer_enabled) return read_status(h);
+    // Re-sort the current positions (no walk, no transfer) so the cell list
+    // describes them, then emit every accepted pair.
+    const int n = int(h->n);
+    const int blocks = grid_for(n);
+    const int64_t stride = h->cap;
+    const int c = h->cur, o = 1 - h->cur;
+    MTPT_TRY(h->emit_counter.ensure(1));
+    const size_t ecap = size_t(std::max<int64_t>(cap, 1));
+    MTPT_TRY(h->emit_i.ensure(ecap));
+    MTPT_TRY(h->emit_j.ensure(ecap));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->emit_counter.p, 0, sizeof(unsigned long long), h->stream));
+    const int ntiles = int(h->n_cells_pad / kScanTile);
+    auto sort_and_emit = [&](auto dim_tag) -> int {
+        constexpr int DIM = decltype(dim_tag)::value;
+        k_walk_key<DIM><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->pos[c].p, h->id[c].p, h->prm.seed, h->step, 0.0, 0, 1, h->box, h->grid,
+            h->key.p, h->count.p, h->status.p);
+        const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
+        k_scan_tile_sums<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p);
+        k_scan_tile_offsets<<<1, kScanThreads, 0, h->stream>>>(h->tile_sums.p, ntiles);
+        k_scan_apply<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p,
+                                                             reinterpret_cast<uint4*>(h->start.p));
+        k_scatter<<<blocks, kBlock, 0, h->stream>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
+        if (h->prm.precision == MTPT_FP32W)
+            k_gather<DIM, true><<<blocks, kBlock, 0, h->stream>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
+                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, h->msplit.p, h->grid);
+        else
+            k_gather<DIM, false><<<blocks, kBlock, 0, h->stream>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
+                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, nullptr, h->grid);
+        k_emit_pairs<DIM><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->pos[o].p, h->xl.p, h->cell.p, h->start.p, h->id[o].p, h->grid, h->pp,
+            (unsigned long long)cap, h->emit_counter.p, h->emit_i.p, h->emit_j.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+        return MTPT_OK;
+    };
+    int rc;
+    switch (h->prm.dim) {
+        case 1: rc = sort_and_emit(std::integral_constant<int, 1>{}); break;
+        case 2: rc = sort_and_emit(std::integral_constant<int, 2>{}); break;
+        default: rc = sort_and_emit(std::integral_constant<int, 3>{}); break;
+    }
+    MTPT_TRY(rc);
+    // the gathered copy in o is the same state in cell order: make it current
+    h->cur = o;
+    h->have_row_sums = false;
+    unsigned long long total = 0;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&total, h->emit_counter.p, sizeof(total), cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *count = int64_t(total);
+    const int64_t ncopy = std::min<int64_t>(int64_t(total), cap);
+    if (ncopy > 0) {
+        MTPT_CUDA_TRY(cudaMemcpy(pair_i, h->emit_i.p, size_t(ncopy) * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        MTPT_CUDA_TRY(cudaMemcpy(pair_j, h->emit_j.p, size_t(ncopy) * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    }
+    MTPT_TRY(read_status(h));
+    return int64_t(total) > cap ? MTPT_ERR_CAPACITY : MTPT_OK;
+}
+
+int mtpt_get_info(mtpt_handle* h, mtpt_info* out) {
+    if (!h || !out) return MTPT_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n = h->n;
+    out->step = h->step;
+    if (h->pair_counter.p) {
+        unsigned long long pc = 0;
+        MTPT_CUDA_TRY(cudaMemcpyAsync(&pc, h->pair_counter.p, sizeof(pc), cudaMemcpyDeviceToHost, h->stream));
+        MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        out->pair_count = pc;
+    }
+    out->D_RW = h->D_RW;
+    out->D_MT = h->D_MT;
+    out->sigma = h->sigma;
+    out->h2 = h->h2;
+    out->psi = h->psi;
+    out->psi2 = h->psi2;
+    out->kernel_norm = h->kernel_norm;
+    for (int a = 0; a < 3; ++a) {
+        out->cells[a] = h->grid.n[a] ? h->grid.n[a] : 1;
+        out->cell_width[a] = h->grid.w[a];
+    }
+    return h->status.p ? read_status(h) : MTPT_OK;
+}
+
+int mtpt_set_step(mtpt_handle* h, uint64_t step) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    h->step = step;
+    return MTPT_OK;
+}
+
+int mtpt_sync(mtpt_handle* h) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return h->status.p ? read_status(h) : MTPT_OK;
+}
+
+int mtpt_timing_enable(mtpt_handle* h, int32_t on) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    h->timing = on != 0;
+    return MTPT_OK;
+}
+
+int mtpt_timing_read(mtpt_handle* h, int32_t cap, mtpt_kernel_stat* out, int32_t* count) {
+    if (!h || !count || cap < 0 || (cap > 0 && !out)) return MTPT_ERR_INVALID_ARG;
+    MTPT_TRY(fold_timing(h));
+    *count = int32_t(h->stats.size());
+    for (int32_t k = 0; k < cap && k < *count; ++k) {
+        std::memset(&out[k], 0, sizeof(out[k]));
+        std::strncpy(out[k].name, h->stats[k].name, sizeof(out[k].name) - 1);
+        out[k].launches = h->stats[k].launches;
+        out[k].total_ms = h->stats[k].total_ms;
+    }
+    return MTPT_OK;
+}
+
+int mtpt_timing_reset(mtpt_handle* h) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    MTPT_TRY(fold_timing(h));
+    h->stats.clear();
+    return MTPT_OK;
+}
+
+const char* mtpt_status_string(int status) {
+    switch (status) {
+        case MTPT_OK: return "ok";
+        case MTPT_ERR_INVALID_ARG: return "invalid argument";
+        case MTPT_ERR_OUT_OF_DOMAIN: return "particle outside the box or not finite";
+        case MTPT_ERR_CUDA: return "CUDA runtime error";
+        case MTPT_ERR_NO_MEMORY: return "allocation failed";
+        case MTPT_ERR_STATE: return "call not valid in the handle's state";
+        case MTPT_ERR_CAPACITY: return "output buffer too small";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,346 @@
+"""Python binding of the C ABI in ``include/mtpt.h`` (argument marshalling only).
+
+Every function keeps the C name.  Host arrays are numpy; device arrays are
+torch CUDA tensors (PyTorch supplies device memory and the stream: the
+``*_device`` calls run on ``torch.cuda.current_stream()``).  The binding
+loads the in-tree ``_lib/libmtpt.so`` and raises if it is missing: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+MTPT_OK = 0
+MTPT_ERR_INVALID_ARG = 1
+MTPT_ERR_OUT_OF_DOMAIN = 2
+MTPT_ERR_CUDA = 3
+MTPT_ERR_NO_MEMORY = 4
+MTPT_ERR_STATE = 5
+MTPT_ERR_CAPACITY = 6
+
+MTPT_FP64 = 0
+MTPT_FP32W = 1
+
+MTPT_DO_WALK = 1
+MTPT_DO_TRANSFER = 2
+
+EXPORTED = [
+    "mtpt_create", "mtpt_destroy", "mtpt_set_stream", "mtpt_set_particles",
+    "mtpt_set_particles_device", "mtpt_step", "mtpt_step_ex", "mtpt_get_masses",
+    "mtpt_get_masses_device", "mtpt_get_positions", "mtpt_get_positions_device",
+    "mtpt_get_row_sums", "mtpt_get_pairs", "mtpt_get_info", "mtpt_set_step", "mtpt_sync",
+    "mtpt_timing_enable", "mtpt_timing_read", "mtpt_timing_reset", "mtpt_status_string",
+]
+
+
+class MtptError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} (status {code})")
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("D", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("dt", ctypes.c_double), ("beta", ctypes.c_double),
+                ("lam", ctypes.c_double),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("seed", ctypes.c_uint64)]
+
+
+class _KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("step", ctypes.c_uint64),
+                ("pair_count", ctypes.c_uint64),
+                ("D_RW", ctypes.c_double), ("D_MT", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("h2", ctypes.c_double),
+                ("psi", ctypes.c_double), ("psi2", ctypes.c_double),
+                ("kernel_norm", ctypes.c_double),
+                ("cells", ctypes.c_int32 * 3), ("cell_width", ctypes.c_double * 3)]
+
+
+@dataclass
+class Params:
+    """Sec. 2-3 parameters: dimension, D, kappa = D_RW / D, dt, beta, lambda
+    (psi = lambda sqrt(4 D_MT dt / beta)), box [lo, hi] with reflecting walls,
+    walk seed and precision form (MTPT_FP64 or MTPT_FP32W)."""
+    dim: int = 2
+    D: float = 1.0
+    kappa: float = 0.5
+    dt: float = 0.1
+    beta: float = 1.0
+    lam: float = 3.0
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+    seed: int = 0
+    precision: int = MTPT_FP64
+
+    def c(self) -> _Params:
+        lo = list(self.lo)[:3] + [0.0] * (3 - min(3, len(self.lo)))
+        hi = list(self.hi)[:3] + [0.0] * (3 - min(3, len(self.hi)))
+        return _Params(self.dim, self.precision, self.D, self.kappa, self.dt, self.beta,
+                       self.lam, (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi),
+                       self.seed)
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Load the in-tree CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.mtpt_create.argtypes = [P(_Params), P(vp)]
+    lib.mtpt_destroy.argtypes = [vp]
+    lib.mtpt_set_stream.argtypes = [vp, vp]
+    lib.mtpt_set_particles.argtypes = [vp, ctypes.c_int64, vp, vp]
+    lib.mtpt_set_particles_device.argtypes = [vp, ctypes.c_int64, vp, vp]
+    lib.mtpt_step.argtypes = [vp, ctypes.c_int64]
+    lib.mtpt_step_ex.argtypes = [vp, ctypes.c_int64, ctypes.c_int32]
+    for name in ("mtpt_get_masses", "mtpt_get_masses_device", "mtpt_get_positions",
+                 "mtpt_get_positions_device", "mtpt_get_row_sums"):
+        getattr(lib, name).argtypes = [vp, vp]
+    lib.mtpt_get_pairs.argtypes = [vp, ctypes.c_int64, P(ctypes.c_int64), vp, vp]
+    lib.mtpt_get_info.argtypes = [vp, P(_Info)]
+    lib.mtpt_set_step.argtypes = [vp, ctypes.c_uint64]
+    lib.mtpt_sync.argtypes = [vp]
+    lib.mtpt_timing_enable.argtypes = [vp, ctypes.c_int32]
+    lib.mtpt_timing_read.argtypes = [vp, ctypes.c_int32, P(_KernelStat), P(ctypes.c_int32)]
+    lib.mtpt_timing_reset.argtypes = [vp]
+    lib.mtpt_status_string.argtypes = [ctypes.c_int]
+    lib.mtpt_status_string.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "mtpt_status_string":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().mtpt_status_string(code).decode()
+
+
+def _check(code: int, where: str):
+    if code != MTPT_OK:
+        raise MtptError(code, where)
+
+
+def _host_f64(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _dev_ptr(t, dtype_name: str, numel: int) -> int:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}" or t.numel() != numel:
+        raise ValueError(f"expected {numel} elements of {dtype_name}")
+    return t.data_ptr()
+
+
+def _torch_stream() -> int:
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# --- the C entry points ------------------------------------------------------
+
+def mtpt_create(params: Params) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    cp = params.c()
+    _check(load().mtpt_create(ctypes.byref(cp), ctypes.byref(h)), "mtpt_create")
+    return h
+
+
+def mtpt_destroy(h) -> None:
+    _check(load().mtpt_destroy(h), "mtpt_destroy")
+
+
+def mtpt_set_stream(h, stream: int | None) -> None:
+    _check(load().mtpt_set_stream(h, ctypes.c_void_p(stream or 0)), "mtpt_set_stream")
+
+
+def mtpt_set_particles(h, dim: int, pos, mass) -> None:
+    mass = np.ascontiguousarray(np.asarray(mass, dtype=np.float64)).ravel()
+    n = mass.size
+    pos = _host_f64(pos, (dim, n))
+    _check(load().mtpt_set_particles(h, n, pos.ctypes.data, mass.ctypes.data),
+           "mtpt_set_particles")
+
+
+def mtpt_set_particles_device(h, dim: int, pos, mass) -> None:
+    n = mass.numel()
+    mtpt_set_stream(h, _torch_stream())
+    _check(load().mtpt_set_particles_device(h, n, _dev_ptr(pos, "float64", dim * n),
+                                            _dev_ptr(mass, "float64", n)),
+           "mtpt_set_particles_device")
+
+
+def mtpt_step(h, nsteps: int) -> None:
+    _check(load().mtpt_step(h, nsteps), "mtpt_step")
+
+
+def mtpt_step_ex(h, nsteps: int, flags: int) -> None:
+    _check(load().mtpt_step_ex(h, nsteps, flags), "mtpt_step_ex")
+
+
+def mtpt_get_info(h) -> dict:
+    info = _Info()
+    _check(load().mtpt_get_info(h, ctypes.byref(info)), "mtpt_get_info")
+    return {"n": info.n, "step": info.step, "pair_count": info.pair_count,
+            "D_RW": info.D_RW, "D_MT": info.D_MT, "sigma": info.sigma, "h2": info.h2,
+            "psi": info.psi, "psi2": info.psi2, "kernel_norm": info.kernel_norm,
+            "cells": tuple(info.cells), "cell_width": tuple(info.cell_width)}
+
+
+def mtpt_get_masses(h, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.float64)
+    _check(load().mtpt_get_masses(h, out.ctypes.data), "mtpt_get_masses")
+    return out
+
+
+def mtpt_get_masses_device(h, out) -> None:
+    _check(load().mtpt_get_masses_device(h, _dev_ptr(out, "float64", out.numel())),
+           "mtpt_get_masses_device")
+
+
+def mtpt_get_positions(h, dim: int, n: int) -> np.ndarray:
+    out = np.empty((dim, n), dtype=np.float64)
+    _check(load().mtpt_get_positions(h, out.ctypes.data), "mtpt_get_positions")
+    return out
+
+
+def mtpt_get_positions_device(h, out) -> None:
+    _check(load().mtpt_get_positions_device(h, _dev_ptr(out, "float64", out.numel())),
+           "mtpt_get_positions_device")
+
+
+def mtpt_get_row_sums(h, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.float64)
+    _check(load().mtpt_get_row_sums(h, out.ctypes.data), "mtpt_get_row_sums")
+    return out
+
+
+def mtpt_get_pairs(h, cap: int):
+    """Ordered neighbour pairs of the current positions as input-order index
+    arrays (i, j), sorted by (i, j)."""
+    pi = np.empty(max(cap, 1), dtype=np.uint32)
+    pj = np.empty(max(cap, 1), dtype=np.uint32)
+    count = ctypes.c_int64()
+    rc = load().mtpt_get_pairs(h, cap, ctypes.byref(count), pi.ctypes.data, pj.ctypes.data)
+    _check(rc, "mtpt_get_pairs")
+    m = count.value
+    i, j = pi[:m].astype(np.int64), pj[:m].astype(np.int64)
+    order = np.lexsort((j, i))
+    return i[order], j[order]
+
+
+def mtpt_set_step(h, step: int) -> None:
+    _check(load().mtpt_set_step(h, step), "mtpt_set_step")
+
+
+def mtpt_sync(h) -> None:
+    _check(load().mtpt_sync(h), "mtpt_sync")
+
+
+def mtpt_timing_enable(h, on: bool) -> None:
+    _check(load().mtpt_timing_enable(h, 1 if on else 0), "mtpt_timing_enable")
+
+
+def mtpt_timing_read(h) -> dict:
+    """{kernel name: (launches, total milliseconds)} since the last reset."""
+    cap = 64
+    arr = (_KernelStat * cap)()
+    count = ctypes.c_int32()
+    _check(load().mtpt_timing_read(h, cap, arr, ctypes.byref(count)), "mtpt_timing_read")
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms))
+            for k in range(min(cap, count.value))}
+
+
+def mtpt_timing_reset(h) -> None:
+    _check(load().mtpt_timing_reset(h), "mtpt_timing_reset")
+
+
+def mtpt_status_string(code: int) -> str:
+    return status_string(code)
+
+
+class Simulation:
+    """Owning wrapper over one handle (host numpy in, host numpy out)."""
+
+    def __init__(self, params: Params, pos=None, mass=None):
+        self.params = params
+        self.h = mtpt_create(params)
+        self.n = 0
+        if pos is not None:
+            self.set_particles(pos, mass)
+
+    def set_particles(self, pos, mass):
+        mass = np.asarray(mass, dtype=np.float64).ravel()
+        mtpt_set_particles(self.h, self.params.dim, pos, mass)
+        self.n = mass.size
+
+    def step(self, nsteps: int = 1, flags: int = MTPT_DO_WALK | MTPT_DO_TRANSFER):
+        mtpt_step_ex(self.h, nsteps, flags)
+
+    def masses(self) -> np.ndarray:
+        return mtpt_get_masses(self.h, self.n)
+
+    def positions(self) -> np.ndarray:
+        return mtpt_get_positions(self.h, self.params.dim, self.n)
+
+    def row_sums(self) -> np.ndarray:
+        return mtpt_get_row_sums(self.h, self.n)
+
+    def pairs(self, cap: int | None = None):
+        if cap is None:
+            cap = max(1024, 64 * self.n)
+        return mtpt_get_pairs(self.h, cap)
+
+    def info(self) -> dict:
+        return mtpt_get_info(self.h)
+
+    def set_step(self, step: int):
+        mtpt_set_step(self.h, step)
+
+    def close(self):
+        if self.h is not None:
+            mtpt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,88 @@
+"""The C-ABI library loads and exports every entry point that include/mtpt.h
+declares; host-side argument checks answer without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2204_03756_gb300 import build as cuda_build
+from paper_2204_03756_gb300 import mtpt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "mtpt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mtpt_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cuda_build.build()
+    return mtpt.load()
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols()
+    for name in ("mtpt_create", "mtpt_set_particles", "mtpt_step", "mtpt_get_masses",
+                 "mtpt_destroy"):
+        assert name in syms
+    assert set(syms) == set(mtpt.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_parameter_validation_without_gpu(lib):
+    good = dict(dim=2, D=1.0, kappa=0.5, dt=0.1, lo=(0, 0), hi=(10, 10))
+    h = mtpt.mtpt_create(mtpt.Params(**good))
+    mtpt.mtpt_destroy(h)
+    bad = [dict(dim=0), dict(dim=4), dict(kappa=1.5), dict(dt=0.0), dict(D=-1.0),
+           dict(lo=(5, 0), hi=(1, 10)), dict(beta=0.0), dict(lam=0.0), dict(precision=7),
+           dict(D=float("nan"))]
+    for b in bad:
+        kw = dict(good)
+        kw.update(b)
+        with pytest.raises(mtpt.MtptError) as e:
+            mtpt.mtpt_create(mtpt.Params(**kw))
+        assert e.value.code == mtpt.MTPT_ERR_INVALID_ARG
+    assert lib.mtpt_create(None, None) == mtpt.MTPT_ERR_INVALID_ARG
+    assert lib.mtpt_destroy(None) == mtpt.MTPT_OK
+    assert lib.mtpt_step(None, 1) == mtpt.MTPT_ERR_INVALID_ARG
+
+
+def test_calls_before_particles_are_rejected(lib):
+    h = mtpt.mtpt_create(mtpt.Params(dim=2, lo=(0, 0), hi=(10, 10)))
+    try:
+        with pytest.raises(mtpt.MtptError) as e:
+            mtpt.mtpt_step(h, 1)
+        assert e.value.code == mtpt.MTPT_ERR_STATE
+        assert lib.mtpt_step(h, -1) == mtpt.MTPT_ERR_INVALID_ARG
+    finally:
+        mtpt.mtpt_destroy(h)
+
+
+def test_out_of_domain_host_input_is_rejected_before_any_device_work(lib):
+    import numpy as np
+    h = mtpt.mtpt_create(mtpt.Params(dim=2, lo=(0, 0), hi=(10, 10)))
+    try:
+        pos = np.array([[1.0, 11.0], [1.0, 1.0]])
+        with pytest.raises(mtpt.MtptError) as e:
+            mtpt.mtpt_set_particles(h, 2, pos, [1.0, 1.0])
+        assert e.value.code == mtpt.MTPT_ERR_OUT_OF_DOMAIN
+        pos = np.array([[1.0, np.nan], [1.0, 1.0]])
+        with pytest.raises(mtpt.MtptError):
+            mtpt.mtpt_set_particles(h, 2, pos, [1.0, 1.0])
+    finally:
+        mtpt.mtpt_destroy(h)
+
+
+def test_status_strings(lib):
+    for code in range(7):
+        assert mtpt.mtpt_status_string(code)
+    assert mtpt.mtpt_status_string(99) == "unknown status"

@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: positions of the random walk and neighbour pair sets bit-exact; masses
+within 1e-12 (binary64 form) or 1e-5 (precision form) of max |M| of the
+oracle; pair counts exact.  Sizes span many cells, several thread blocks and
+ragged tails."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2204_03756_gb300 import mtpt, workloads
+
+from gpu_helpers import TOL, oracle_params, params_of, rel_err, run_both
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [mtpt.MTPT_FP64, mtpt.MTPT_FP32W]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2204_03756_gb300 import build
+    build.build()
+    mtpt.load()
+
+
+def test_walk_is_bit_exact_with_the_oracle():
+    w = workloads.get("heaviside_2d", 10_001)
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w, kappa=1.0, D=2.0)          # pure walk, no transfer
+    g, r = run_both(p, pos, mass, 7)
+    assert np.array_equal(g["pos"], r["pos"])
+    assert np.array_equal(g["mass"], mass)
+    assert g["info"]["pair_count"] == 0 and g["info"]["step"] == 7
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_walk_with_walls_bit_exact_3d(dim):
+    rng = np.random.default_rng(dim)
+    n = 3000
+    lo, hi = (0.0,) * dim, (3.0,) * dim          # small box: many reflections
+    pos = rng.uniform(0, 3.0, size=(dim, n))
+    pos[:, :10] = 0.0
+    pos[:, 10:20] = 3.0
+    p = mtpt.Params(dim=dim, D=1.0, kappa=0.5, dt=0.2, lo=lo, hi=hi, seed=17)
+    g, r = run_both(p, pos, np.zeros(n), 5)
+    assert np.array_equal(g["pos"], r["pos"])
+
+
+def _pairs_gpu(p, pos):
+    with mtpt.Simulation(p, pos, np.zeros(pos.shape[1])) as sim:
+        return sim.pairs()
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("dim,n,L", [(1, 1999, 400.0), (2, 2000, 30.0), (3, 1777, 9.0)])
+def test_pair_sets_bit_exact_vs_brute_force(form, dim, n, L):
+    rng = np.random.default_rng(100 + dim)
+    pos = rng.uniform(0, L, size=(dim, n))
+    pos[:, :40] = np.round(pos[:, :40])          # lattice points and duplicates
+    pos[0, 40:60] = 0.0                          # on the wall
+    pos[:, 60:70] = pos[:, 70:80]                # coincident pairs
+    p = mtpt.Params(dim=dim, D=1.0, kappa=0.5, dt=0.1, lo=(0.0,) * dim, hi=(L,) * dim,
+                    seed=1, precision=form)
+    gi, gj = _pairs_gpu(p, pos)
+    psi2 = O.derived(oracle_params(p))["psi2"]
+    bi, bj = O.pairs(pos, psi2, "brute")
+    assert np.array_equal(gi, bi) and np.array_equal(gj, bj)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pair_sets_on_exact_ties(form):
+    # D_MT dt = 0.25 makes psi = lambda exactly; lambda = 1.25, psi^2 = 1.5625 and
+    # 0.75^2 + 1^2 = 1.5625: these pairs sit exactly on the cutoff.
+    p = mtpt.Params(dim=2, D=2.5, kappa=0.0, dt=0.1, lam=1.25, lo=(0, 0), hi=(20, 20),
+                    seed=3, precision=form)
+    d = O.derived(oracle_params(p))
+    assert d["psi2"] == 1.5625
+    base = np.array([[2.0, 2.75, 10.0, 10.75, 10.0 + 1.25, 15.0, 15.0],
+                     [2.0, 3.0, 10.0, 11.0, 10.0, 15.0, np.nextafter(16.25, 20.0)]])
+    gi, gj = _pairs_gpu(p, base)
+    bi, bj = O.pairs(base, d["psi2"], "brute")
+    assert np.array_equal(gi, bi) and np.array_equal(gj, bj)
+    got = set(zip(gi.tolist(), gj.tolist()))
+    assert (0, 1) in got and (2, 3) in got and (2, 4) in got and (5, 6) not in got
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pair_sets_large_vs_kdtree(form):
+    w = workloads.get("heaviside_3d", 60_000)
+    pos, _ = workloads.initial_state(w)
+    p = params_of(w, precision=form)
+    gi, gj = _pairs_gpu(p, pos)
+    ki, kj = O.pairs(pos, O.derived(oracle_params(p))["psi2"], "kdtree")
+    assert np.array_equal(gi, ki) and np.array_equal(gj, kj)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_row_sums_match_the_oracle(form):
+    w = workloads.get("heaviside_2d", 5003)
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w, precision=form, kappa=0.0)  # transfer only: positions fixed
+    with mtpt.Simulation(p, pos, mass) as sim:
+        sim.step(1)
+        rs = sim.row_sums()
+        m = sim.masses()
+    m_ref, rs_ref, cs_ref, _ = O.mass_transfer(oracle_params(p), pos, mass)
+    tol = 1e-13 if form == mtpt.MTPT_FP64 else 3e-6
+    assert rel_err(rs, rs_ref) <= tol
+    assert rel_err(m, m_ref) <= TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_heaviside_2d_full_config_masses(form):
+    """The 2-d plain-diffusion workload in full: N = 10,000, 100 steps."""
+    w = workloads.get("heaviside_2d")
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w, precision=form)
+    g, r = run_both(p, pos, mass, w.steps)
+    assert np.array_equal(g["pos"], r["pos"])
+    assert g["info"]["pair_count"] == r["pairs"]
+    err = rel_err(g["mass"], r["mass"])
+    assert err <= TOL[form], err
+    drift = abs(g["mass"].sum() - mass.sum()) / mass.sum()
+    assert drift < 1e-12, drift
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_heaviside_3d_scaled_masses(form):
+    w = workloads.get("heaviside_3d", 20_000)
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w, precision=form)
+    g, r = run_both(p, pos, mass, 20)
+    assert np.array_equal(g["pos"], r["pos"])
+    assert g["info"]["pair_count"] == r["pairs"]
+    assert rel_err(g["mass"], r["mass"]) <= TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_gaussian_and_uniform_mass_workloads_scaled(form):
+    for name, n, steps in (("gaussian_2d", 40_000, 10), ("uniform_mass_2d", 30_000, 10)):
+        w = workloads.get(name, n)
+        pos, mass = workloads.initial_state(w)
+        p = params_of(w, precision=form)
+        g, r = run_both(p, pos, mass, steps)
+        assert np.array_equal(g["pos"], r["pos"])
+        assert rel_err(g["mass"], r["mass"]) <= TOL[form], name
+
+
+def test_one_dimensional_run():
+    rng = np.random.default_rng(9)
+    n = 4097
+    pos = rng.uniform(0, 500.0, size=(1, n))
+    mass = (pos[0] < 250).astype(float)
+    for form in FORMS:
+        p = mtpt.Params(dim=1, D=1.0, kappa=0.5, dt=0.1, lo=(0.0,), hi=(500.0,), seed=5,
+                        precision=form)
+        g, r = run_both(p, pos, mass, 30)
+        assert np.array_equal(g["pos"], r["pos"])
+        assert rel_err(g["mass"], r["mass"]) <= TOL[form]
+
+
+def test_uniform_masses_stay_uniform_bit_exactly():
+    w = workloads.get("heaviside_2d", 7000)
+    pos, _ = workloads.initial_state(w)
+    mass = np.full(w.n, 0.375)
+    for form in FORMS:
+        with mtpt.Simulation(params_of(w, precision=form), pos, mass) as sim:
+            sim.step(5)
+            assert np.array_equal(sim.masses(), mass)
+
+
+def test_transfer_only_keeps_positions_and_walk_only_keeps_masses():
+    w = workloads.get("heaviside_2d", 3000)
+    pos, mass = workloads.initial_state(w)
+    with mtpt.Simulation(params_of(w), pos, mass) as sim:
+        sim.step(3, flags=mtpt.MTPT_DO_TRANSFER)
+        assert np.array_equal(sim.positions(), pos)
+        assert sim.info()["step"] == 0
+        m3 = sim.masses()
+        sim.step(2, flags=mtpt.MTPT_DO_WALK)
+        assert np.array_equal(sim.masses(), m3)
+        assert sim.info()["step"] == 2
+
+
+def test_runs_are_bit_reproducible():
+    w = workloads.get("gaussian_2d", 50_000)
+    pos, mass = workloads.initial_state(w)
+    outs = []
+    for _ in range(2):
+        with mtpt.Simulation(params_of(w), pos, mass) as sim:
+            sim.step(6)
+            outs.append((sim.masses(), sim.positions()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_checkpoint_resume_is_bit_identical():
+    w = workloads.get("heaviside_2d", 6000)
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w)
+    with mtpt.Simulation(p, pos, mass) as sim:
+        sim.step(10)
+        full_m, full_x = sim.masses(), sim.positions()
+    with mtpt.Simulation(p, pos, mass) as sim:
+        sim.step(4)
+        mid_m, mid_x = sim.masses(), sim.positions()
+    with mtpt.Simulation(p, mid_x, mid_m) as sim:
+        sim.set_step(4)
+        sim.step(6)
+        assert np.array_equal(sim.masses(), full_m)
+        assert np.array_equal(sim.positions(), full_x)
+
+
+def test_edge_cases_empty_single_and_one_cell():
+    p = mtpt.Params(dim=2, D=1.0, kappa=0.5, dt=0.1, lo=(0, 0), hi=(10, 10), seed=2)
+    with mtpt.Simulation(p, np.zeros((2, 0)), np.zeros(0)) as sim:
+        sim.step(3)
+        assert sim.masses().size == 0
+        assert sim.info()["pair_count"] == 0
+    with mtpt.Simulation(p, np.array([[5.0], [5.0]]), np.array([2.0])) as sim:
+        sim.step(3)
+        assert np.array_equal(sim.masses(), [2.0])
+    # every particle in one cell (box smaller than the cutoff): all pairs
+    rng = np.random.default_rng(4)
+    n = 700
+    q = mtpt.Params(dim=2, D=1.0, kappa=0.5, dt=0.1, lo=(0, 0), hi=(0.9, 0.9), seed=2)
+    pos = rng.uniform(0, 0.9, size=(2, n))
+    mass = rng.uniform(0, 1, n)
+    with mtpt.Simulation(q, pos, mass) as sim:
+        assert sim.info()["cells"][:2] == (1, 1)
+    g, r = run_both(q, pos, mass, 3, method="brute")
+    assert np.array_equal(g["pos"], r["pos"])
+    assert g["info"]["pair_count"] == r["pairs"] == 3 * n * (n - 1)
+    assert rel_err(g["mass"], r["mass"]) <= 1e-12
+
+
+def test_ragged_sizes_around_block_boundaries():
+    for n in (1, 2, 255, 256, 257, 511, 513):
+        ww = workloads.get("heaviside_2d", n)
+        pos, mass = workloads.initial_state(ww)
+        p = params_of(ww)
+        g, r = run_both(p, pos, mass, 4, method="brute")
+        assert np.array_equal(g["pos"], r["pos"])
+        assert rel_err(g["mass"], r["mass"]) <= 1e-12
+
+
+def test_device_buffers_through_torch():
+    import torch
+    w = workloads.get("heaviside_2d", 9000)
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w)
+    h = mtpt.mtpt_create(p)
+    try:
+        pt = torch.from_numpy(pos.copy()).cuda()
+        mt = torch.from_numpy(mass.copy()).cuda()
+        mtpt.mtpt_set_particles_device(h, 2, pt, mt)
+        mtpt.mtpt_step(h, 5)
+        out_m = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        out_x = torch.empty(2 * w.n, dtype=torch.float64, device="cuda")
+        mtpt.mtpt_get_masses_device(h, out_m)
+        mtpt.mtpt_get_positions_device(h, out_x)
+        mtpt.mtpt_sync(h)
+        torch.cuda.synchronize()
+        xr, mr, _ = O.run(oracle_params(p), pos, mass, 5)
+        assert np.array_equal(out_x.cpu().numpy().reshape(2, -1), xr)
+        assert rel_err(out_m.cpu().numpy(), mr) <= 1e-12
+        # a device-side domain violation is latched and reported at the next sync
+        bad = pt.clone()
+        bad[0, 0] = 1e9
+        mtpt.mtpt_set_particles_device(h, 2, bad, mt)
+        with pytest.raises(mtpt.MtptError) as e:
+            mtpt.mtpt_sync(h)
+        assert e.value.code == mtpt.MTPT_ERR_OUT_OF_DOMAIN
+    finally:
+        mtpt.mtpt_destroy(h)
