@@ -298,12 +298,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=200_000)
+    ap.add_argument("--n", type=int, default=None,
+                    help="scale the workload to n particles at the same density "
+                         "(profiling runs; the default is the workload's own size)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
     world, rank, local = _dist()
-    w = workloads.get(args.workload)
+    w = workloads.get(args.workload, args.n)
 
     if args.impl == "reference":
         if rank != 0:
