@@ -48,7 +48,8 @@ typedef enum mtpt_status {
     MTPT_ERR_CUDA = 3,            /* a CUDA runtime call failed */
     MTPT_ERR_NO_MEMORY = 4,       /* device or host allocation failed */
     MTPT_ERR_STATE = 5,           /* call not valid in the handle's state */
-    MTPT_ERR_CAPACITY = 6         /* a caller buffer is too small */
+    MTPT_ERR_CAPACITY = 6,        /* a caller buffer is too small */
+    MTPT_ERR_TOO_LARGE = 7        /* problem exceeds mtpt_step_noalloc's fixed scratch */
 } mtpt_status;
 
 /* Precision forms of the pair arithmetic. */
@@ -196,6 +197,46 @@ int mtpt_timing_read(mtpt_handle* h, int32_t cap, mtpt_kernel_stat* out, int32_t
 
 /* Clear the per-kernel sums. */
 int mtpt_timing_reset(mtpt_handle* h);
+
+/* One full time step (walk, then mass transfer) on caller-owned DEVICE
+ * buffers, without allocating any memory.
+ *
+ * This entry point has no counterpart in the paper; it exists for callers
+ * that cannot allocate device memory when they step the particles: code
+ * whose GPU memory is owned entirely by another allocator (a framework's
+ * caching allocator, or a host application that reserves the whole device up
+ * front), where a cudaMalloc from this library could fail or fragment that
+ * pool, and time-critical loops that cannot pay for cudaMalloc/cudaFree
+ * (cudaFree synchronises the device).  It creates no handle and calls no
+ * cudaMalloc, cudaFree or other allocating routine: its working memory is a
+ * fixed file-scope device array of MTPT_NOALLOC_SCRATCH_BYTES (9 MiB) that
+ * every GPU which loads this library holds until the process exits.
+ *
+ * pos_dev (dim x n SoA float64) and mass_dev (n float64) hold the state in
+ * the caller's order and are updated in place; particle i is id i for the
+ * walk's generator and `step` is the generator's step counter, so the result
+ * equals mtpt_set_particles + mtpt_set_step(step) + mtpt_step(1) on the same
+ * state.  params is read as in mtpt_create.  Work is enqueued on `stream`
+ * (a cudaStream_t; NULL = legacy default stream) and the call does not wait
+ * for it; positions are not range-checked on the device (pass particles
+ * inside the box).
+ *
+ * Limits: n <= MTPT_NOALLOC_MAX_PARTICLES (65,536); larger n returns
+ * MTPT_ERR_TOO_LARGE before any work is enqueued.
+ *
+ * Shared scratch: every call uses the same array, which keeps the last
+ * call's contents (each call clears what must start at zero).  Calls whose
+ * GPU work overlaps -- on different streams, or from different threads
+ * without ordering -- race on that array and give wrong results; order them
+ * on one stream.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call on a device before any stream capture begins. */
+#define MTPT_NOALLOC_MAX_PARTICLES 65536
+#define MTPT_NOALLOC_SCRATCH_BYTES (9u << 20)
+int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step, double* pos_dev,
+                      double* mass_dev, void* stream);
 
 /* Human-readable text of a status code (static storage). */
 const char* mtpt_status_string(int status);

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -734,8 +735,142 @@ const char* mtpt_status_string(int status) {
         case MTPT_ERR_NO_MEMORY: return "allocation failed";
         case MTPT_ERR_STATE: return "call not valid in the handle's state";
         case MTPT_ERR_CAPACITY: return "output buffer too small";
+        case MTPT_ERR_TOO_LARGE: return "problem larger than the fixed no-allocation scratch";
         default: return "unknown status";
     }
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mtpt_step_noalloc: one time step with all working memory in a fixed
+// file-scope device array instead of cudaMalloc'ed buffers, for callers that
+// must not allocate.  It runs the same kernels as mtpt_step through a handle
+// that lives on the host stack and whose buffers point into the array.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MTPT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+std::once_flag g_noalloc_once[kNoallocMaxDevices];
+cudaError_t g_noalloc_err[kNoallocMaxDevices] = {};
+
+// The array's device address on the current device, looked up once per
+// device.  In host code `g_noalloc_scratch` names a host-side stand-in, never
+// a device address, so kernels only ever receive the looked-up pointer.
+int noalloc_scratch(void** out) {
+    int dev = -1;
+    MTPT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return MTPT_ERR_CUDA;
+    std::call_once(g_noalloc_once[dev], [dev]() {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) (void)cudaGetLastError();
+        g_noalloc_err[dev] = e;
+        g_noalloc_addr[dev] = (e == cudaSuccess) ? p : nullptr;
+    });
+    if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev]) return MTPT_ERR_CUDA;
+    *out = g_noalloc_addr[dev];
+    return MTPT_OK;
+}
+
+// Bump carving of the scratch array into 256-byte-aligned pieces.
+struct Carver {
+    unsigned char* base;
+    size_t used = 0;
+    bool overflow = false;
+    template <typename T>
+    T* take(size_t count) {
+        const size_t off = (used + 255) & ~size_t(255);
+        const size_t bytes = count * sizeof(T);
+        if (off + bytes > size_t(MTPT_NOALLOC_SCRATCH_BYTES)) {
+            overflow = true;
+            return nullptr;
+        }
+        used = off + bytes;
+        return reinterpret_cast<T*>(base + off);
+    }
+};
+
+}  // namespace
+
+extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step,
+                                 double* pos_dev, double* mass_dev, void* stream) {
+    MTPT_TRY(validate_params(params));
+    if (n < 0 || (n > 0 && (!pos_dev || !mass_dev))) return MTPT_ERR_INVALID_ARG;
+    if (n > MTPT_NOALLOC_MAX_PARTICLES) return MTPT_ERR_TOO_LARGE;
+    void* scratch = nullptr;
+    MTPT_TRY(noalloc_scratch(&scratch));
+    if (n == 0) return MTPT_OK;
+
+    mtpt_handle h;                       // host-side bookkeeping only
+    h.prm = *params;
+    h.stream = static_cast<cudaStream_t>(stream);
+    derive(&h);
+    h.n = n;
+    h.cap = n;
+    MTPT_TRY(setup_grid(&h));
+    const int d = h.prm.dim;
+    const size_t cells_pad = size_t(h.n_cells_pad);
+
+    Carver cv{static_cast<unsigned char*>(scratch)};
+    double* mass_in = cv.take<double>(size_t(n));
+    double* pos_sorted = cv.take<double>(size_t(d) * size_t(n));
+    double* mass_sorted = cv.take<double>(size_t(n));
+    uint32_t* id_in = cv.take<uint32_t>(size_t(n));
+    uint32_t* id_sorted = cv.take<uint32_t>(size_t(n));
+    h.key.p = cv.take<uint32_t>(size_t(n));
+    h.perm.p = cv.take<uint32_t>(size_t(n));
+    h.cell.p = cv.take<uint32_t>(size_t(n));
+    h.xl.p = cv.take<float>(size_t(d) * size_t(n));
+    if (h.prm.precision == MTPT_FP64) {
+        h.r64.p = cv.take<double>(size_t(n));
+    } else {
+        h.r32.p = cv.take<float>(size_t(n));
+        h.msplit.p = cv.take<float2>(size_t(n));
+    }
+    h.count.p = cv.take<uint32_t>(cells_pad);
+    h.start.p = cv.take<uint32_t>(cells_pad);
+    h.tile_sums.p = cv.take<uint32_t>(cells_pad / kScanTile);
+    h.exp_table.p = cv.take<double>(64);
+    h.status.p = cv.take<uint32_t>(1);
+    h.pair_counter.p = cv.take<unsigned long long>(1);
+    if (cv.overflow) return MTPT_ERR_TOO_LARGE;
+
+    // The handle's buffer pairs: index 0 is the caller's state (positions are
+    // walked in place; masses are read from a scratch copy), index 1 the
+    // cell-ordered copy.  None of these pointers is owned by `h`.
+    h.pos[0].p = pos_dev;
+    h.pos[1].p = pos_sorted;
+    h.mass[0].p = mass_in;
+    h.mass[1].p = mass_sorted;
+    h.id[0].p = id_in;
+    h.id[1].p = id_sorted;
+    h.cur = 0;
+    h.step = step;
+
+    cudaStream_t st = h.stream;
+    // what must start at zero: cell counts, status word, pair counter
+    if (h.transfer_enabled)
+        MTPT_CUDA_TRY(cudaMemsetAsync(h.count.p, 0, cells_pad * sizeof(uint32_t), st));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h.status.p, 0, sizeof(uint32_t), st));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h.pair_counter.p, 0, sizeof(unsigned long long), st));
+    static double table[64];
+    static std::once_flag table_once;
+    std::call_once(table_once, []() {
+        for (int j = 0; j < 64; ++j) table[j] = double(exp2l(-static_cast<long double>(j) / 64.0L));
+    });
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h.exp_table.p, table, sizeof(table), cudaMemcpyHostToDevice, st));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(mass_in, mass_dev, size_t(n) * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, st));
+    k_iota<<<grid_for(n), kBlock, 0, st>>>(int(n), id_in);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    MTPT_TRY(dispatch_step(&h, MTPT_DO_WALK | MTPT_DO_TRANSFER));
+    // masses back to the caller's order; positions are already there
+    k_unpermute<double><<<grid_for(n), kBlock, 0, st>>>(int(n), h.cap, 1, h.id[h.cur].p,
+                                                        h.mass[h.cur].p, 1.0, mass_dev);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
+}

@@ -23,6 +23,8 @@ MTPT_ERR_CUDA = 3
 MTPT_ERR_NO_MEMORY = 4
 MTPT_ERR_STATE = 5
 MTPT_ERR_CAPACITY = 6
+MTPT_ERR_TOO_LARGE = 7
+NOALLOC_MAX_PARTICLES = 65536
 
 MTPT_FP64 = 0
 MTPT_FP32W = 1
@@ -35,7 +37,8 @@ EXPORTED = [
     "mtpt_set_particles_device", "mtpt_step", "mtpt_step_ex", "mtpt_get_masses",
     "mtpt_get_masses_device", "mtpt_get_positions", "mtpt_get_positions_device",
     "mtpt_get_row_sums", "mtpt_get_pairs", "mtpt_get_info", "mtpt_set_step", "mtpt_sync",
-    "mtpt_timing_enable", "mtpt_timing_read", "mtpt_timing_reset", "mtpt_status_string",
+    "mtpt_timing_enable", "mtpt_timing_read", "mtpt_timing_reset", "mtpt_step_noalloc",
+    "mtpt_status_string",
 ]
 
 
@@ -129,6 +132,7 @@ def load():
     lib.mtpt_timing_enable.argtypes = [vp, ctypes.c_int32]
     lib.mtpt_timing_read.argtypes = [vp, ctypes.c_int32, P(_KernelStat), P(ctypes.c_int32)]
     lib.mtpt_timing_reset.argtypes = [vp]
+    lib.mtpt_step_noalloc.argtypes = [P(_Params), ctypes.c_int64, ctypes.c_uint64, vp, vp, vp]
     lib.mtpt_status_string.argtypes = [ctypes.c_int]
     lib.mtpt_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -284,6 +288,19 @@ def mtpt_timing_read(h) -> dict:
 
 def mtpt_timing_reset(h) -> None:
     _check(load().mtpt_timing_reset(h), "mtpt_timing_reset")
+
+
+def mtpt_step_noalloc(params: Params, step: int, pos, mass) -> None:
+    """One time step on torch CUDA buffers (pos: dim*n float64 SoA, mass: n
+    float64, updated in place) with no device allocation, for callers whose
+    device memory is owned by another allocator.  Enqueued on torch's current
+    stream; n is limited to NOALLOC_MAX_PARTICLES."""
+    n = mass.numel()
+    cp = params.c()
+    _check(load().mtpt_step_noalloc(ctypes.byref(cp), n, step,
+                                    _dev_ptr(pos, "float64", params.dim * n),
+                                    _dev_ptr(mass, "float64", n), _torch_stream()),
+           "mtpt_step_noalloc")
 
 
 def mtpt_status_string(code: int) -> str:
