@@ -293,7 +293,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
-    ap.add_argument("--forms", default="fp64,fp32w",
+    ap.add_argument("--forms", default="fp32w,fp64",
                     help="comma list; the first is the headline value")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -1,11 +1,19 @@
 // kernels.cuh -- CUDA kernels of one MTPT time step (Sec. 3) for sm_103a.
 //
+// GB300 issues every binary64 instruction (arithmetic, compares, f32<->f64
+// conversions) at about 1/70 of the binary32 rate, so the kernels keep
+// binary64 to the operations whose results must match the binary64 method
+// bit for bit (the walk's x + sigma xi, and the pair test inside a narrow
+// band around the cutoff) and do everything else in binary32 and integer
+// arithmetic.
+//
 // Data layout (structure of arrays, `stride` = capacity >= n):
 //   pos[a * stride + s]  binary64 coordinates, particles in cell order
 //   mass[s], id[s]       binary64 mass, uint32 input index (keys the walk)
 //   cell[s]              linear cell index of particle s
-//   xl[a * stride + s]   binary32 offset of the particle from its cell's
-//                        lower corner (the pair loop's prefilter operand)
+//   rec[s]               float4: binary32 offsets of the particle from its
+//                        cell's lower corner (x, y, z), and in .w the
+//                        precision form's row sum r_s once pass 1 has run
 //   start[c]             first particle of cell c (exclusive prefix sum)
 // Cells are row-major (x fastest), so the three cells (cx-1..cx+1) of one
 // neighbour row are one contiguous particle range.
@@ -25,6 +33,7 @@ constexpr int kScanTile = 4 * kScanThreads;   // cells per scan block
 
 struct Box {
     double lo[3], hi[3];
+    long long lo_key[3], hi_key[3];   // order-preserving integer images of lo, hi
 };
 
 struct Grid {
@@ -33,6 +42,10 @@ struct Grid {
     double w[3];       // cell width per axis, >= psi
     double inv_w[3];   // 1 / w
     float wf[3];       // w rounded to binary32
+    float lo_f[3];     // lo rounded to binary32 (binary32 cell index)
+    float inv_w_f[3];  // 1 / w in binary32
+    int cell_f32;      // 1: cell index from binary32 arithmetic (margin in w), 0: binary64
+    int corner_off[3]; // offset of axis a's corner table in `corners`
 };
 
 struct PairParams {
@@ -44,6 +57,57 @@ struct PairParams {
     double beta;
     ExpNegConsts ec;
 };
+
+// ---------------------------------------------------------------------------
+// Integer helpers for binary64 values.
+// ---------------------------------------------------------------------------
+
+// Order-preserving image of a binary64 value in int64: for non-NaN x, y,
+// key(x) < key(y) implies x <= y (-0 sorts below +0).
+__device__ __forceinline__ long long order_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// x split as hi + lo with hi = x truncated to binary32 (integer operations
+// only: no binary64 instruction) and lo the binary32 nearest to the exact
+// remainder x - hi (|lo| < 2^-23 |x|).  Values below 2^-126 in magnitude give
+// hi = lo = 0; |x| must be below 2^127.
+__device__ __forceinline__ void split_double(double x, float* hi, float* lo) {
+    const uint32_t whi = uint32_t(__double2hiint(x));
+    const uint32_t wlo = uint32_t(__double2loint(x));
+    const int e = int((whi >> 20) & 0x7ffu);
+    const uint32_t sign = whi & 0x80000000u;
+    if (e < 949) {   // |x| < 2^-74: residual below binary32's normal range
+        *hi = e < 897 ? __uint_as_float(sign)
+                      : __uint_as_float(sign | (uint32_t(e - 896) << 23) | ((whi & 0xfffffu) << 3) | (wlo >> 29));
+        *lo = __uint_as_float(sign);
+        return;
+    }
+    *hi = __uint_as_float(sign | (uint32_t(e - 896) << 23) | ((whi & 0xfffffu) << 3) | (wlo >> 29));
+    const float m = __uint2float_rn(wlo & 0x1fffffffu);           // remainder mantissa
+    const float scale = __uint_as_float(uint32_t(e - 948) << 23);  // 2^(e - 1075)
+    *lo = __uint_as_float(__float_as_uint(__fmul_rn(m, scale)) | sign);
+}
+
+// Exact binary32 -> binary64 conversion by integer operations (no binary64
+// pipe instruction) for zero and normal values; subnormal inputs take the
+// hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sign = b & 0x80000000u;
+    const uint32_t mag = b & 0x7fffffffu;
+    if (mag == 0u) return __hiloint2double(int(sign), 0);
+    const uint32_t e = mag >> 23;
+    if (e == 0u || e == 255u) return double(f);
+    const uint32_t m = mag & 0x7fffffu;
+    return __hiloint2double(int(sign | ((e + 896u) << 20) | (m >> 3)), int(m << 29));
+}
+
+// True when x is an infinity or a NaN (integer test on the exponent field).
+__device__ __forceinline__ bool not_finite(double x) {
+    return (uint32_t(__double2hiint(x)) & 0x7ff00000u) == 0x7ff00000u;
+}
 
 // ---------------------------------------------------------------------------
 // Step 1: random walk with reflecting walls, then the particle's cell.
@@ -60,18 +124,28 @@ __device__ __forceinline__ double reflect(double x, double lo, double hi) {
     return x < lo ? lo : (x > hi ? hi : x);
 }
 
+__device__ __forceinline__ int clamp_cell(float u, int n) {
+    // u is finite here; truncation equals floor for u >= 0
+    return u <= 0.0f ? 0 : (u >= float(n - 1) ? n - 1 : int(u));
+}
+
 template <int DIM>
 __device__ __forceinline__ uint32_t cell_of(const double* x, const Grid& g, bool* bad) {
     uint32_t lin = 0, mult = 1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        const double u = __dmul_rn(__dsub_rn(x[a], g.lo[a]), g.inv_w[a]);
         int c = 0;
-        if (u == u) {                       // not NaN
-            c = u <= 0.0 ? 0 : (u >= double(g.n[a] - 1) ? g.n[a] - 1 : __double2int_rz(u));
+        if (g.cell_f32) {
+            float hi, lo;
+            split_double(x[a], &hi, &lo);
+            const float u = __fmul_rn(__fsub_rn(hi, g.lo_f[a]), g.inv_w_f[a]);
+            if (!not_finite(x[a])) c = clamp_cell(u, g.n[a]);
         } else {
-            *bad = true;
+            const double u = __dmul_rn(__dsub_rn(x[a], g.lo[a]), g.inv_w[a]);
+            if (u == u) c = u <= 0.0 ? 0 : (u >= double(g.n[a] - 1) ? g.n[a] - 1 : __double2int_rz(u));
+            else *bad = true;
         }
+        if (not_finite(x[a])) *bad = true;
         lin += uint32_t(c) * mult;
         mult *= uint32_t(g.n[a]);
     }
@@ -93,9 +167,14 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
         const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            const double v = __dadd_rn(x[a], __dmul_rn(sigma, double(z[a])));
-            x[a] = reflect(v, box.lo[a], box.hi[a]);
-            pos[a * stride + i] = x[a];
+            double v = __dadd_rn(x[a], __dmul_rn(sigma, f32_to_f64(z[a])));
+            const long long k = order_key(v);
+            // strictly inside in the integer order => inside in binary64, no
+            // mirror needed; anything else (walls, outside, NaN) takes the
+            // binary64 reflection
+            if (!(k > box.lo_key[a] && k < box.hi_key[a])) v = reflect(v, box.lo[a], box.hi[a]);
+            x[a] = v;
+            pos[a * stride + i] = v;
         }
     }
     if (do_key) {
@@ -118,6 +197,19 @@ __global__ void k_check_domain(int n, int64_t stride, const double* __restrict__
         const double x = pos[a * stride + i];
         if (!(x >= box.lo[a] && x <= box.hi[a])) atomicOr(status, kStatusOutOfDomain);
     }
+}
+
+// Cell-corner table: entry g.corner_off[a] + c holds lo_a + c w_a as a
+// binary32 head (nearest) and tail (nearest to the remainder).
+__global__ void k_corners(int total, int dim, Grid g, float2* __restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int a = 0;
+    while (a + 1 < dim && t >= g.corner_off[a + 1]) ++a;
+    const int c = t - g.corner_off[a];
+    const double corner = __dadd_rn(g.lo[a], __dmul_rn(double(c), g.w[a]));
+    const float hi = __double2float_rn(corner);
+    out[t] = make_float2(hi, __double2float_rn(__dsub_rn(corner, double(hi))));
 }
 
 __global__ void k_iota(int n, uint32_t* __restrict__ id) {
@@ -208,17 +300,18 @@ k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ 
 
 // Step 2c: gather into cell order.  The slot order the atomics gave inside a
 // cell is replaced by the rank of the particle id, so the layout (and every
-// sum over it) is identical run to run.  Also writes the particle's cell, the
-// binary32 offset from the cell corner and (precision form) the mass split
-// into a binary32 head and tail.
+// sum over it) is identical run to run.  Also writes the particle's cell, its
+// binary32 offset from the cell corner (from the binary32 head/tail split of
+// the coordinate and of the corner: error below 2^-23 w, no binary64
+// instruction) and, in the precision form, the mass's head/tail split.
 template <int DIM, bool SPLIT_MASS>
 __global__ void __launch_bounds__(kBlock)
 k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ key,
          const uint32_t* __restrict__ start, const uint32_t* __restrict__ id_in,
          const double* __restrict__ pos_in, const double* __restrict__ mass_in,
          uint32_t* __restrict__ id_out, double* __restrict__ pos_out, double* __restrict__ mass_out,
-         uint32_t* __restrict__ cell_out, float* __restrict__ xl_out, float2* __restrict__ msplit_out,
-         Grid g) {
+         uint32_t* __restrict__ cell_out, float4* __restrict__ rec_out,
+         float2* __restrict__ msplit_out, const float2* __restrict__ corners, Grid g) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t src = perm[s];
@@ -233,10 +326,11 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
     const double m = mass_in[src];
     mass_out[dst] = m;
     if (SPLIT_MASS) {
-        const float hi = __double2float_rn(m);
-        const float lo = __double2float_rn(__dsub_rn(m, double(hi)));
+        float hi, lo;
+        split_double(m, &hi, &lo);
         msplit_out[dst] = make_float2(hi, lo);
     }
+    float off[3] = {0.0f, 0.0f, 0.0f};
     uint32_t rest = c;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -244,41 +338,58 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
         rest /= uint32_t(g.n[a]);
         const double x = pos_in[a * stride + src];
         pos_out[a * stride + dst] = x;
-        const double corner = __dadd_rn(g.lo[a], __dmul_rn(double(ca), g.w[a]));
-        xl_out[a * stride + dst] = __double2float_rn(__dsub_rn(x, corner));
+        float xh, xlo;
+        split_double(x, &xh, &xlo);
+        const float2 cr = __ldg(corners + g.corner_off[a] + ca);
+        off[a] = __fadd_rn(__fsub_rn(xh, cr.x), __fsub_rn(xlo, cr.y));
     }
+    rec_out[dst] = make_float4(off[0], off[1], off[2], 0.0f);
 }
 
 // ---------------------------------------------------------------------------
 // Steps 2-5: neighbour visits.  For particle s (cell order) every particle j
-// in the 3^DIM surrounding cells is a candidate.  The binary32 squared
-// distance from the cell offsets decides every candidate outside a narrow
-// band around psi^2; inside the band the exact binary64 test
+// in the 3^DIM surrounding cells is a candidate, s itself included.  The
+// binary32 squared distance from the cell offsets decides every candidate
+// outside a narrow band around psi^2; inside the band the exact binary64 test
 // dx*dx + dy*dy (+ dz*dz) <= psi^2 (no fma, dx = x_i - x_j) decides.  The
 // band half-width is set on the host from an error bound of the binary32
 // evaluation, so the accepted set equals the exact binary64 pair set.
 //
-// The binary32 difference is always evaluated in the frame of the pair's
-// lower index, so d2f(i, j) == d2f(j, i) bit for bit, and every quantity
-// derived from it is symmetric in the pair.
+// The binary32 difference is (off_j - off_s) + shift, which changes sign
+// exactly when s and j swap, so d2f(s, j) == d2f(j, s) bit for bit and every
+// quantity derived from it is symmetric in the pair.  The self pair has
+// d2f = 0, K = 1 exactly: it supplies the self term of the row sum and a zero
+// flux, so no candidate is skipped.
 // ---------------------------------------------------------------------------
 template <int DIM>
 __device__ __forceinline__ double exact_d2(const double* __restrict__ pos, int64_t stride,
-                                           const double* xi, uint32_t j) {
+                                           uint32_t i, uint32_t j) {
     double d2 = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        const double d = __dsub_rn(xi[a], __ldg(pos + a * stride + j));
+        const double d = __dsub_rn(__ldg(pos + a * stride + i), __ldg(pos + a * stride + j));
         const double sq = __dmul_rn(d, d);
         d2 = (a == 0) ? sq : __dadd_rn(d2, sq);
     }
     return d2;
 }
 
+template <int DIM>
+__device__ __forceinline__ float d2_f32(const float4& me, const float4& o, float sx, float sy,
+                                        float sz) {
+    const float dx = __fadd_rn(__fsub_rn(o.x, me.x), sx);
+    if (DIM == 1) return __fmul_rn(dx, dx);
+    const float dy = __fadd_rn(__fsub_rn(o.y, me.y), sy);
+    if (DIM == 2) return __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+    const float dz = __fadd_rn(__fsub_rn(o.z, me.z), sz);
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+// visit(j, d2f, rec_j) is called for every neighbour j of s (s included).
 template <int DIM, class Visit>
 __device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int64_t stride,
-                                                 const float* __restrict__ xl,
-                                                 const double* __restrict__ pos, const double* xi,
+                                                 const float4* __restrict__ rec,
+                                                 const double* __restrict__ pos,
                                                  const uint32_t* __restrict__ start, const Grid& g,
                                                  const PairParams& pp, Visit&& visit) {
     int c[3] = {0, 0, 0};
@@ -290,44 +401,32 @@ __device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int6
             rest /= uint32_t(g.n[a]);
         }
     }
-    float xs[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) xs[a] = xl[a * stride + s];
+    const float4 me = rec[s];
     const int xlo = c[0] > 0 ? c[0] - 1 : 0;
     const int xhi = c[0] < g.n[0] - 1 ? c[0] + 1 : c[0];
-    const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
-    const int ylo = DIM >= 2 ? -1 : 0, yhi = DIM >= 2 ? 1 : 0;
+    const int zlo = DIM == 3 ? (c[2] > 0 ? -1 : 0) : 0;
+    const int zhi = DIM == 3 ? (c[2] < g.n[2] - 1 ? 1 : 0) : 0;
+    const int ylo = DIM >= 2 ? (c[1] > 0 ? -1 : 0) : 0;
+    const int yhi = DIM >= 2 ? (c[1] < g.n[1] - 1 ? 1 : 0) : 0;
+    const float wx = g.wf[0];
     for (int dz = zlo; dz <= zhi; ++dz) {
-        const int zz = c[2] + dz;
-        if (DIM == 3 && (zz < 0 || zz >= g.n[2])) continue;
+        const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
         for (int dy = ylo; dy <= yhi; ++dy) {
-            const int yy = c[1] + dy;
-            if (DIM >= 2 && (yy < 0 || yy >= g.n[1])) continue;
-            const uint32_t row = (uint32_t(zz) * uint32_t(g.n[1]) + uint32_t(yy)) * uint32_t(g.n[0]);
+            const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
+            const uint32_t row = (uint32_t(c[2] + dz) * uint32_t(g.n[1]) + uint32_t(c[1] + dy)) *
+                                 uint32_t(g.n[0]);
             const uint32_t j0 = __ldg(start + row + xlo);
             const uint32_t b1 = __ldg(start + row + c[0]);
             const uint32_t b2 = __ldg(start + row + c[0] + 1);
             const uint32_t j3 = __ldg(start + row + xhi + 1);
-            const float sh[3] = {0.0f, DIM >= 2 ? float(dy) * g.wf[1] : 0.0f,
-                                 DIM == 3 ? float(dz) * g.wf[2] : 0.0f};
+#pragma unroll 2
             for (uint32_t j = j0; j < j3; ++j) {
-                if (j == s) continue;
-                const bool fwd = s < j;
-                float d2f = 0.0f;
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) {
-                    const float xj = __ldg(xl + a * stride + j);
-                    float shift = a == 0 ? (j < b1 ? -g.wf[0] : (j < b2 ? 0.0f : g.wf[0])) : sh[a];
-                    const float p = fwd ? xj : xs[a];
-                    const float q = fwd ? xs[a] : xj;
-                    shift = fwd ? shift : -shift;
-                    const float d = __fsub_rn(__fadd_rn(p, shift), q);
-                    const float sq = __fmul_rn(d, d);
-                    d2f = (a == 0) ? sq : __fadd_rn(d2f, sq);
-                }
+                const float4 o = __ldg(rec + j);
+                const float sx = j < b1 ? -wx : (j < b2 ? 0.0f : wx);
+                const float d2f = d2_f32<DIM>(me, o, sx, sy, sz);
                 if (d2f > pp.band_hi) continue;
-                if (d2f >= pp.band_lo && exact_d2<DIM>(pos, stride, xi, j) > pp.psi2) continue;
-                visit(j, d2f);
+                if (d2f >= pp.band_lo && exact_d2<DIM>(pos, stride, s, j) > pp.psi2) continue;
+                visit(j, d2f, o);
             }
         }
     }
@@ -339,12 +438,24 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Compensated summation (Kahan-Babuska / Neumaier): s + c carries the sum to
-// about twice binary32 precision.
-__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
+// Compensated summation of positive terms (Kahan): s - c carries the sum,
+// four additions per term.  Used for the row sums, whose terms are all
+// positive.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// Compensated summation of mixed-sign terms (Kahan-Babuska / Neumaier):
+// s + c carries the sum to about twice binary32 precision whatever the order
+// of magnitudes.  Used for the flux sums.
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float x) {
     const float t = __fadd_rn(s, x);
-    const float big = fabsf(s) >= fabsf(x) ? s : x;
-    const float small = fabsf(s) >= fabsf(x) ? x : s;
+    const bool s_big = fabsf(s) >= fabsf(x);
+    const float big = s_big ? s : x;
+    const float small = s_big ? x : s;
     c = __fadd_rn(c, __fadd_rn(__fsub_rn(big, t), small));
     s = t;
 }
@@ -354,86 +465,159 @@ __device__ __forceinline__ void add_pair_count(uint32_t cnt, unsigned long long*
     if ((threadIdx.x & 31) == 0 && warp_total) atomicAdd(counter, (unsigned long long)warp_total);
 }
 
-// Pass 1, binary64 form: r_s = 1 + sum_j exp(-a d2_sj) (the kernel without its
-// constant factor, which cancels in W), and the ordered pair count.
+// ---------------------------------------------------------------------------
+// Binary64 form.  GB300's binary64 unit is narrow: a warp instruction costs
+// the same there whether 32 lanes or 3 are active, so evaluating the pair
+// kernel inside the divergent candidate loop wastes most of it.  Each warp
+// therefore (A) finds its accepted pairs with the binary32 prefilter --
+// counting first, then writing them lane-major into a shared-memory list --
+// (B) evaluates the binary64 pair terms with all 32 lanes, one list entry per
+// lane, and (C) lets each lane add its own entries in list order, so every
+// sum runs in candidate order and results repeat bit for bit.  Lists longer
+// than kDenseCap entries are processed in chunks (candidates re-enumerated
+// per chunk), so any density is handled.
+// ---------------------------------------------------------------------------
+constexpr int kDenseCap = 256;            // list entries per warp per chunk
+constexpr int kWarpsPerBlock = kBlock / 32;
+
+__device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t v, uint32_t* total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    *total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+// Shared state of the dense binary64 passes.
+struct DenseLists {
+    uint32_t j[kWarpsPerBlock][kDenseCap];
+    double v[kWarpsPerBlock][kDenseCap];
+    uint8_t owner[kWarpsPerBlock][kDenseCap];
+};
+
+// Runs phases A-C for the calling warp.  eval(owner_s, j) returns the binary64
+// pair term; add(term) is called by each lane for its own entries in order.
+template <int DIM, class Eval, class Add>
+__device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t stride,
+                                                const float4* __restrict__ rec,
+                                                const double* __restrict__ pos,
+                                                const uint32_t* __restrict__ cell,
+                                                const uint32_t* __restrict__ start, const Grid& g,
+                                                const PairParams& pp, DenseLists& L, Eval&& eval,
+                                                Add&& add) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t my_cell = valid ? cell[s] : 0u;
+    uint32_t cnt = 0;
+    if (valid)
+        visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, g, pp,
+                              [&](uint32_t j, float, const float4&) { cnt += (j != s) ? 1u : 0u; });
+    uint32_t total;
+    const uint32_t off = warp_exclusive_scan(cnt, &total);
+    const uint32_t warp_s0 = s - uint32_t(lane);
+    for (uint32_t chunk = 0; chunk < total; chunk += kDenseCap) {
+        const uint32_t chunk_end = chunk + kDenseCap;
+        if (valid && cnt > 0 && off < chunk_end && off + cnt > chunk) {
+            uint32_t k = off;
+            visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, g, pp,
+                                  [&](uint32_t j, float, const float4&) {
+                                      if (j == s) return;
+                                      if (k >= chunk && k < chunk_end) {
+                                          L.j[warp][k - chunk] = j;
+                                          L.owner[warp][k - chunk] = uint8_t(lane);
+                                      }
+                                      ++k;
+                                  });
+        }
+        __syncwarp();
+        const uint32_t m = min(total - chunk, uint32_t(kDenseCap));
+        for (uint32_t e = uint32_t(lane); e < m; e += 32)
+            L.v[warp][e] = eval(warp_s0 + L.owner[warp][e], L.j[warp][e]);
+        __syncwarp();
+        if (valid) {
+            const uint32_t q0 = max(off, chunk), q1 = min(off + cnt, chunk_end);
+            for (uint32_t q = q0; q < q1; ++q) add(L.v[warp][q - chunk]);
+        }
+        __syncwarp();
+    }
+    return cnt;
+}
+
+// Pass 1, binary64 form: r_s = 1 + sum_{j != s} exp(-a d2_sj) (the kernel
+// without its constant factor, which cancels in W; the self term is 1), and
+// the ordered pair count.
 template <int DIM>
 __global__ void __launch_bounds__(kBlock)
-k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float* __restrict__ xl,
+k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
              const double* __restrict__ exp_table, Grid g, PairParams pp,
              double* __restrict__ r_out, unsigned long long* __restrict__ pair_counter) {
     __shared__ double table[64];
+    __shared__ DenseLists lists;
     if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t cnt = 0;
-    if (s < n) {
-        double xi[DIM];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) xi[a] = pos[a * stride + s];
-        double r = 1.0;
-        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, xl, pos, xi, start, g, pp,
-                              [&](uint32_t j, float) {
-                                  const double d2 = exact_d2<DIM>(pos, stride, xi, j);
-                                  r = __dadd_rn(r, exp_neg(__dmul_rn(d2, pp.a), table, pp.ec));
-                                  ++cnt;
-                              });
-        r_out[s] = r;
-    }
-    add_pair_count(cnt, pair_counter);
+    const bool valid = s < n;
+    double r = 1.0;
+    const uint32_t cnt = dense_pairs<DIM>(
+        valid, uint32_t(s), stride, rec, pos, cell, start, g, pp, lists,
+        [&](uint32_t so, uint32_t j) {
+            return exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), pp.a), table, pp.ec);
+        },
+        [&](double K) { r = __dadd_rn(r, K); });
+    if (valid) r_out[s] = r;
+    add_pair_count(valid ? cnt : 0u, pair_counter);
 }
 
 // Pass 2, binary64 form: M'_s = M_s + beta sum_j (M_j - M_s) 2 K_sj / (r_s + r_j).
 template <int DIM>
 __global__ void __launch_bounds__(kBlock)
-k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const float* __restrict__ xl,
+k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
                const double* __restrict__ exp_table, Grid g, PairParams pp,
                const double* __restrict__ r, const double* __restrict__ mass,
                double* __restrict__ mass_out) {
     __shared__ double table[64];
+    __shared__ DenseLists lists;
     if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    double xi[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) xi[a] = pos[a * stride + s];
-    const double rs = r[s], ms = mass[s];
+    const bool valid = s < n;
     double acc = 0.0;
-    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, xl, pos, xi, start, g, pp,
-                          [&](uint32_t j, float) {
-                              const double d2 = exact_d2<DIM>(pos, stride, xi, j);
-                              const double K = exp_neg(__dmul_rn(d2, pp.a), table, pp.ec);
-                              const double W = __ddiv_rn(__dmul_rn(2.0, K), __dadd_rn(rs, __ldg(r + j)));
-                              acc = __fma_rn(__dsub_rn(__ldg(mass + j), ms), W, acc);
-                          });
-    mass_out[s] = __dadd_rn(ms, __dmul_rn(pp.beta, acc));
+    dense_pairs<DIM>(
+        valid, uint32_t(s), stride, rec, pos, cell, start, g, pp, lists,
+        [&](uint32_t so, uint32_t j) {
+            const double K = exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), pp.a), table, pp.ec);
+            const double W = __ddiv_rn(__dmul_rn(2.0, K), __dadd_rn(__ldg(r + so), __ldg(r + j)));
+            return __dmul_rn(__dsub_rn(__ldg(mass + j), __ldg(mass + so)), W);
+        },
+        [&](double f) { acc = __dadd_rn(acc, f); });
+    if (valid) mass_out[s] = __dadd_rn(mass[s], __dmul_rn(pp.beta, acc));
 }
 
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
-// hardware ex2, compensated binary32 row sum, rounded to binary32.
+// hardware ex2, compensated binary32 row sum, rounded to binary32 into rec.w.
 template <int DIM>
-__global__ void __launch_bounds__(kBlock)
-k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float* __restrict__ xl,
+__global__ void __launch_bounds__(kBlock, 6)
+k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start, Grid g,
-             PairParams pp, float* __restrict__ r_out, unsigned long long* __restrict__ pair_counter) {
+             PairParams pp, unsigned long long* __restrict__ pair_counter) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cnt = 0;
     if (s < n) {
-        double xi[DIM];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) xi[a] = pos[a * stride + s];
-        float rsum = 1.0f, rc = 0.0f;
-        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, xl, pos, xi, start, g, pp,
-                              [&](uint32_t, float d2f) {
-                                  const float K = ex2_approx(-pp.a_log2e * d2f);
-                                  const float t = __fadd_rn(rsum, K);   // rsum >= 1 >= K
-                                  rc = __fadd_rn(rc, __fadd_rn(__fsub_rn(rsum, t), K));
-                                  rsum = t;
+        float rsum = 0.0f, rc = 0.0f;
+        const float na = -pp.a_log2e;
+        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, g, pp,
+                              [&](uint32_t, float d2f, const float4&) {
+                                  kahan_add(rsum, rc, ex2_approx(na * d2f));
                                   ++cnt;
                               });
-        r_out[s] = __fadd_rn(rsum, rc);
+        // only .w changes; concurrent readers of this record use .x-.z
+        reinterpret_cast<float*>(rec + s)[3] = __fsub_rn(rsum, rc);
+        cnt -= 1;
     }
     add_pair_count(cnt, pair_counter);
 }
@@ -442,47 +626,45 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float*
 // bit), mass difference from the binary32 head/tail split (exactly
 // antisymmetric), flux accumulated with compensation, update in binary64.
 template <int DIM>
-__global__ void __launch_bounds__(kBlock)
-k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float* __restrict__ xl,
+__global__ void __launch_bounds__(kBlock, 6)
+k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start, Grid g,
-               PairParams pp, const float* __restrict__ r, const float2* __restrict__ msplit,
-               const double* __restrict__ mass, double* __restrict__ mass_out) {
+               PairParams pp, const float2* __restrict__ msplit, const double* __restrict__ mass,
+               double* __restrict__ mass_out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    double xi[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) xi[a] = pos[a * stride + s];
-    const float rs = r[s];
+    const float rs = rec[s].w;
     const float2 ms = msplit[s];
     float acc = 0.0f, comp = 0.0f;
-    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, xl, pos, xi, start, g, pp,
-                          [&](uint32_t j, float d2f) {
-                              const float K = ex2_approx(-pp.a_log2e * d2f);
-                              const float W = __fdividef(2.0f * K, __fadd_rn(rs, __ldg(r + j)));
+    const float na = -pp.a_log2e;
+    const float two_beta = float(2.0 * pp.beta);   // beta folded into W (still symmetric)
+    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, g, pp,
+                          [&](uint32_t j, float d2f, const float4& o) {
+                              const float K = ex2_approx(na * d2f);
+                              const float W = __fdividef(two_beta * K, __fadd_rn(rs, o.w));
                               const float2 mj = __ldg(msplit + j);
                               const float dm = __fadd_rn(__fsub_rn(mj.x, ms.x), __fsub_rn(mj.y, ms.y));
-                              comp_add(acc, comp, __fmul_rn(dm, W));
+                              neumaier_add(acc, comp, __fmul_rn(dm, W));
                           });
-    const double delta = __dadd_rn(double(acc), double(comp));
-    mass_out[s] = __dadd_rn(mass[s], __dmul_rn(pp.beta, delta));
+    // two binary64 additions per particle: acc + comp is exact in binary64
+    const double delta = __dadd_rn(f32_to_f64(acc), f32_to_f64(comp));
+    mass_out[s] = __dadd_rn(mass[s], delta);
 }
 
-// Test support: every accepted ordered pair as (id_s, id_j).
+// Test support: every accepted ordered pair j != s as (id_s, id_j).
 template <int DIM>
 __global__ void __launch_bounds__(kBlock)
-k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float* __restrict__ xl,
+k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
              const uint32_t* __restrict__ id, Grid g, PairParams pp, unsigned long long cap,
              unsigned long long* __restrict__ counter, uint32_t* __restrict__ out_i,
              uint32_t* __restrict__ out_j) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    double xi[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) xi[a] = pos[a * stride + s];
     const uint32_t ids = id[s];
-    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, xl, pos, xi, start, g, pp,
-                          [&](uint32_t j, float) {
+    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, g, pp,
+                          [&](uint32_t j, float, const float4&) {
+                              if (j == uint32_t(s)) return;
                               const unsigned long long k = atomicAdd(counter, 1ull);
                               if (k < cap) {
                                   out_i[k] = ids;
@@ -491,15 +673,16 @@ k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float*
                           });
 }
 
-// Outputs in input order: out[a * n + id[s]] = src[a * stride + s].
+// Outputs in input order: out[a * n + id[s]] = src[a * stride + s] * scale.
 template <typename T>
 __global__ void k_unpermute(int n, int64_t stride, int naxes, const uint32_t* __restrict__ id,
-                            const T* __restrict__ src, double scale, double* __restrict__ out) {
+                            const T* __restrict__ src, int src_step, double scale,
+                            double* __restrict__ out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t k = id[s];
     for (int a = 0; a < naxes; ++a)
-        out[int64_t(a) * n + k] = __dmul_rn(double(src[a * stride + s]), scale);
+        out[int64_t(a) * n + k] = __dmul_rn(double(src[(a * stride + s) * src_step]), scale);
 }
 
 }  // namespace mtpt

@@ -95,6 +95,8 @@ struct mtpt_handle {
     PairParams pp{};
     int64_t n = 0, cap = 0;
     int64_t n_cells = 0, n_cells_pad = 0;
+    int n_corners = 0;
+    double band_eta = 0.0;
     uint64_t step = 0;
     bool have_row_sums = false;
     // state, double-buffered (cur = index into the pair)
@@ -103,9 +105,9 @@ struct mtpt_handle {
     int cur = 0;
     // per-step scratch
     DevBuf<uint32_t> key, perm, cell, count, start, tile_sums;
-    DevBuf<float> xl;
+    DevBuf<float4> rec;
+    DevBuf<float2> corners;
     DevBuf<double> r64;
-    DevBuf<float> r32;
     DevBuf<float2> msplit;
     DevBuf<double> out_tmp;
     DevBuf<double> exp_table;
@@ -185,6 +187,7 @@ int validate_params(const mtpt_params* p) {
     for (int a = 0; a < p->dim; ++a) {
         if (!std::isfinite(p->lo[a]) || !std::isfinite(p->hi[a]) || !(p->lo[a] < p->hi[a]))
             return MTPT_ERR_INVALID_ARG;
+        if (std::fabs(p->lo[a]) > 1e15 || std::fabs(p->hi[a]) > 1e15) return MTPT_ERR_INVALID_ARG;
     }
     return MTPT_OK;
 }
@@ -207,14 +210,35 @@ void derive(mtpt_handle* h) {
     }
 }
 
+// Host image of the kernels' order key (int64 order of binary64 values).
+long long host_order_key(double x) {
+    long long b;
+    std::memcpy(&b, &x, sizeof(b));
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
 // Cell grid: width >= psi on every axis (slightly above, so a pair at
 // distance psi never spans two cell boundaries under rounding), with the
 // total cell count capped near 4 n so sparse boxes do not allocate huge
 // empty grids (cells then just get wider, which stays correct).
+//
+// The cell index of a walked particle is computed in binary32 when its error
+// is small: with u = 2^-24, the binary32 evaluation of (x - lo) / w is within
+// dc = 3 u (B + L) / psi cells of the exact one (B = max(|lo|, |hi|)), so
+// cells of width w >= psi / (1 - 2 dc) keep every pair within psi in adjacent
+// cells.  Boxes where dc > 1e-3 (very many cells per axis) use binary64.
 int setup_grid(mtpt_handle* h) {
     const mtpt_params& p = h->prm;
     Grid& g = h->grid;
-    const double psi_eff = h->psi * (1.0 + 1e-9);
+    const double u = std::ldexp(1.0, -24);
+    double dc = 0.0;
+    for (int a = 0; a < p.dim && h->psi > 0.0; ++a) {
+        const double B = std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a]));
+        dc = std::max(dc, 3.0 * u * (B + (p.hi[a] - p.lo[a])) / h->psi);
+    }
+    g.cell_f32 = (h->transfer_enabled && dc <= 1e-3) ? 1 : 0;
+    const double widen = g.cell_f32 ? 1.0 / (1.0 - 2.0 * dc) : 1.0;
+    const double psi_eff = h->psi * widen * (1.0 + 1e-9);
     double ncell[3] = {1, 1, 1};
     for (int a = 0; a < p.dim; ++a) {
         const double L = p.hi[a] - p.lo[a];
@@ -236,30 +260,41 @@ int setup_grid(mtpt_handle* h) {
         }
     }
     if (total > 2.0e9) return MTPT_ERR_INVALID_ARG;
-    double wmax_over_psi = 1.0;
+    double sum_w = 0.0, sum_b = 0.0;
+    int off = 0;
     for (int a = 0; a < 3; ++a) {
         g.n[a] = int(ncell[a]);
         g.lo[a] = a < p.dim ? p.lo[a] : 0.0;
         g.w[a] = a < p.dim ? (p.hi[a] - p.lo[a]) / ncell[a] : 1.0;
         g.inv_w[a] = 1.0 / g.w[a];
         g.wf[a] = float(g.w[a]);
-        if (a < p.dim && h->psi > 0.0) wmax_over_psi += g.w[a] / h->psi;
+        g.lo_f[a] = float(g.lo[a]);
+        g.inv_w_f[a] = float(g.inv_w[a]);
+        g.corner_off[a] = off;
+        off += (a < p.dim) ? g.n[a] : 0;
+        if (a < p.dim && h->psi > 0.0) {
+            sum_w += g.w[a] / h->psi;
+            sum_b += (std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a])) + g.w[a]) / h->psi;
+        }
     }
+    h->n_corners = off;
     h->n_cells = int64_t(total);
     h->n_cells_pad = ((h->n_cells + 1 + kScanTile - 1) / kScanTile) * kScanTile;
 
-    // Pair-test band.  With u = 2^-24, every binary32 coordinate offset is
-    // within u w of its exact value and each of the four roundings in
-    // (xl_j + shift) - xl_i adds at most u (2 w); so the squared distance
-    // evaluated in binary32 is within u (3 + 12 sum_a w_a / psi) psi^2 of the
-    // exact one for any candidate near the cutoff.  Four times that bound is
-    // the band half-width.
+    // Pair-test band.  Each binary32 cell offset is within 2u w (1 + dc) +
+    // 2^-46 B of the exact offset; the binary32 difference
+    // (off_j - off_i) + shift adds the rounding of both operations and of the
+    // shift, so per axis |dx_f - dx| <= 7 u w (1 + dc) + 2^-44 B, and with the
+    // roundings of the squares and sums
+    //   |d2f - d2| <= psi^2 (u (3 + 14 (1 + dc) sum_a w_a / psi) + 2^-43 sum_a B_a / psi)
+    // for every candidate within reach of the cutoff.  Twice that bound is the
+    // band half-width eta.
     PairParams& pp = h->pp;
-    const double u = std::ldexp(1.0, -24);
-    const double eta = 4.0 * u * (3.0 + 12.0 * wmax_over_psi);
+    const double eta = 2.0 * (u * (3.0 + 14.0 * (1.0 + dc) * sum_w) + std::ldexp(sum_b, -43)) + 1e-14;
     pp.psi2 = h->psi2;
-    pp.band_lo = float(h->psi2 * (1.0 - eta));
-    pp.band_hi = float(h->psi2 * (1.0 + eta));
+    pp.band_lo = std::nextafter(float(h->psi2 * (1.0 - eta)), 0.0f);
+    pp.band_hi = std::nextafter(float(h->psi2 * (1.0 + eta)), INFINITY);
+    h->band_eta = eta;
     pp.a = h->h2 > 0.0 ? 1.0 / (2.0 * h->h2) : 0.0;
     pp.a_log2e = float(pp.a * 1.4426950408889634);
     pp.beta = p.beta;
@@ -268,6 +303,20 @@ int setup_grid(mtpt_handle* h) {
     pp.ec.inv_step = 64.0 / ln2_hi;
     pp.ec.step_hi = ln2_hi / 64.0;
     pp.ec.step_lo = ln2_lo / 64.0;
+    for (int a = 0; a < 3; ++a) {
+        h->box.lo_key[a] = host_order_key(h->box.lo[a]);
+        h->box.hi_key[a] = host_order_key(h->box.hi[a]);
+    }
+    return MTPT_OK;
+}
+
+// Corner table of every axis on the device: corner = lo + c w (binary64),
+// stored as its binary32 head and tail.
+int build_corners(mtpt_handle* h) {
+    if (!h->transfer_enabled || h->n_corners == 0) return MTPT_OK;
+    k_corners<<<grid_for(h->n_corners), kBlock, 0, h->stream>>>(h->n_corners, h->prm.dim, h->grid,
+                                                               h->corners.p);
+    MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
 
@@ -292,11 +341,10 @@ int ensure_capacity(mtpt_handle* h, int64_t n) {
         MTPT_TRY(h->key.ensure(cap));
         MTPT_TRY(h->perm.ensure(cap));
         MTPT_TRY(h->cell.ensure(cap));
-        MTPT_TRY(h->xl.ensure(size_t(d) * cap));
+        MTPT_TRY(h->rec.ensure(cap));
         if (h->prm.precision == MTPT_FP64) {
             MTPT_TRY(h->r64.ensure(cap));
         } else {
-            MTPT_TRY(h->r32.ensure(cap));
             MTPT_TRY(h->msplit.ensure(cap));
         }
         h->cap = cap;
@@ -313,6 +361,8 @@ int ensure_cells(mtpt_handle* h) {
         MTPT_TRY(h->start.ensure(padded));
         MTPT_TRY(h->tile_sums.ensure(padded / kScanTile));
     }
+    MTPT_TRY(h->corners.ensure(size_t(std::max(h->n_corners, 1))));
+    MTPT_TRY(build_corners(h));
     // counts start (and, after each scatter, end) at zero
     MTPT_CUDA_TRY(cudaMemsetAsync(h->count.p, 0, padded * sizeof(uint32_t), h->stream));
     return MTPT_OK;
@@ -370,12 +420,14 @@ int launch_step(mtpt_handle* h, int flags) {
         MTPT_TIMED(h, "gather");
         k_gather<DIM, true><<<blocks, kBlock, 0, st>>>(
             n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, h->msplit.p, h->grid);
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
+            h->corners.p, h->grid);
     } else {
         MTPT_TIMED(h, "gather");
         k_gather<DIM, false><<<blocks, kBlock, 0, st>>>(
             n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, nullptr, h->grid);
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr,
+            h->corners.p, h->grid);
     }
     MTPT_CUDA_TRY(cudaGetLastError());
     // state now lives in buffer o (cell order); masses are updated into c
@@ -383,25 +435,24 @@ int launch_step(mtpt_handle* h, int flags) {
     if (!split) {
         {
         MTPT_TIMED(h, "rowsum_f64");
-        k_rowsum_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
+        k_rowsum_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
                                                      h->start.p, h->exp_table.p, h->grid, h->pp,
                                                      h->r64.p, h->pair_counter.p);
         }
         MTPT_TIMED(h, "exchange_f64");
-        k_exchange_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
+        k_exchange_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
                                                        h->start.p, h->exp_table.p, h->grid, h->pp,
                                                        h->r64.p, h->mass[o].p, h->mass[c].p);
     } else {
         {
         MTPT_TIMED(h, "rowsum_f32");
-        k_rowsum_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
-                                                     h->start.p, h->grid, h->pp, h->r32.p,
-                                                     h->pair_counter.p);
+        k_rowsum_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
+                                                     h->start.p, h->grid, h->pp, h->pair_counter.p);
         }
         MTPT_TIMED(h, "exchange_f32");
-        k_exchange_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->xl.p, h->cell.p,
-                                                       h->start.p, h->grid, h->pp, h->r32.p,
-                                                       h->msplit.p, h->mass[o].p, h->mass[c].p);
+        k_exchange_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
+                                                       h->start.p, h->grid, h->pp, h->msplit.p,
+                                                       h->mass[o].p, h->mass[c].p);
     }
     MTPT_CUDA_TRY(cudaGetLastError());
     // positions and ids live in o; the updated masses were written into c's
@@ -427,10 +478,12 @@ int ensure_out_tmp(mtpt_handle* h) {
 // Copy `naxes` arrays of the current state (stride cap, cell order) into
 // `out_dev` (stride n, input order), multiplied by `scale`.
 template <typename T>
-int unpermute_to(mtpt_handle* h, const T* src, int naxes, double scale, double* out_dev) {
+int unpermute_to(mtpt_handle* h, const T* src, int naxes, double scale, double* out_dev,
+                 int src_step = 1) {
     if (h->n == 0) return MTPT_OK;
     k_unpermute<T><<<grid_for(h->n), kBlock, 0, h->stream>>>(int(h->n), h->cap, naxes,
-                                                            h->id[h->cur].p, src, scale, out_dev);
+                                                            h->id[h->cur].p, src, src_step, scale,
+                                                            out_dev);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -493,8 +546,8 @@ int mtpt_destroy(mtpt_handle* h) {
         h->id[b].release();
     }
     h->key.release(); h->perm.release(); h->cell.release(); h->count.release();
-    h->start.release(); h->tile_sums.release(); h->xl.release(); h->r64.release();
-    h->r32.release(); h->msplit.release(); h->out_tmp.release(); h->exp_table.release();
+    h->start.release(); h->tile_sums.release(); h->rec.release(); h->corners.release();
+    h->r64.release(); h->msplit.release(); h->out_tmp.release(); h->exp_table.release();
     h->status.release(); h->pair_counter.release(); h->emit_counter.release();
     h->emit_i.release(); h->emit_j.release();
     for (auto& pe : h->pending) {
@@ -593,7 +646,8 @@ int mtpt_get_row_sums(mtpt_handle* h, double* out) {
     if (h->prm.precision == MTPT_FP64)
         MTPT_TRY(unpermute_to<double>(h, h->r64.p, 1, h->kernel_norm, h->out_tmp.p));
     else
-        MTPT_TRY(unpermute_to<float>(h, h->r32.p, 1, h->kernel_norm, h->out_tmp.p));
+        MTPT_TRY(unpermute_to<float>(h, reinterpret_cast<const float*>(h->rec.p) + 3, 1,
+                                     h->kernel_norm, h->out_tmp.p, 4));
     return copy_out_host(h, 1, out);
 }
 
@@ -629,13 +683,15 @@ int mtpt_get_pairs(mtpt_handle* h, int64_t cap, int64_t* count, uint32_t* pair_i
         if (h->prm.precision == MTPT_FP32W)
             k_gather<DIM, true><<<blocks, kBlock, 0, h->stream>>>(
                 n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, h->msplit.p, h->grid);
+                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
+                h->corners.p, h->grid);
         else
             k_gather<DIM, false><<<blocks, kBlock, 0, h->stream>>>(
                 n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->xl.p, nullptr, h->grid);
+                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr,
+                h->corners.p, h->grid);
         k_emit_pairs<DIM><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->pos[o].p, h->xl.p, h->cell.p, h->start.p, h->id[o].p, h->grid, h->pp,
+            n, stride, h->pos[o].p, h->rec.p, h->cell.p, h->start.p, h->id[o].p, h->grid, h->pp,
             (unsigned long long)cap, h->emit_counter.p, h->emit_i.p, h->emit_j.p);
         MTPT_CUDA_TRY(cudaGetLastError());
         return MTPT_OK;
@@ -824,13 +880,13 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.key.p = cv.take<uint32_t>(size_t(n));
     h.perm.p = cv.take<uint32_t>(size_t(n));
     h.cell.p = cv.take<uint32_t>(size_t(n));
-    h.xl.p = cv.take<float>(size_t(d) * size_t(n));
+    h.rec.p = cv.take<float4>(size_t(n));
     if (h.prm.precision == MTPT_FP64) {
         h.r64.p = cv.take<double>(size_t(n));
     } else {
-        h.r32.p = cv.take<float>(size_t(n));
         h.msplit.p = cv.take<float2>(size_t(n));
     }
+    h.corners.p = cv.take<float2>(size_t(std::max(h.n_corners, 1)));
     h.count.p = cv.take<uint32_t>(cells_pad);
     h.start.p = cv.take<uint32_t>(cells_pad);
     h.tile_sums.p = cv.take<uint32_t>(cells_pad / kScanTile);
@@ -867,10 +923,11 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
                                   cudaMemcpyDeviceToDevice, st));
     k_iota<<<grid_for(n), kBlock, 0, st>>>(int(n), id_in);
     MTPT_CUDA_TRY(cudaGetLastError());
+    MTPT_TRY(build_corners(&h));
     MTPT_TRY(dispatch_step(&h, MTPT_DO_WALK | MTPT_DO_TRANSFER));
     // masses back to the caller's order; positions are already there
     k_unpermute<double><<<grid_for(n), kBlock, 0, st>>>(int(n), h.cap, 1, h.id[h.cur].p,
-                                                        h.mass[h.cur].p, 1.0, mass_dev);
+                                                        h.mass[h.cur].p, 1, 1.0, mass_dev);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
