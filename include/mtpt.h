@@ -130,8 +130,34 @@ int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const doubl
 int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
                               const double* mass_dev);
 
+/* Batch of independent realisations stepped together (the ensemble form).
+ * params[k] holds realisation k's parameters (D, kappa, dt, beta, lambda,
+ * box, seed may all differ); dim and precision must be equal across the
+ * batch (MTPT_ERR_INVALID_ARG otherwise), 1 <= count <= 2^20.  Every time
+ * step is one launch per kernel over all realisations' particles, and
+ * realisation k evolves bit for bit as a handle created with params[k] on the
+ * same particles would. */
+int mtpt_create_batch(const mtpt_params* params, int32_t count, mtpt_handle** out);
+
+/* Load the particles of every realisation of a batch from HOST buffers:
+ * counts[k] particles for realisation k (count entries), concatenated in
+ * realisation order.  pos is dim x total (SoA over the concatenation: axis a
+ * of particle i of realisation k at pos[a * total + offset_k + i], offset_k
+ * the sum of the earlier counts), mass is total doubles.  Realisation k's
+ * particles must lie inside its own box.  Outputs (masses, positions, row
+ * sums) use the same concatenated order; the generator id of a particle is
+ * its index within its realisation. */
+int mtpt_set_particles_batch(mtpt_handle* h, const int64_t* counts, const double* pos,
+                             const double* mass);
+
+/* Derived quantities of realisation k of a batch (n is that realisation's
+ * particle count; pair_count is not filled). */
+int mtpt_get_realisation_info(mtpt_handle* h, int32_t k, mtpt_info* out);
+
 /* Advance nsteps full time steps (walk, then mass transfer on the moved
- * positions).  Enqueued on the stream; returns the launch status. */
+ * positions).  Enqueued on the stream; returns the launch status.  Calls of
+ * four or more steps capture two steps as a CUDA graph on first use and
+ * replay it (same results as step-by-step launches). */
 int mtpt_step(mtpt_handle* h, int64_t nsteps);
 
 /* As mtpt_step with a subset of the step: flags is a combination of

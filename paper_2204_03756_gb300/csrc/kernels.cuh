@@ -58,6 +58,42 @@ struct PairParams {
     ExpNegConsts ec;
 };
 
+// Everything one realisation's kernels need.  A single run passes one by
+// value (SingleView); a batch of independent realisations keeps a table in
+// device memory and a realisation index per particle (BatchView).
+struct RealParams {
+    Box box;
+    Grid g;
+    PairParams pp;
+    double sigma;        // walk scale sqrt(2 D_RW dt)
+    double kernel_norm;  // (2 pi h^2)^(-d/2)
+    uint64_t seed;       // generator key of the walk
+    uint32_t id_offset;  // first global particle index of the realisation
+    uint32_t cell_base;  // first global cell of the realisation
+    int32_t transfer;    // 1 when D_MT > 0 (pair passes run)
+    int32_t walk;        // 1 when sigma > 0
+};
+
+struct SingleView {
+    static constexpr bool kBatch = false;
+    RealParams p;
+    __device__ __forceinline__ const RealParams& of_input(uint32_t) const { return p; }
+    __device__ __forceinline__ const RealParams& of_sorted(uint32_t) const { return p; }
+};
+
+struct BatchView {
+    static constexpr bool kBatch = true;
+    const RealParams* tbl;
+    const uint32_t* rid_input;    // realisation of each particle before the sort
+    const uint32_t* rid_sorted;   // realisation of each particle in cell order
+    __device__ __forceinline__ const RealParams& of_input(uint32_t i) const {
+        return tbl[__ldg(rid_input + i)];
+    }
+    __device__ __forceinline__ const RealParams& of_sorted(uint32_t s) const {
+        return tbl[__ldg(rid_sorted + s)];
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Integer helpers for binary64 values.
 // ---------------------------------------------------------------------------
@@ -152,34 +188,38 @@ __device__ __forceinline__ uint32_t cell_of(const double* x, const Grid& g, bool
     return lin;
 }
 
-template <int DIM>
+template <int DIM, class View>
 __global__ void __launch_bounds__(kBlock)
 k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __restrict__ id,
-           uint64_t seed, uint64_t step, double sigma, int do_walk, int do_key, Box box, Grid g,
-           uint32_t* __restrict__ key, uint32_t* __restrict__ count, uint32_t* __restrict__ status) {
+           const unsigned long long* __restrict__ step_dev, int do_walk, int do_key,
+           const __grid_constant__ View v, uint32_t* __restrict__ key,
+           uint32_t* __restrict__ count, uint32_t* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const uint64_t step = *step_dev;
+    const RealParams& P = v.of_input(uint32_t(i));
     double x[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) x[a] = pos[a * stride + i];
-    if (do_walk) {
-        const float4 z4 = normals4(seed, id[i], step);
+    if (do_walk && P.walk) {
+        const float4 z4 = normals4(P.seed, id[i] - P.id_offset, step);
         const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            double v = __dadd_rn(x[a], __dmul_rn(sigma, f32_to_f64(z[a])));
-            const long long k = order_key(v);
+            double xv = __dadd_rn(x[a], __dmul_rn(P.sigma, f32_to_f64(z[a])));
+            const long long k = order_key(xv);
             // strictly inside in the integer order => inside in binary64, no
             // mirror needed; anything else (walls, outside, NaN) takes the
             // binary64 reflection
-            if (!(k > box.lo_key[a] && k < box.hi_key[a])) v = reflect(v, box.lo[a], box.hi[a]);
-            x[a] = v;
-            pos[a * stride + i] = v;
+            if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
+                xv = reflect(xv, P.box.lo[a], P.box.hi[a]);
+            x[a] = xv;
+            pos[a * stride + i] = xv;
         }
     }
     if (do_key) {
         bool bad = false;
-        const uint32_t c = cell_of<DIM>(x, g, &bad);
+        const uint32_t c = P.cell_base + cell_of<DIM>(x, P.g, &bad);
         if (bad) atomicOr(status, kStatusNonFinite);
         key[i] = c;
         atomicAdd(&count[c], 1u);
@@ -187,29 +227,39 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
 }
 
 // Domain check of positions loaded from device memory.
-template <int DIM>
-__global__ void k_check_domain(int n, int64_t stride, const double* __restrict__ pos, Box box,
-                               uint32_t* __restrict__ status) {
+template <int DIM, class View>
+__global__ void k_check_domain(int n, int64_t stride, const double* __restrict__ pos,
+                               const __grid_constant__ View v, uint32_t* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const RealParams& P = v.of_input(uint32_t(i));
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         const double x = pos[a * stride + i];
-        if (!(x >= box.lo[a] && x <= box.hi[a])) atomicOr(status, kStatusOutOfDomain);
+        if (!(x >= P.box.lo[a] && x <= P.box.hi[a])) atomicOr(status, kStatusOutOfDomain);
     }
 }
 
-// Cell-corner table: entry g.corner_off[a] + c holds lo_a + c w_a as a
-// binary32 head (nearest) and tail (nearest to the remainder).
-__global__ void k_corners(int total, int dim, Grid g, float2* __restrict__ out) {
+// Cell-corner tables: entry P.g.corner_off[a] + c holds lo_a + c w_a of
+// realisation P as a binary32 head (nearest) and tail (nearest to the
+// remainder).  One thread per (realisation, axis, cell) entry; `first[k]` is
+// the first entry of realisation k (first[nreal] = total).
+__global__ void k_corners(int total, int nreal, int dim, const RealParams* __restrict__ tbl,
+                          const int* __restrict__ first, float2* __restrict__ out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
+    int lo = 0, hi = nreal - 1;            // realisation: last k with first[k] <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const Grid& g = tbl[lo].g;
     int a = 0;
     while (a + 1 < dim && t >= g.corner_off[a + 1]) ++a;
     const int c = t - g.corner_off[a];
     const double corner = __dadd_rn(g.lo[a], __dmul_rn(double(c), g.w[a]));
-    const float hi = __double2float_rn(corner);
-    out[t] = make_float2(hi, __double2float_rn(__dsub_rn(corner, double(hi))));
+    const float hi_f = __double2float_rn(corner);
+    out[t] = make_float2(hi_f, __double2float_rn(__dsub_rn(corner, double(hi_f))));
 }
 
 __global__ void k_iota(int n, uint32_t* __restrict__ id) {
@@ -261,8 +311,12 @@ k_scan_tile_sums(const uint4* __restrict__ count4, uint32_t* __restrict__ tile_s
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
+// Also advances the walk's step counter (device-resident, so a captured graph
+// of steps replays with the right counters) when `advance` is set; every
+// kernel of the step that reads the counter has completed by then.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_tile_offsets(uint32_t* __restrict__ tile_sums, int ntiles) {
+k_scan_tile_offsets(uint32_t* __restrict__ tile_sums, int ntiles,
+                    unsigned long long* __restrict__ step_dev, int advance) {
     uint32_t carry = 0;
     for (int base = 0; base < ntiles; base += kScanThreads) {
         const int t = base + threadIdx.x;
@@ -272,6 +326,27 @@ k_scan_tile_offsets(uint32_t* __restrict__ tile_sums, int ntiles) {
         if (t < ntiles) tile_sums[t] = carry + excl;
         carry += total;
     }
+    if (advance && threadIdx.x == 0) *step_dev += 1ull;
+}
+
+// Step counter updates for steps without a scan (walk only) and for resets.
+__global__ void k_advance_step(unsigned long long* __restrict__ step_dev) { *step_dev += 1ull; }
+__global__ void k_set_step(unsigned long long* __restrict__ step_dev, unsigned long long value) {
+    *step_dev = value;
+}
+
+// Realisation index of every particle of a batch: the last k with
+// first[k] <= i (first[nreal] = n).
+__global__ void k_fill_rid(int n, int nreal, const uint32_t* __restrict__ first,
+                           uint32_t* __restrict__ rid) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nreal - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= uint32_t(i)) lo = mid; else hi = mid - 1;
+    }
+    rid[i] = uint32_t(lo);
 }
 
 __global__ void __launch_bounds__(kScanThreads)
@@ -304,14 +379,15 @@ k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ 
 // binary32 offset from the cell corner (from the binary32 head/tail split of
 // the coordinate and of the corner: error below 2^-23 w, no binary64
 // instruction) and, in the precision form, the mass's head/tail split.
-template <int DIM, bool SPLIT_MASS>
+template <int DIM, bool SPLIT_MASS, class View>
 __global__ void __launch_bounds__(kBlock)
 k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ key,
          const uint32_t* __restrict__ start, const uint32_t* __restrict__ id_in,
          const double* __restrict__ pos_in, const double* __restrict__ mass_in,
          uint32_t* __restrict__ id_out, double* __restrict__ pos_out, double* __restrict__ mass_out,
          uint32_t* __restrict__ cell_out, float4* __restrict__ rec_out,
-         float2* __restrict__ msplit_out, const float2* __restrict__ corners, Grid g) {
+         float2* __restrict__ msplit_out, const float2* __restrict__ corners,
+         uint32_t* __restrict__ rid_out, const __grid_constant__ View v) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t src = perm[s];
@@ -323,6 +399,8 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
     const uint32_t dst = b + rank;
     id_out[dst] = my_id;
     cell_out[dst] = c;
+    if constexpr (View::kBatch) rid_out[dst] = __ldg(v.rid_input + src);
+    const RealParams& P = v.of_input(src);
     const double m = mass_in[src];
     mass_out[dst] = m;
     if (SPLIT_MASS) {
@@ -331,17 +409,19 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
         msplit_out[dst] = make_float2(hi, lo);
     }
     float off[3] = {0.0f, 0.0f, 0.0f};
-    uint32_t rest = c;
+    uint32_t rest = c - P.cell_base;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        const uint32_t ca = rest % uint32_t(g.n[a]);
-        rest /= uint32_t(g.n[a]);
+        const uint32_t ca = rest % uint32_t(P.g.n[a]);
+        rest /= uint32_t(P.g.n[a]);
         const double x = pos_in[a * stride + src];
         pos_out[a * stride + dst] = x;
-        float xh, xlo;
-        split_double(x, &xh, &xlo);
-        const float2 cr = __ldg(corners + g.corner_off[a] + ca);
-        off[a] = __fadd_rn(__fsub_rn(xh, cr.x), __fsub_rn(xlo, cr.y));
+        if (P.transfer) {
+            float xh, xlo;
+            split_double(x, &xh, &xlo);
+            const float2 cr = __ldg(corners + P.g.corner_off[a] + ca);
+            off[a] = __fadd_rn(__fsub_rn(xh, cr.x), __fsub_rn(xlo, cr.y));
+        }
     }
     rec_out[dst] = make_float4(off[0], off[1], off[2], 0.0f);
 }
@@ -390,11 +470,13 @@ template <int DIM, class Visit>
 __device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int64_t stride,
                                                  const float4* __restrict__ rec,
                                                  const double* __restrict__ pos,
-                                                 const uint32_t* __restrict__ start, const Grid& g,
-                                                 const PairParams& pp, Visit&& visit) {
+                                                 const uint32_t* __restrict__ start,
+                                                 const RealParams& P, Visit&& visit) {
+    const Grid& g = P.g;
+    const PairParams& pp = P.pp;
     int c[3] = {0, 0, 0};
     {
-        uint32_t rest = cell;
+        uint32_t rest = cell - P.cell_base;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             c[a] = int(rest % uint32_t(g.n[a]));
@@ -413,8 +495,8 @@ __device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int6
         const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
         for (int dy = ylo; dy <= yhi; ++dy) {
             const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
-            const uint32_t row = (uint32_t(c[2] + dz) * uint32_t(g.n[1]) + uint32_t(c[1] + dy)) *
-                                 uint32_t(g.n[0]);
+            const uint32_t row = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
+                                                uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
             const uint32_t j0 = __ldg(start + row + xlo);
             const uint32_t b1 = __ldg(start + row + c[0]);
             const uint32_t b2 = __ldg(start + row + c[0] + 1);
@@ -506,14 +588,14 @@ __device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t 
                                                 const float4* __restrict__ rec,
                                                 const double* __restrict__ pos,
                                                 const uint32_t* __restrict__ cell,
-                                                const uint32_t* __restrict__ start, const Grid& g,
-                                                const PairParams& pp, DenseLists& L, Eval&& eval,
+                                                const uint32_t* __restrict__ start,
+                                                const RealParams& P, DenseLists& L, Eval&& eval,
                                                 Add&& add) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t my_cell = valid ? cell[s] : 0u;
     uint32_t cnt = 0;
     if (valid)
-        visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, g, pp,
+        visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, P,
                               [&](uint32_t j, float, const float4&) { cnt += (j != s) ? 1u : 0u; });
     uint32_t total;
     const uint32_t off = warp_exclusive_scan(cnt, &total);
@@ -522,7 +604,7 @@ __device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t 
         const uint32_t chunk_end = chunk + kDenseCap;
         if (valid && cnt > 0 && off < chunk_end && off + cnt > chunk) {
             uint32_t k = off;
-            visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, g, pp,
+            visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, P,
                                   [&](uint32_t j, float, const float4&) {
                                       if (j == s) return;
                                       if (k >= chunk && k < chunk_end) {
@@ -549,35 +631,37 @@ __device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t 
 // Pass 1, binary64 form: r_s = 1 + sum_{j != s} exp(-a d2_sj) (the kernel
 // without its constant factor, which cancels in W; the self term is 1), and
 // the ordered pair count.
-template <int DIM>
+template <int DIM, class View>
 __global__ void __launch_bounds__(kBlock)
 k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
-             const double* __restrict__ exp_table, Grid g, PairParams pp,
+             const double* __restrict__ exp_table, const __grid_constant__ View v,
              double* __restrict__ r_out, unsigned long long* __restrict__ pair_counter) {
     __shared__ double table[64];
     __shared__ DenseLists lists;
     if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = s < n;
+    const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
+    const bool valid = s < n && P.transfer;
     double r = 1.0;
     const uint32_t cnt = dense_pairs<DIM>(
-        valid, uint32_t(s), stride, rec, pos, cell, start, g, pp, lists,
+        valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
         [&](uint32_t so, uint32_t j) {
-            return exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), pp.a), table, pp.ec);
+            const RealParams& Po = v.of_sorted(so);
+            return exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), Po.pp.a), table, Po.pp.ec);
         },
         [&](double K) { r = __dadd_rn(r, K); });
-    if (valid) r_out[s] = r;
+    if (s < n) r_out[s] = r;
     add_pair_count(valid ? cnt : 0u, pair_counter);
 }
 
 // Pass 2, binary64 form: M'_s = M_s + beta sum_j (M_j - M_s) 2 K_sj / (r_s + r_j).
-template <int DIM>
+template <int DIM, class View>
 __global__ void __launch_bounds__(kBlock)
 k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
-               const double* __restrict__ exp_table, Grid g, PairParams pp,
+               const double* __restrict__ exp_table, const __grid_constant__ View v,
                const double* __restrict__ r, const double* __restrict__ mass,
                double* __restrict__ mass_out) {
     __shared__ double table[64];
@@ -585,39 +669,47 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
     if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = s < n;
+    const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
+    const bool valid = s < n && P.transfer;
     double acc = 0.0;
     dense_pairs<DIM>(
-        valid, uint32_t(s), stride, rec, pos, cell, start, g, pp, lists,
+        valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
         [&](uint32_t so, uint32_t j) {
-            const double K = exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), pp.a), table, pp.ec);
+            const RealParams& Po = v.of_sorted(so);
+            const double K = exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), Po.pp.a), table,
+                                     Po.pp.ec);
             const double W = __ddiv_rn(__dmul_rn(2.0, K), __dadd_rn(__ldg(r + so), __ldg(r + j)));
             return __dmul_rn(__dsub_rn(__ldg(mass + j), __ldg(mass + so)), W);
         },
         [&](double f) { acc = __dadd_rn(acc, f); });
-    if (valid) mass_out[s] = __dadd_rn(mass[s], __dmul_rn(pp.beta, acc));
+    if (s < n) mass_out[s] = valid ? __dadd_rn(mass[s], __dmul_rn(P.pp.beta, acc)) : mass[s];
 }
 
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
 // hardware ex2, compensated binary32 row sum, rounded to binary32 into rec.w.
-template <int DIM>
+template <int DIM, class View>
 __global__ void __launch_bounds__(kBlock, 6)
 k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, float4* __restrict__ rec,
-             const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start, Grid g,
-             PairParams pp, unsigned long long* __restrict__ pair_counter) {
+             const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
+             const __grid_constant__ View v, unsigned long long* __restrict__ pair_counter) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cnt = 0;
     if (s < n) {
+        const RealParams& P = v.of_sorted(uint32_t(s));
         float rsum = 0.0f, rc = 0.0f;
-        const float na = -pp.a_log2e;
-        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, g, pp,
-                              [&](uint32_t, float d2f, const float4&) {
-                                  kahan_add(rsum, rc, ex2_approx(na * d2f));
-                                  ++cnt;
-                              });
+        if (P.transfer) {
+            const float na = -P.pp.a_log2e;
+            visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
+                                  [&](uint32_t, float d2f, const float4&) {
+                                      kahan_add(rsum, rc, ex2_approx(na * d2f));
+                                      ++cnt;
+                                  });
+            cnt -= 1;   // the self pair
+        } else {
+            rsum = 1.0f;
+        }
         // only .w changes; concurrent readers of this record use .x-.z
         reinterpret_cast<float*>(rec + s)[3] = __fsub_rn(rsum, rc);
-        cnt -= 1;
     }
     add_pair_count(cnt, pair_counter);
 }
@@ -625,20 +717,25 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, float4* __re
 // Pass 2, precision form: W = 2K / (r_s + r_j) in binary32 (symmetric bit for
 // bit), mass difference from the binary32 head/tail split (exactly
 // antisymmetric), flux accumulated with compensation, update in binary64.
-template <int DIM>
+template <int DIM, class View>
 __global__ void __launch_bounds__(kBlock, 6)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
-               const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start, Grid g,
-               PairParams pp, const float2* __restrict__ msplit, const double* __restrict__ mass,
-               double* __restrict__ mass_out) {
+               const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
+               const __grid_constant__ View v, const float2* __restrict__ msplit,
+               const double* __restrict__ mass, double* __restrict__ mass_out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    const RealParams& P = v.of_sorted(uint32_t(s));
+    if (!P.transfer) {
+        mass_out[s] = mass[s];
+        return;
+    }
     const float rs = rec[s].w;
     const float2 ms = msplit[s];
     float acc = 0.0f, comp = 0.0f;
-    const float na = -pp.a_log2e;
-    const float two_beta = float(2.0 * pp.beta);   // beta folded into W (still symmetric)
-    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, g, pp,
+    const float na = -P.pp.a_log2e;
+    const float two_beta = float(2.0 * P.pp.beta);   // beta folded into W (still symmetric)
+    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
                           [&](uint32_t j, float d2f, const float4& o) {
                               const float K = ex2_approx(na * d2f);
                               const float W = __fdividef(two_beta * K, __fadd_rn(rs, o.w));
@@ -652,17 +749,19 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
 }
 
 // Test support: every accepted ordered pair j != s as (id_s, id_j).
-template <int DIM>
+template <int DIM, class View>
 __global__ void __launch_bounds__(kBlock)
 k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
-             const uint32_t* __restrict__ id, Grid g, PairParams pp, unsigned long long cap,
-             unsigned long long* __restrict__ counter, uint32_t* __restrict__ out_i,
-             uint32_t* __restrict__ out_j) {
+             const uint32_t* __restrict__ id, const __grid_constant__ View v,
+             unsigned long long cap, unsigned long long* __restrict__ counter,
+             uint32_t* __restrict__ out_i, uint32_t* __restrict__ out_j) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    const RealParams& P = v.of_sorted(uint32_t(s));
+    if (!P.transfer) return;
     const uint32_t ids = id[s];
-    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, g, pp,
+    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
                           [&](uint32_t j, float, const float4&) {
                               if (j == uint32_t(s)) return;
                               const unsigned long long k = atomicAdd(counter, 1ull);
@@ -671,6 +770,18 @@ k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float4
                                   out_j[k] = id[j];
                               }
                           });
+}
+
+// Row sums in input order and in the paper's units:
+// out[id[s]] = r_s * kernel_norm of the particle's realisation.
+template <typename T, class View>
+__global__ void k_row_sums_out(int n, const uint32_t* __restrict__ id, const T* __restrict__ src,
+                               int src_step, const __grid_constant__ View v,
+                               double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const RealParams& P = v.of_sorted(uint32_t(s));
+    out[id[s]] = __dmul_rn(double(src[int64_t(s) * src_step]), P.kernel_norm);
 }
 
 // Outputs in input order: out[a * n + id[s]] = src[a * stride + s] * scale.

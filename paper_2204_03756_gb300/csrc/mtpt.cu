@@ -1,10 +1,14 @@
 // mtpt.cu -- host side of the C ABI declared in include/mtpt.h.
 //
-// A handle owns the particle state on one device in cell order and runs one
-// time step of Sec. 3 as a fixed sequence of kernels on the handle's stream:
+// A handle owns the particle state of one realisation -- or of a batch of
+// independent realisations -- on one device, in cell order, and runs one time
+// step of Sec. 3 as a fixed sequence of kernels on the handle's stream:
 //   walk_key -> scan (3 launches) -> scatter -> gather -> rowsum -> exchange
-// No step goes through the host: the only host<->device traffic is in
-// mtpt_set_particles / mtpt_get_*.
+// A batch concatenates its realisations' particles and gives each
+// realisation its own block of cells in one global cell list, so every phase
+// is one launch over all particles of all realisations.  Multi-step calls
+// replay a captured CUDA graph of two steps.  No step goes through the host:
+// the only host<->device traffic is in mtpt_set_particles* / mtpt_get_*.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +28,7 @@ using namespace mtpt;
 namespace {
 
 constexpr int kMaxDim = 3;
+constexpr int64_t kGraphMinSteps = 4;   // multi-step calls from this size replay a graph
 
 #define MTPT_CUDA_TRY(expr)                                   \
     do {                                                      \
@@ -34,9 +39,9 @@ constexpr int kMaxDim = 3;
         }                                                     \
     } while (0)
 
-#define MTPT_TRY(expr)              \
-    do {                            \
-        int rc_ = (expr);           \
+#define MTPT_TRY(expr)                  \
+    do {                                \
+        int rc_ = (expr);               \
         if (rc_ != MTPT_OK) return rc_; \
     } while (0)
 
@@ -66,6 +71,15 @@ struct DevBuf {
 
 int grid_for(int64_t n) { return int((n + kBlock - 1) / kBlock); }
 
+// Host-side data of one realisation.
+struct RealHost {
+    mtpt_params prm{};
+    double D_RW = 0, D_MT = 0, h2 = 0, psi = 0, psi2 = 0, band_eta = 0;
+    int64_t n = 0;
+    int64_t n_cells = 0;
+    int n_corners = 0;
+};
+
 }  // namespace
 
 struct mtpt_handle;
@@ -85,36 +99,48 @@ struct KernelTimer {
 #define MTPT_TIMED(h, name) KernelTimer MTPT_CAT(kernel_timer_, __LINE__)((h), (name))
 
 struct mtpt_handle {
-    mtpt_params prm{};
+    int dim = 2, precision = MTPT_FP64;
+    bool batch = false;               // created by mtpt_create_batch
+    int nreal = 1;
+    // realisations: inline storage for a single run (no host allocation on
+    // that path), heap storage for a batch
+    RealHost real_inline;
+    RealParams params_inline{};
+    std::vector<RealHost> real_heap;
+    std::vector<RealParams> params_heap;
+    RealHost* reals = &real_inline;
+    RealParams* params = &params_inline;
+    bool any_transfer = false, any_walk = false;
     cudaStream_t stream = nullptr;
-    // derived (Sec. 3)
-    double D_RW = 0, D_MT = 0, sigma = 0, h2 = 0, psi = 0, psi2 = 0, kernel_norm = 0;
-    bool transfer_enabled = false;
-    Box box{};
-    Grid grid{};
-    PairParams pp{};
     int64_t n = 0, cap = 0;
     int64_t n_cells = 0, n_cells_pad = 0;
     int n_corners = 0;
-    double band_eta = 0.0;
-    uint64_t step = 0;
+    uint64_t step = 0;                // host mirror of the device step counter
     bool have_row_sums = false;
+    bool have_particles = false;
     // state, double-buffered (cur = index into the pair)
     DevBuf<double> pos[2], mass[2];
-    DevBuf<uint32_t> id[2];
+    DevBuf<uint32_t> id[2], rid[2];
     int cur = 0;
     // per-step scratch
     DevBuf<uint32_t> key, perm, cell, count, start, tile_sums;
     DevBuf<float4> rec;
     DevBuf<float2> corners;
+    DevBuf<int> corner_first;
+    DevBuf<uint32_t> id_first;
+    DevBuf<RealParams> params_dev;
     DevBuf<double> r64;
     DevBuf<float2> msplit;
     DevBuf<double> out_tmp;
     DevBuf<double> exp_table;
     DevBuf<uint32_t> status;
-    DevBuf<unsigned long long> pair_counter;
+    DevBuf<unsigned long long> pair_counter, step_dev;
     DevBuf<unsigned long long> emit_counter;
     DevBuf<uint32_t> emit_i, emit_j;
+    // captured two-step graph (valid for `graph_cur`, `graph_flags`)
+    cudaGraphExec_t graph = nullptr;
+    int graph_cur = -1, graph_flags = -1;
+    cudaStream_t capture_stream = nullptr;
     // per-kernel timing
     bool timing = false;
     struct PendingEvent { const char* name; cudaEvent_t a, b; };
@@ -175,6 +201,13 @@ int fold_timing(mtpt_handle* h) {
     return MTPT_OK;
 }
 
+void drop_graph(mtpt_handle* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_cur = -1;
+    h->graph_flags = -1;
+}
+
 int validate_params(const mtpt_params* p) {
     if (!p) return MTPT_ERR_INVALID_ARG;
     if (p->dim < 1 || p->dim > kMaxDim) return MTPT_ERR_INVALID_ARG;
@@ -192,24 +225,6 @@ int validate_params(const mtpt_params* p) {
     return MTPT_OK;
 }
 
-// Sec. 3: D_RW = kappa D, D_MT = (1 - kappa) D, walk scale sqrt(2 D_RW dt),
-// h^2 = 2 D_MT dt / beta, psi = lambda sqrt(4 D_MT dt / beta).
-void derive(mtpt_handle* h) {
-    const mtpt_params& p = h->prm;
-    h->D_RW = p.kappa * p.D;
-    h->D_MT = (1.0 - p.kappa) * p.D;
-    h->sigma = std::sqrt(2.0 * h->D_RW * p.dt);
-    h->h2 = 2.0 * h->D_MT * p.dt / p.beta;
-    h->psi = p.lambda * std::sqrt(4.0 * h->D_MT * p.dt / p.beta);
-    h->psi2 = h->psi * h->psi;
-    h->kernel_norm = h->h2 > 0.0 ? std::pow(2.0 * M_PI * h->h2, -0.5 * p.dim) : 0.0;
-    h->transfer_enabled = h->h2 > 0.0;
-    for (int a = 0; a < 3; ++a) {
-        h->box.lo[a] = a < p.dim ? p.lo[a] : 0.0;
-        h->box.hi[a] = a < p.dim ? p.hi[a] : 0.0;
-    }
-}
-
 // Host image of the kernels' order key (int64 order of binary64 values).
 long long host_order_key(double x) {
     long long b;
@@ -217,35 +232,58 @@ long long host_order_key(double x) {
     return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 
-// Cell grid: width >= psi on every axis (slightly above, so a pair at
-// distance psi never spans two cell boundaries under rounding), with the
-// total cell count capped near 4 n so sparse boxes do not allocate huge
-// empty grids (cells then just get wider, which stays correct).
+// Sec. 3: D_RW = kappa D, D_MT = (1 - kappa) D, walk scale sqrt(2 D_RW dt),
+// h^2 = 2 D_MT dt / beta, psi = lambda sqrt(4 D_MT dt / beta).
+void derive(RealHost& R, RealParams& P) {
+    const mtpt_params& p = R.prm;
+    R.D_RW = p.kappa * p.D;
+    R.D_MT = (1.0 - p.kappa) * p.D;
+    P.sigma = std::sqrt(2.0 * R.D_RW * p.dt);
+    R.h2 = 2.0 * R.D_MT * p.dt / p.beta;
+    R.psi = p.lambda * std::sqrt(4.0 * R.D_MT * p.dt / p.beta);
+    R.psi2 = R.psi * R.psi;
+    P.kernel_norm = R.h2 > 0.0 ? std::pow(2.0 * M_PI * R.h2, -0.5 * p.dim) : 0.0;
+    P.transfer = R.h2 > 0.0 ? 1 : 0;
+    P.walk = P.sigma > 0.0 ? 1 : 0;
+    P.seed = p.seed;
+    for (int a = 0; a < 3; ++a) {
+        P.box.lo[a] = a < p.dim ? p.lo[a] : 0.0;
+        P.box.hi[a] = a < p.dim ? p.hi[a] : 0.0;
+        P.box.lo_key[a] = host_order_key(P.box.lo[a]);
+        P.box.hi_key[a] = host_order_key(P.box.hi[a]);
+    }
+}
+
+// Cell grid of one realisation: width >= psi on every axis (slightly above,
+// so a pair at distance psi never spans two cell boundaries under rounding),
+// with the cell count capped near 4 n so sparse boxes do not allocate huge
+// empty grids (cells then just get wider, which stays correct).  A
+// realisation without mass transfer gets a single cell.
 //
 // The cell index of a walked particle is computed in binary32 when its error
 // is small: with u = 2^-24, the binary32 evaluation of (x - lo) / w is within
 // dc = 3 u (B + L) / psi cells of the exact one (B = max(|lo|, |hi|)), so
 // cells of width w >= psi / (1 - 2 dc) keep every pair within psi in adjacent
 // cells.  Boxes where dc > 1e-3 (very many cells per axis) use binary64.
-int setup_grid(mtpt_handle* h) {
-    const mtpt_params& p = h->prm;
-    Grid& g = h->grid;
+int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base) {
+    const mtpt_params& p = R.prm;
+    Grid& g = P.g;
     const double u = std::ldexp(1.0, -24);
     double dc = 0.0;
-    for (int a = 0; a < p.dim && h->psi > 0.0; ++a) {
+    for (int a = 0; a < p.dim && R.psi > 0.0; ++a) {
         const double B = std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a]));
-        dc = std::max(dc, 3.0 * u * (B + (p.hi[a] - p.lo[a])) / h->psi);
+        dc = std::max(dc, 3.0 * u * (B + (p.hi[a] - p.lo[a])) / R.psi);
     }
-    g.cell_f32 = (h->transfer_enabled && dc <= 1e-3) ? 1 : 0;
+    g.cell_f32 = (P.transfer && dc <= 1e-3) ? 1 : 0;
     const double widen = g.cell_f32 ? 1.0 / (1.0 - 2.0 * dc) : 1.0;
-    const double psi_eff = h->psi * widen * (1.0 + 1e-9);
+    const double psi_eff = R.psi * widen * (1.0 + 1e-9);
     double ncell[3] = {1, 1, 1};
     for (int a = 0; a < p.dim; ++a) {
         const double L = p.hi[a] - p.lo[a];
-        double k = h->transfer_enabled ? std::floor(L / psi_eff) : 1.0;
+        double k = P.transfer ? std::floor(L / psi_eff) : 1.0;
         ncell[a] = std::max(1.0, std::min(k, double(1 << 30)));
     }
-    const double cap = std::max(4.0 * double(h->n) + 64.0, 64.0);
+    const double cap = std::max(4.0 * double(R.n) + 64.0, 64.0);
     double total = ncell[0] * ncell[1] * ncell[2];
     for (int guard = 0; guard < 64 && total > cap; ++guard) {
         const double f = std::pow(cap / total, 1.0 / p.dim);
@@ -261,7 +299,7 @@ int setup_grid(mtpt_handle* h) {
     }
     if (total > 2.0e9) return MTPT_ERR_INVALID_ARG;
     double sum_w = 0.0, sum_b = 0.0;
-    int off = 0;
+    int off = corner_base;
     for (int a = 0; a < 3; ++a) {
         g.n[a] = int(ncell[a]);
         g.lo[a] = a < p.dim ? p.lo[a] : 0.0;
@@ -271,15 +309,15 @@ int setup_grid(mtpt_handle* h) {
         g.lo_f[a] = float(g.lo[a]);
         g.inv_w_f[a] = float(g.inv_w[a]);
         g.corner_off[a] = off;
-        off += (a < p.dim) ? g.n[a] : 0;
-        if (a < p.dim && h->psi > 0.0) {
-            sum_w += g.w[a] / h->psi;
-            sum_b += (std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a])) + g.w[a]) / h->psi;
+        off += (a < p.dim && P.transfer) ? g.n[a] : 0;
+        if (a < p.dim && R.psi > 0.0) {
+            sum_w += g.w[a] / R.psi;
+            sum_b += (std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a])) + g.w[a]) / R.psi;
         }
     }
-    h->n_corners = off;
-    h->n_cells = int64_t(total);
-    h->n_cells_pad = ((h->n_cells + 1 + kScanTile - 1) / kScanTile) * kScanTile;
+    R.n_corners = off - corner_base;
+    R.n_cells = int64_t(total);
+    P.cell_base = uint32_t(cell_base);
 
     // Pair-test band.  Each binary32 cell offset is within 2u w (1 + dc) +
     // 2^-46 B of the exact offset; the binary32 difference
@@ -289,13 +327,13 @@ int setup_grid(mtpt_handle* h) {
     //   |d2f - d2| <= psi^2 (u (3 + 14 (1 + dc) sum_a w_a / psi) + 2^-43 sum_a B_a / psi)
     // for every candidate within reach of the cutoff.  Twice that bound is the
     // band half-width eta.
-    PairParams& pp = h->pp;
+    PairParams& pp = P.pp;
     const double eta = 2.0 * (u * (3.0 + 14.0 * (1.0 + dc) * sum_w) + std::ldexp(sum_b, -43)) + 1e-14;
-    pp.psi2 = h->psi2;
-    pp.band_lo = std::nextafter(float(h->psi2 * (1.0 - eta)), 0.0f);
-    pp.band_hi = std::nextafter(float(h->psi2 * (1.0 + eta)), INFINITY);
-    h->band_eta = eta;
-    pp.a = h->h2 > 0.0 ? 1.0 / (2.0 * h->h2) : 0.0;
+    R.band_eta = eta;
+    pp.psi2 = R.psi2;
+    pp.band_lo = std::nextafter(float(R.psi2 * (1.0 - eta)), 0.0f);
+    pp.band_hi = std::nextafter(float(R.psi2 * (1.0 + eta)), INFINITY);
+    pp.a = R.h2 > 0.0 ? 1.0 / (2.0 * R.h2) : 0.0;
     pp.a_log2e = float(pp.a * 1.4426950408889634);
     pp.beta = p.beta;
     // ln 2 = ln2_hi + ln2_lo (leading and trailing binary64 parts)
@@ -303,46 +341,65 @@ int setup_grid(mtpt_handle* h) {
     pp.ec.inv_step = 64.0 / ln2_hi;
     pp.ec.step_hi = ln2_hi / 64.0;
     pp.ec.step_lo = ln2_lo / 64.0;
-    for (int a = 0; a < 3; ++a) {
-        h->box.lo_key[a] = host_order_key(h->box.lo[a]);
-        h->box.hi_key[a] = host_order_key(h->box.hi[a]);
-    }
     return MTPT_OK;
 }
 
-// Corner table of every axis on the device: corner = lo + c w (binary64),
-// stored as its binary32 head and tail.
-int build_corners(mtpt_handle* h) {
-    if (!h->transfer_enabled || h->n_corners == 0) return MTPT_OK;
-    k_corners<<<grid_for(h->n_corners), kBlock, 0, h->stream>>>(h->n_corners, h->prm.dim, h->grid,
+// Grids of every realisation, laid out one after another in the global cell
+// list and the corner table.
+int setup_grids(mtpt_handle* h) {
+    int64_t cell_base = 0;
+    int corner_base = 0;
+    h->any_transfer = false;
+    h->any_walk = false;
+    for (int k = 0; k < h->nreal; ++k) {
+        MTPT_TRY(setup_grid(h->reals[k], h->params[k], cell_base, corner_base));
+        cell_base += h->reals[k].n_cells;
+        corner_base += h->reals[k].n_corners;
+        h->any_transfer |= h->params[k].transfer != 0;
+        h->any_walk |= h->params[k].walk != 0;
+    }
+    if (cell_base > int64_t(0xffffffffLL) - kScanTile) return MTPT_ERR_INVALID_ARG;
+    h->n_cells = cell_base;
+    h->n_corners = corner_base;
+    h->n_cells_pad = ((h->n_cells + 1 + kScanTile - 1) / kScanTile) * kScanTile;
+    return MTPT_OK;
+}
+
+double* exp_table_host() {
+    static double table[64];
+    static std::once_flag once;
+    std::call_once(once, []() {
+        for (int j = 0; j < 64; ++j) table[j] = double(exp2l(-static_cast<long double>(j) / 64.0L));
+    });
+    return table;
+}
+
+// Corner tables of every transferring realisation.
+int build_corners(mtpt_handle* h, const RealParams* params_dev, const int* first_dev) {
+    if (!h->any_transfer || h->n_corners == 0) return MTPT_OK;
+    k_corners<<<grid_for(h->n_corners), kBlock, 0, h->stream>>>(h->n_corners, h->nreal, h->dim,
+                                                               params_dev, first_dev,
                                                                h->corners.p);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
 
-int upload_exp_table(mtpt_handle* h) {
-    MTPT_TRY(h->exp_table.ensure(64));
-    double t[64];
-    for (int j = 0; j < 64; ++j) t[j] = double(exp2l(-static_cast<long double>(j) / 64.0L));
-    MTPT_CUDA_TRY(cudaMemcpyAsync(h->exp_table.p, t, sizeof(t), cudaMemcpyHostToDevice, h->stream));
-    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return MTPT_OK;
-}
-
 int ensure_capacity(mtpt_handle* h, int64_t n) {
-    const int d = h->prm.dim;
+    const int d = h->dim;
     const int64_t cap = std::max<int64_t>(n, 1);
     if (cap > h->cap) {
+        drop_graph(h);
         for (int b = 0; b < 2; ++b) {
             MTPT_TRY(h->pos[b].ensure(size_t(d) * cap));
             MTPT_TRY(h->mass[b].ensure(cap));
             MTPT_TRY(h->id[b].ensure(cap));
+            if (h->batch) MTPT_TRY(h->rid[b].ensure(cap));
         }
         MTPT_TRY(h->key.ensure(cap));
         MTPT_TRY(h->perm.ensure(cap));
         MTPT_TRY(h->cell.ensure(cap));
         MTPT_TRY(h->rec.ensure(cap));
-        if (h->prm.precision == MTPT_FP64) {
+        if (h->precision == MTPT_FP64) {
             MTPT_TRY(h->r64.ensure(cap));
         } else {
             MTPT_TRY(h->msplit.ensure(cap));
@@ -351,20 +408,49 @@ int ensure_capacity(mtpt_handle* h, int64_t n) {
     }
     MTPT_TRY(h->status.ensure(1));
     MTPT_TRY(h->pair_counter.ensure(1));
+    MTPT_TRY(h->step_dev.ensure(1));
     return MTPT_OK;
 }
 
 int ensure_cells(mtpt_handle* h) {
     const size_t padded = size_t(h->n_cells_pad);
     if (padded > h->count.count) {
+        drop_graph(h);
         MTPT_TRY(h->count.ensure(padded));
         MTPT_TRY(h->start.ensure(padded));
         MTPT_TRY(h->tile_sums.ensure(padded / kScanTile));
     }
+    if (size_t(std::max(h->n_corners, 1)) > h->corners.count) drop_graph(h);
     MTPT_TRY(h->corners.ensure(size_t(std::max(h->n_corners, 1))));
-    MTPT_TRY(build_corners(h));
     // counts start (and, after each scatter, end) at zero
     MTPT_CUDA_TRY(cudaMemsetAsync(h->count.p, 0, padded * sizeof(uint32_t), h->stream));
+    return MTPT_OK;
+}
+
+// Uploads the realisation table and the corner and particle offsets, and
+// builds the corner tables.
+int upload_tables(mtpt_handle* h) {
+    const int nr = h->nreal;
+    MTPT_TRY(h->params_dev.ensure(size_t(nr)));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h->params_dev.p, h->params, size_t(nr) * sizeof(RealParams),
+                                  cudaMemcpyHostToDevice, h->stream));
+    std::vector<int> cf(size_t(nr) + 1);
+    std::vector<uint32_t> idf(size_t(nr) + 1);
+    for (int k = 0; k < nr; ++k) {
+        cf[size_t(k)] = h->params[k].g.corner_off[0];
+        idf[size_t(k)] = h->params[k].id_offset;
+    }
+    cf[size_t(nr)] = h->n_corners;
+    idf[size_t(nr)] = uint32_t(h->n);
+    MTPT_TRY(h->corner_first.ensure(size_t(nr) + 1));
+    MTPT_TRY(h->id_first.ensure(size_t(nr) + 1));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h->corner_first.p, cf.data(), cf.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, h->stream));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h->id_first.p, idf.data(), idf.size() * sizeof(uint32_t),
+                                  cudaMemcpyHostToDevice, h->stream));
+    MTPT_TRY(build_corners(h, h->params_dev.p, h->corner_first.p));
+    // the host vectors are pageable: wait before they go out of scope
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return MTPT_OK;
 }
 
@@ -376,25 +462,54 @@ int read_status(mtpt_handle* h) {
     return MTPT_OK;
 }
 
-template <int DIM>
+template <class View>
+View make_view(const mtpt_handle* h, int input_buf, int sorted_buf);
+
+template <>
+SingleView make_view<SingleView>(const mtpt_handle* h, int, int) {
+    SingleView v;
+    v.p = h->params[0];
+    return v;
+}
+
+template <>
+BatchView make_view<BatchView>(const mtpt_handle* h, int input_buf, int sorted_buf) {
+    BatchView v;
+    v.tbl = h->params_dev.p;
+    v.rid_input = h->rid[input_buf].p;
+    v.rid_sorted = h->rid[sorted_buf].p;
+    return v;
+}
+
+// Enqueues one time step (or part of it, per `flags`).  The step counter
+// lives on the device and advances inside the step, so the same launches can
+// be captured once and replayed.
+template <int DIM, class View>
 int launch_step(mtpt_handle* h, int flags) {
     const int n = int(h->n);
     if (n == 0) return MTPT_OK;
     const int64_t stride = h->cap;
     const int blocks = grid_for(n);
     cudaStream_t st = h->stream;
-    const bool walk = (flags & MTPT_DO_WALK) && h->sigma > 0.0;
-    const bool transfer = (flags & MTPT_DO_TRANSFER) && h->transfer_enabled;
+    const bool walk = (flags & MTPT_DO_WALK) && h->any_walk;
+    const bool transfer = (flags & MTPT_DO_TRANSFER) && h->any_transfer;
     const int c = h->cur, o = 1 - h->cur;
+    const View vin = make_view<View>(h, c, c);
     if (walk || transfer) {
         MTPT_TIMED(h, "walk_key");
-        k_walk_key<DIM><<<blocks, kBlock, 0, st>>>(
-            n, stride, h->pos[c].p, h->id[c].p, h->prm.seed, h->step, h->sigma, walk ? 1 : 0,
-            transfer ? 1 : 0, h->box, h->grid, h->key.p, h->count.p, h->status.p);
+        k_walk_key<DIM, View><<<blocks, kBlock, 0, st>>>(
+            n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0, transfer ? 1 : 0,
+            vin, h->key.p, h->count.p, h->status.p);
         MTPT_CUDA_TRY(cudaGetLastError());
     }
-    if (flags & MTPT_DO_WALK) h->step += 1;
-    if (!transfer) return MTPT_OK;
+    const bool advance = (flags & MTPT_DO_WALK) != 0;
+    if (!transfer) {
+        if (advance) {
+            k_advance_step<<<1, 1, 0, st>>>(h->step_dev.p);
+            MTPT_CUDA_TRY(cudaGetLastError());
+        }
+        return MTPT_OK;
+    }
 
     const int ntiles = int(h->n_cells_pad / kScanTile);
     const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
@@ -404,7 +519,8 @@ int launch_step(mtpt_handle* h, int flags) {
     }
     {
         MTPT_TIMED(h, "scan_tile_offsets");
-        k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(h->tile_sums.p, ntiles);
+        k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(h->tile_sums.p, ntiles, h->step_dev.p,
+                                                        advance ? 1 : 0);
     }
     {
         MTPT_TIMED(h, "scan_apply");
@@ -415,44 +531,48 @@ int launch_step(mtpt_handle* h, int flags) {
         MTPT_TIMED(h, "scatter");
         k_scatter<<<blocks, kBlock, 0, st>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
     }
-    const bool split = h->prm.precision == MTPT_FP32W;
-    if (split) {
+    const bool split = h->precision == MTPT_FP32W;
+    uint32_t* rid_out = View::kBatch ? h->rid[o].p : nullptr;
+    {
         MTPT_TIMED(h, "gather");
-        k_gather<DIM, true><<<blocks, kBlock, 0, st>>>(
-            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
-            h->corners.p, h->grid);
-    } else {
-        MTPT_TIMED(h, "gather");
-        k_gather<DIM, false><<<blocks, kBlock, 0, st>>>(
-            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr,
-            h->corners.p, h->grid);
+        if (split)
+            k_gather<DIM, true, View><<<blocks, kBlock, 0, st>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
+                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
+                h->msplit.p, h->corners.p, rid_out, vin);
+        else
+            k_gather<DIM, false, View><<<blocks, kBlock, 0, st>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
+                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
+                nullptr, h->corners.p, rid_out, vin);
     }
     MTPT_CUDA_TRY(cudaGetLastError());
     // state now lives in buffer o (cell order); masses are updated into c
+    const View vs = make_view<View>(h, o, o);
     const double* pos_s = h->pos[o].p;
     if (!split) {
         {
-        MTPT_TIMED(h, "rowsum_f64");
-        k_rowsum_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
-                                                     h->start.p, h->exp_table.p, h->grid, h->pp,
-                                                     h->r64.p, h->pair_counter.p);
+            MTPT_TIMED(h, "rowsum_f64");
+            k_rowsum_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
+                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
+                h->pair_counter.p);
         }
         MTPT_TIMED(h, "exchange_f64");
-        k_exchange_f64<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
-                                                       h->start.p, h->exp_table.p, h->grid, h->pp,
-                                                       h->r64.p, h->mass[o].p, h->mass[c].p);
+        k_exchange_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
+            h->mass[o].p, h->mass[c].p);
     } else {
         {
-        MTPT_TIMED(h, "rowsum_f32");
-        k_rowsum_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
-                                                     h->start.p, h->grid, h->pp, h->pair_counter.p);
+            MTPT_TIMED(h, "rowsum_f32");
+            k_rowsum_f32<DIM, View><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p,
+                                                               h->cell.p, h->start.p, vs,
+                                                               h->pair_counter.p);
         }
         MTPT_TIMED(h, "exchange_f32");
-        k_exchange_f32<DIM><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p, h->cell.p,
-                                                       h->start.p, h->grid, h->pp, h->msplit.p,
-                                                       h->mass[o].p, h->mass[c].p);
+        k_exchange_f32<DIM, View><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p,
+                                                             h->cell.p, h->start.p, vs,
+                                                             h->msplit.p, h->mass[o].p,
+                                                             h->mass[c].p);
     }
     MTPT_CUDA_TRY(cudaGetLastError());
     // positions and ids live in o; the updated masses were written into c's
@@ -464,26 +584,87 @@ int launch_step(mtpt_handle* h, int flags) {
 }
 
 int dispatch_step(mtpt_handle* h, int flags) {
-    switch (h->prm.dim) {
-        case 1: return launch_step<1>(h, flags);
-        case 2: return launch_step<2>(h, flags);
-        default: return launch_step<3>(h, flags);
+    if (h->batch) {
+        switch (h->dim) {
+            case 1: return launch_step<1, BatchView>(h, flags);
+            case 2: return launch_step<2, BatchView>(h, flags);
+            default: return launch_step<3, BatchView>(h, flags);
+        }
+    }
+    switch (h->dim) {
+        case 1: return launch_step<1, SingleView>(h, flags);
+        case 2: return launch_step<2, SingleView>(h, flags);
+        default: return launch_step<3, SingleView>(h, flags);
     }
 }
 
+// Captures two consecutive steps (the buffer pairs swap every step, so two
+// steps return them to the starting arrangement) into an executable graph.
+int capture_two_steps(mtpt_handle* h, int flags) {
+    drop_graph(h);
+    if (!h->capture_stream)
+        MTPT_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    const cudaStream_t user = h->stream;
+    const int cur0 = h->cur;
+    const bool rows0 = h->have_row_sums;
+    DevBuf<double> mass0 = h->mass[0], mass1 = h->mass[1];
+    h->stream = h->capture_stream;
+    MTPT_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = dispatch_step(h, flags);
+    if (rc == MTPT_OK) rc = dispatch_step(h, flags);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+    // capture only recorded the launches: restore the host bookkeeping
+    h->stream = user;
+    h->cur = cur0;
+    h->have_row_sums = rows0;
+    h->mass[0] = mass0;
+    h->mass[1] = mass1;
+    if (ec != cudaSuccess || rc != MTPT_OK || !graph) {
+        (void)cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return rc != MTPT_OK ? rc : MTPT_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        (void)cudaGetLastError();
+        return MTPT_ERR_CUDA;
+    }
+    h->graph = exec;
+    h->graph_cur = cur0;
+    h->graph_flags = flags;
+    return MTPT_OK;
+}
+
+int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {
+    const bool use_graph = nsteps >= kGraphMinSteps && !h->timing && h->n > 0;
+    int64_t done = 0;
+    if (use_graph) {
+        if (!h->graph || h->graph_cur != h->cur || h->graph_flags != flags)
+            MTPT_TRY(capture_two_steps(h, flags));
+        for (; done + 2 <= nsteps; done += 2) MTPT_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
+        // an even number of steps leaves the buffers where they started; a
+        // transfer step leaves row sums behind
+        const bool transfer = (flags & MTPT_DO_TRANSFER) && h->any_transfer;
+        if (transfer && done > 0) h->have_row_sums = true;
+    }
+    for (; done < nsteps; ++done) MTPT_TRY(dispatch_step(h, flags));
+    if (flags & MTPT_DO_WALK) h->step += uint64_t(nsteps);
+    return MTPT_OK;
+}
+
 int ensure_out_tmp(mtpt_handle* h) {
-    return h->out_tmp.ensure(size_t(h->prm.dim) * std::max<int64_t>(h->n, 1));
+    return h->out_tmp.ensure(size_t(h->dim) * std::max<int64_t>(h->n, 1));
 }
 
 // Copy `naxes` arrays of the current state (stride cap, cell order) into
-// `out_dev` (stride n, input order), multiplied by `scale`.
-template <typename T>
-int unpermute_to(mtpt_handle* h, const T* src, int naxes, double scale, double* out_dev,
-                 int src_step = 1) {
+// `out_dev` (stride n, input order).
+int unpermute_to(mtpt_handle* h, const double* src, int naxes, double* out_dev) {
     if (h->n == 0) return MTPT_OK;
-    k_unpermute<T><<<grid_for(h->n), kBlock, 0, h->stream>>>(int(h->n), h->cap, naxes,
-                                                            h->id[h->cur].p, src, src_step, scale,
-                                                            out_dev);
+    k_unpermute<double><<<grid_for(h->n), kBlock, 0, h->stream>>>(
+        int(h->n), h->cap, naxes, h->id[h->cur].p, src, 1, 1.0, out_dev);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -495,16 +676,42 @@ int copy_out_host(mtpt_handle* h, int naxes, double* out) {
     return read_status(h);
 }
 
-int load_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass,
+int set_step_dev(mtpt_handle* h, uint64_t step) {
+    k_set_step<<<1, 1, 0, h->stream>>>(h->step_dev.p, (unsigned long long)step);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    h->step = step;
+    return MTPT_OK;
+}
+
+// Loads particles (counts[k] per realisation, concatenated) from host or
+// device buffers.
+int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, const double* mass,
                    cudaMemcpyKind kind) {
-    const int d = h->prm.dim;
-    if (n < 0 || n > int64_t(0x7fffffff) - kBlock) return MTPT_ERR_INVALID_ARG;
+    const int d = h->dim;
+    int64_t n = 0;
+    for (int k = 0; k < h->nreal; ++k) {
+        if (counts[k] < 0) return MTPT_ERR_INVALID_ARG;
+        n += counts[k];
+    }
+    if (n > int64_t(0x7fffffff) - kBlock) return MTPT_ERR_INVALID_ARG;
     if (n > 0 && (!pos || !mass)) return MTPT_ERR_INVALID_ARG;
+    int64_t off = 0;
+    for (int k = 0; k < h->nreal; ++k) {
+        h->reals[k].n = counts[k];
+        h->params[k].id_offset = uint32_t(off);
+        off += counts[k];
+    }
     h->n = n;
     MTPT_TRY(ensure_capacity(h, n));
-    MTPT_TRY(setup_grid(h));
-    if (h->transfer_enabled) MTPT_TRY(ensure_cells(h));
-    if (!h->exp_table.p) MTPT_TRY(upload_exp_table(h));
+    MTPT_TRY(setup_grids(h));
+    if (h->any_transfer) MTPT_TRY(ensure_cells(h));
+    drop_graph(h);
+    if (!h->exp_table.p) {
+        MTPT_TRY(h->exp_table.ensure(64));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->exp_table.p, exp_table_host(), 64 * sizeof(double),
+                                      cudaMemcpyHostToDevice, h->stream));
+    }
+    MTPT_TRY(upload_tables(h));
     h->cur = 0;
     if (n > 0) {
         MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[0].p, size_t(h->cap) * sizeof(double), pos,
@@ -513,11 +720,164 @@ int load_particles(mtpt_handle* h, int64_t n, const double* pos, const double* m
         MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[0].p, mass, size_t(n) * sizeof(double), kind, h->stream));
         k_iota<<<grid_for(n), kBlock, 0, h->stream>>>(int(n), h->id[0].p);
         MTPT_CUDA_TRY(cudaGetLastError());
+        if (h->batch) {
+            k_fill_rid<<<grid_for(n), kBlock, 0, h->stream>>>(int(n), h->nreal, h->id_first.p,
+                                                             h->rid[0].p);
+            MTPT_CUDA_TRY(cudaGetLastError());
+        }
     }
     MTPT_CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(uint32_t), h->stream));
     MTPT_CUDA_TRY(cudaMemsetAsync(h->pair_counter.p, 0, sizeof(unsigned long long), h->stream));
-    h->step = 0;
+    MTPT_TRY(set_step_dev(h, 0));
     h->have_row_sums = false;
+    h->have_particles = true;
+    return MTPT_OK;
+}
+
+int check_host_particles(const mtpt_handle* h, const int64_t* counts, const double* pos,
+                         const double* mass) {
+    int64_t n = 0;
+    for (int k = 0; k < h->nreal; ++k) {
+        if (counts[k] < 0) return MTPT_ERR_INVALID_ARG;
+        n += counts[k];
+    }
+    if (n > 0 && (!pos || !mass)) return MTPT_ERR_INVALID_ARG;
+    int64_t off = 0;
+    for (int k = 0; k < h->nreal; ++k) {
+        const mtpt_params& p = h->reals[k].prm;
+        for (int a = 0; a < h->dim; ++a) {
+            const double* x = pos + size_t(a) * size_t(n) + size_t(off);
+            for (int64_t i = 0; i < counts[k]; ++i)
+                if (!(x[i] >= p.lo[a] && x[i] <= p.hi[a])) return MTPT_ERR_OUT_OF_DOMAIN;
+        }
+        off += counts[k];
+    }
+    const double mass_limit = h->precision == MTPT_FP32W ? 1e30 : HUGE_VAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(mass[i]) || std::fabs(mass[i]) > mass_limit) return MTPT_ERR_INVALID_ARG;
+    return MTPT_OK;
+}
+
+int create_common(const mtpt_params* params, int count, bool batch, mtpt_handle** out) {
+    if (!out) return MTPT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params || count < 1 || count > (1 << 20)) return MTPT_ERR_INVALID_ARG;
+    for (int k = 0; k < count; ++k) {
+        MTPT_TRY(validate_params(params + k));
+        if (params[k].dim != params[0].dim || params[k].precision != params[0].precision)
+            return MTPT_ERR_INVALID_ARG;
+    }
+    mtpt_handle* h = new (std::nothrow) mtpt_handle();
+    if (!h) return MTPT_ERR_NO_MEMORY;
+    h->dim = params[0].dim;
+    h->precision = params[0].precision;
+    h->batch = batch;
+    h->nreal = count;
+    if (count > 1) {
+        try {
+            h->real_heap.resize(size_t(count));
+            h->params_heap.resize(size_t(count));
+        } catch (...) {
+            delete h;
+            return MTPT_ERR_NO_MEMORY;
+        }
+        h->reals = h->real_heap.data();
+        h->params = h->params_heap.data();
+    }
+    for (int k = 0; k < count; ++k) {
+        h->reals[k].prm = params[k];
+        derive(h->reals[k], h->params[k]);
+    }
+    *out = h;
+    return MTPT_OK;
+}
+
+void fill_info(const mtpt_handle* h, int k, mtpt_info* out) {
+    const RealHost& R = h->reals[k];
+    const RealParams& P = h->params[k];
+    out->D_RW = R.D_RW;
+    out->D_MT = R.D_MT;
+    out->sigma = P.sigma;
+    out->h2 = R.h2;
+    out->psi = R.psi;
+    out->psi2 = R.psi2;
+    out->kernel_norm = P.kernel_norm;
+    for (int a = 0; a < 3; ++a) {
+        out->cells[a] = P.g.n[a] ? P.g.n[a] : 1;
+        out->cell_width[a] = P.g.w[a];
+    }
+}
+
+template <int DIM, class View>
+int launch_emit(mtpt_handle* h, int64_t cap) {
+    const int n = int(h->n);
+    const int blocks = grid_for(n);
+    const int64_t stride = h->cap;
+    const int c = h->cur, o = 1 - h->cur;
+    const View vin = make_view<View>(h, c, c);
+    k_walk_key<DIM, View><<<blocks, kBlock, 0, h->stream>>>(n, stride, h->pos[c].p, h->id[c].p,
+                                                            h->step_dev.p, 0, 1, vin, h->key.p,
+                                                            h->count.p, h->status.p);
+    const int ntiles = int(h->n_cells_pad / kScanTile);
+    const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
+    k_scan_tile_sums<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p);
+    k_scan_tile_offsets<<<1, kScanThreads, 0, h->stream>>>(h->tile_sums.p, ntiles, h->step_dev.p, 0);
+    k_scan_apply<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p,
+                                                         reinterpret_cast<uint4*>(h->start.p));
+    k_scatter<<<blocks, kBlock, 0, h->stream>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
+    uint32_t* rid_out = View::kBatch ? h->rid[o].p : nullptr;
+    if (h->precision == MTPT_FP32W)
+        k_gather<DIM, true, View><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
+            h->corners.p, rid_out, vin);
+    else
+        k_gather<DIM, false, View><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr, h->corners.p,
+            rid_out, vin);
+    const View vs = make_view<View>(h, o, o);
+    k_emit_pairs<DIM, View><<<blocks, kBlock, 0, h->stream>>>(
+        n, stride, h->pos[o].p, h->rec.p, h->cell.p, h->start.p, h->id[o].p, vs,
+        (unsigned long long)cap, h->emit_counter.p, h->emit_i.p, h->emit_j.p);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    // the gathered copy in o is the same state in cell order: make it current
+    h->cur = o;
+    h->have_row_sums = false;
+    return MTPT_OK;
+}
+
+int dispatch_emit(mtpt_handle* h, int64_t cap) {
+    if (h->batch) {
+        switch (h->dim) {
+            case 1: return launch_emit<1, BatchView>(h, cap);
+            case 2: return launch_emit<2, BatchView>(h, cap);
+            default: return launch_emit<3, BatchView>(h, cap);
+        }
+    }
+    switch (h->dim) {
+        case 1: return launch_emit<1, SingleView>(h, cap);
+        case 2: return launch_emit<2, SingleView>(h, cap);
+        default: return launch_emit<3, SingleView>(h, cap);
+    }
+}
+
+template <class View, class T>
+int launch_row_sums_out(mtpt_handle* h, const T* src, int src_step) {
+    const View v = make_view<View>(h, h->cur, h->cur);
+    k_row_sums_out<T, View><<<grid_for(h->n), kBlock, 0, h->stream>>>(
+        int(h->n), h->id[h->cur].p, src, src_step, v, h->out_tmp.p);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
+}
+
+template <int DIM, class View>
+int launch_check_domain(mtpt_handle* h) {
+    const View v = make_view<View>(h, 0, 0);
+    k_check_domain<DIM, View><<<grid_for(h->n), kBlock, 0, h->stream>>>(int(h->n), h->cap,
+                                                                      h->pos[0].p, v,
+                                                                      h->status.p);
+    MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
 
@@ -526,30 +886,30 @@ int load_particles(mtpt_handle* h, int64_t n, const double* pos, const double* m
 extern "C" {
 
 int mtpt_create(const mtpt_params* params, mtpt_handle** out) {
-    if (!out) return MTPT_ERR_INVALID_ARG;
-    *out = nullptr;
-    MTPT_TRY(validate_params(params));
-    mtpt_handle* h = new (std::nothrow) mtpt_handle();
-    if (!h) return MTPT_ERR_NO_MEMORY;
-    h->prm = *params;
-    derive(h);
-    *out = h;
-    return MTPT_OK;
+    return create_common(params, 1, false, out);
+}
+
+int mtpt_create_batch(const mtpt_params* params, int32_t count, mtpt_handle** out) {
+    return create_common(params, count, true, out);
 }
 
 int mtpt_destroy(mtpt_handle* h) {
     if (!h) return MTPT_OK;
     cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (int b = 0; b < 2; ++b) {
         h->pos[b].release();
         h->mass[b].release();
         h->id[b].release();
+        h->rid[b].release();
     }
     h->key.release(); h->perm.release(); h->cell.release(); h->count.release();
     h->start.release(); h->tile_sums.release(); h->rec.release(); h->corners.release();
+    h->corner_first.release(); h->id_first.release(); h->params_dev.release();
     h->r64.release(); h->msplit.release(); h->out_tmp.release(); h->exp_table.release();
-    h->status.release(); h->pair_counter.release(); h->emit_counter.release();
-    h->emit_i.release(); h->emit_j.release();
+    h->status.release(); h->pair_counter.release(); h->step_dev.release();
+    h->emit_counter.release(); h->emit_i.release(); h->emit_j.release();
     for (auto& pe : h->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
@@ -566,35 +926,41 @@ int mtpt_set_stream(mtpt_handle* h, void* stream) {
 }
 
 int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass) {
-    if (!h) return MTPT_ERR_INVALID_ARG;
+    if (!h || h->nreal != 1) return MTPT_ERR_INVALID_ARG;
     if (n < 0) return MTPT_ERR_INVALID_ARG;
-    if (n > 0 && (!pos || !mass)) return MTPT_ERR_INVALID_ARG;
-    const int d = h->prm.dim;
-    for (int a = 0; a < d; ++a) {
-        const double lo = h->prm.lo[a], hi = h->prm.hi[a];
-        const double* x = pos + size_t(a) * size_t(n);
-        for (int64_t i = 0; i < n; ++i)
-            if (!(x[i] >= lo && x[i] <= hi)) return MTPT_ERR_OUT_OF_DOMAIN;
-    }
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(mass[i])) return MTPT_ERR_INVALID_ARG;
-    MTPT_TRY(load_particles(h, n, pos, mass, cudaMemcpyHostToDevice));
+    MTPT_TRY(check_host_particles(h, &n, pos, mass));
+    MTPT_TRY(load_particles(h, &n, pos, mass, cudaMemcpyHostToDevice));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MTPT_OK;
+}
+
+int mtpt_set_particles_batch(mtpt_handle* h, const int64_t* counts, const double* pos,
+                             const double* mass) {
+    if (!h || !counts) return MTPT_ERR_INVALID_ARG;
+    MTPT_TRY(check_host_particles(h, counts, pos, mass));
+    MTPT_TRY(load_particles(h, counts, pos, mass, cudaMemcpyHostToDevice));
     MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return MTPT_OK;
 }
 
 int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
                               const double* mass_dev) {
-    if (!h) return MTPT_ERR_INVALID_ARG;
-    MTPT_TRY(load_particles(h, n, pos_dev, mass_dev, cudaMemcpyDeviceToDevice));
+    if (!h || h->nreal != 1 || n < 0) return MTPT_ERR_INVALID_ARG;
+    MTPT_TRY(load_particles(h, &n, pos_dev, mass_dev, cudaMemcpyDeviceToDevice));
     if (n > 0) {
-        const int blocks = grid_for(n);
-        switch (h->prm.dim) {
-            case 1: k_check_domain<1><<<blocks, kBlock, 0, h->stream>>>(int(n), h->cap, h->pos[0].p, h->box, h->status.p); break;
-            case 2: k_check_domain<2><<<blocks, kBlock, 0, h->stream>>>(int(n), h->cap, h->pos[0].p, h->box, h->status.p); break;
-            default: k_check_domain<3><<<blocks, kBlock, 0, h->stream>>>(int(n), h->cap, h->pos[0].p, h->box, h->status.p); break;
+        if (h->batch) {
+            switch (h->dim) {
+                case 1: MTPT_TRY((launch_check_domain<1, BatchView>(h))); break;
+                case 2: MTPT_TRY((launch_check_domain<2, BatchView>(h))); break;
+                default: MTPT_TRY((launch_check_domain<3, BatchView>(h))); break;
+            }
+        } else {
+            switch (h->dim) {
+                case 1: MTPT_TRY((launch_check_domain<1, SingleView>(h))); break;
+                case 2: MTPT_TRY((launch_check_domain<2, SingleView>(h))); break;
+                default: MTPT_TRY((launch_check_domain<3, SingleView>(h))); break;
+            }
         }
-        MTPT_CUDA_TRY(cudaGetLastError());
     }
     return MTPT_OK;
 }
@@ -602,9 +968,8 @@ int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
 int mtpt_step_ex(mtpt_handle* h, int64_t nsteps, int32_t flags) {
     if (!h || nsteps < 0) return MTPT_ERR_INVALID_ARG;
     if (flags & ~(MTPT_DO_WALK | MTPT_DO_TRANSFER)) return MTPT_ERR_INVALID_ARG;
-    if (!h->status.p) return MTPT_ERR_STATE;
-    for (int64_t s = 0; s < nsteps; ++s) MTPT_TRY(dispatch_step(h, flags));
-    return MTPT_OK;
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    return run_steps(h, nsteps, flags);
 }
 
 int mtpt_step(mtpt_handle* h, int64_t nsteps) {
@@ -613,99 +978,63 @@ int mtpt_step(mtpt_handle* h, int64_t nsteps) {
 
 int mtpt_get_masses_device(mtpt_handle* h, double* out_dev) {
     if (!h || (!out_dev && h->n > 0)) return MTPT_ERR_INVALID_ARG;
-    if (!h->status.p) return MTPT_ERR_STATE;
-    return unpermute_to<double>(h, h->mass[h->cur].p, 1, 1.0, out_dev);
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    return unpermute_to(h, h->mass[h->cur].p, 1, out_dev);
 }
 
 int mtpt_get_masses(mtpt_handle* h, double* out) {
     if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
-    if (!h->status.p) return MTPT_ERR_STATE;
+    if (!h->have_particles) return MTPT_ERR_STATE;
     MTPT_TRY(ensure_out_tmp(h));
-    MTPT_TRY(unpermute_to<double>(h, h->mass[h->cur].p, 1, 1.0, h->out_tmp.p));
+    MTPT_TRY(unpermute_to(h, h->mass[h->cur].p, 1, h->out_tmp.p));
     return copy_out_host(h, 1, out);
 }
 
 int mtpt_get_positions_device(mtpt_handle* h, double* out_dev) {
     if (!h || (!out_dev && h->n > 0)) return MTPT_ERR_INVALID_ARG;
-    if (!h->status.p) return MTPT_ERR_STATE;
-    return unpermute_to<double>(h, h->pos[h->cur].p, h->prm.dim, 1.0, out_dev);
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    return unpermute_to(h, h->pos[h->cur].p, h->dim, out_dev);
 }
 
 int mtpt_get_positions(mtpt_handle* h, double* out) {
     if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
-    if (!h->status.p) return MTPT_ERR_STATE;
+    if (!h->have_particles) return MTPT_ERR_STATE;
     MTPT_TRY(ensure_out_tmp(h));
-    MTPT_TRY(unpermute_to<double>(h, h->pos[h->cur].p, h->prm.dim, 1.0, h->out_tmp.p));
-    return copy_out_host(h, h->prm.dim, out);
+    MTPT_TRY(unpermute_to(h, h->pos[h->cur].p, h->dim, h->out_tmp.p));
+    return copy_out_host(h, h->dim, out);
 }
 
 int mtpt_get_row_sums(mtpt_handle* h, double* out) {
     if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
-    if (!h->status.p || !h->have_row_sums) return MTPT_ERR_STATE;
+    if (!h->have_particles || !h->have_row_sums) return MTPT_ERR_STATE;
     MTPT_TRY(ensure_out_tmp(h));
-    if (h->prm.precision == MTPT_FP64)
-        MTPT_TRY(unpermute_to<double>(h, h->r64.p, 1, h->kernel_norm, h->out_tmp.p));
-    else
-        MTPT_TRY(unpermute_to<float>(h, reinterpret_cast<const float*>(h->rec.p) + 3, 1,
-                                     h->kernel_norm, h->out_tmp.p, 4));
+    if (h->n > 0) {
+        if (h->precision == MTPT_FP64) {
+            if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, double>(h, h->r64.p, 1)));
+            else MTPT_TRY((launch_row_sums_out<SingleView, double>(h, h->r64.p, 1)));
+        } else {
+            const float* rw = reinterpret_cast<const float*>(h->rec.p) + 3;
+            if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, float>(h, rw, 4)));
+            else MTPT_TRY((launch_row_sums_out<SingleView, float>(h, rw, 4)));
+        }
+    }
     return copy_out_host(h, 1, out);
 }
 
 int mtpt_get_pairs(mtpt_handle* h, int64_t cap, int64_t* count, uint32_t* pair_i,
                    uint32_t* pair_j) {
     if (!h || !count || cap < 0 || (cap > 0 && (!pair_i || !pair_j))) return MTPT_ERR_INVALID_ARG;
-    if (!h->status.p) return MTPT_ERR_STATE;
+    if (!h->have_particles) return MTPT_ERR_STATE;
     *count = 0;
-    if (h->n == 0 || !h->transfer_enabled) return read_status(h);
-    // Re-sort the current positions (no walk, no transfer) so the cell list
-    // describes them, then emit every accepted pair.
-    const int n = int(h->n);
-    const int blocks = grid_for(n);
-    const int64_t stride = h->cap;
-    const int c = h->cur, o = 1 - h->cur;
+    if (h->n == 0 || !h->any_transfer) return read_status(h);
     MTPT_TRY(h->emit_counter.ensure(1));
     const size_t ecap = size_t(std::max<int64_t>(cap, 1));
     MTPT_TRY(h->emit_i.ensure(ecap));
     MTPT_TRY(h->emit_j.ensure(ecap));
     MTPT_CUDA_TRY(cudaMemsetAsync(h->emit_counter.p, 0, sizeof(unsigned long long), h->stream));
-    const int ntiles = int(h->n_cells_pad / kScanTile);
-    auto sort_and_emit = [&](auto dim_tag) -> int {
-        constexpr int DIM = decltype(dim_tag)::value;
-        k_walk_key<DIM><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->pos[c].p, h->id[c].p, h->prm.seed, h->step, 0.0, 0, 1, h->box, h->grid,
-            h->key.p, h->count.p, h->status.p);
-        const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
-        k_scan_tile_sums<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p);
-        k_scan_tile_offsets<<<1, kScanThreads, 0, h->stream>>>(h->tile_sums.p, ntiles);
-        k_scan_apply<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p,
-                                                             reinterpret_cast<uint4*>(h->start.p));
-        k_scatter<<<blocks, kBlock, 0, h->stream>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
-        if (h->prm.precision == MTPT_FP32W)
-            k_gather<DIM, true><<<blocks, kBlock, 0, h->stream>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
-                h->corners.p, h->grid);
-        else
-            k_gather<DIM, false><<<blocks, kBlock, 0, h->stream>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-                h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr,
-                h->corners.p, h->grid);
-        k_emit_pairs<DIM><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->pos[o].p, h->rec.p, h->cell.p, h->start.p, h->id[o].p, h->grid, h->pp,
-            (unsigned long long)cap, h->emit_counter.p, h->emit_i.p, h->emit_j.p);
-        MTPT_CUDA_TRY(cudaGetLastError());
-        return MTPT_OK;
-    };
-    int rc;
-    switch (h->prm.dim) {
-        case 1: rc = sort_and_emit(std::integral_constant<int, 1>{}); break;
-        case 2: rc = sort_and_emit(std::integral_constant<int, 2>{}); break;
-        default: rc = sort_and_emit(std::integral_constant<int, 3>{}); break;
-    }
-    MTPT_TRY(rc);
-    // the gathered copy in o is the same state in cell order: make it current
-    h->cur = o;
-    h->have_row_sums = false;
+    // Re-sort the current positions (no walk, no transfer) so the cell list
+    // describes them, then emit every accepted pair.
+    MTPT_TRY(dispatch_emit(h, cap));
     unsigned long long total = 0;
     MTPT_CUDA_TRY(cudaMemcpyAsync(&total, h->emit_counter.p, sizeof(total), cudaMemcpyDeviceToHost, h->stream));
     MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -730,24 +1059,26 @@ int mtpt_get_info(mtpt_handle* h, mtpt_info* out) {
         MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
         out->pair_count = pc;
     }
-    out->D_RW = h->D_RW;
-    out->D_MT = h->D_MT;
-    out->sigma = h->sigma;
-    out->h2 = h->h2;
-    out->psi = h->psi;
-    out->psi2 = h->psi2;
-    out->kernel_norm = h->kernel_norm;
-    for (int a = 0; a < 3; ++a) {
-        out->cells[a] = h->grid.n[a] ? h->grid.n[a] : 1;
-        out->cell_width[a] = h->grid.w[a];
-    }
+    fill_info(h, 0, out);
     return h->status.p ? read_status(h) : MTPT_OK;
+}
+
+int mtpt_get_realisation_info(mtpt_handle* h, int32_t k, mtpt_info* out) {
+    if (!h || !out || k < 0 || k >= h->nreal) return MTPT_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n = h->reals[k].n;
+    out->step = h->step;
+    fill_info(h, k, out);
+    return MTPT_OK;
 }
 
 int mtpt_set_step(mtpt_handle* h, uint64_t step) {
     if (!h) return MTPT_ERR_INVALID_ARG;
-    h->step = step;
-    return MTPT_OK;
+    if (!h->have_particles) {
+        h->step = step;
+        return MTPT_OK;
+    }
+    return set_step_dev(h, step);
 }
 
 int mtpt_sync(mtpt_handle* h) {
@@ -802,7 +1133,8 @@ const char* mtpt_status_string(int status) {
 // mtpt_step_noalloc: one time step with all working memory in a fixed
 // file-scope device array instead of cudaMalloc'ed buffers, for callers that
 // must not allocate.  It runs the same kernels as mtpt_step through a handle
-// that lives on the host stack and whose buffers point into the array.
+// that lives on the host stack (inline realisation storage, no host
+// allocation) and whose buffers point into the array.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -862,13 +1194,17 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     if (n == 0) return MTPT_OK;
 
     mtpt_handle h;                       // host-side bookkeeping only
-    h.prm = *params;
+    h.dim = params->dim;
+    h.precision = params->precision;
+    h.reals[0].prm = *params;
+    derive(h.reals[0], h.params[0]);
     h.stream = static_cast<cudaStream_t>(stream);
-    derive(&h);
     h.n = n;
     h.cap = n;
-    MTPT_TRY(setup_grid(&h));
-    const int d = h.prm.dim;
+    h.reals[0].n = n;
+    h.params[0].id_offset = 0;
+    MTPT_TRY(setup_grids(&h));
+    const int d = h.dim;
     const size_t cells_pad = size_t(h.n_cells_pad);
 
     Carver cv{static_cast<unsigned char*>(scratch)};
@@ -881,7 +1217,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.perm.p = cv.take<uint32_t>(size_t(n));
     h.cell.p = cv.take<uint32_t>(size_t(n));
     h.rec.p = cv.take<float4>(size_t(n));
-    if (h.prm.precision == MTPT_FP64) {
+    if (h.precision == MTPT_FP64) {
         h.r64.p = cv.take<double>(size_t(n));
     } else {
         h.msplit.p = cv.take<float2>(size_t(n));
@@ -893,6 +1229,9 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.exp_table.p = cv.take<double>(64);
     h.status.p = cv.take<uint32_t>(1);
     h.pair_counter.p = cv.take<unsigned long long>(1);
+    h.step_dev.p = cv.take<unsigned long long>(1);
+    RealParams* params_dev = cv.take<RealParams>(1);
+    int* corner_first = cv.take<int>(2);
     if (cv.overflow) return MTPT_ERR_TOO_LARGE;
 
     // The handle's buffer pairs: index 0 is the caller's state (positions are
@@ -905,25 +1244,28 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.id[0].p = id_in;
     h.id[1].p = id_sorted;
     h.cur = 0;
-    h.step = step;
+    h.have_particles = true;
 
     cudaStream_t st = h.stream;
     // what must start at zero: cell counts, status word, pair counter
-    if (h.transfer_enabled)
+    if (h.any_transfer)
         MTPT_CUDA_TRY(cudaMemsetAsync(h.count.p, 0, cells_pad * sizeof(uint32_t), st));
     MTPT_CUDA_TRY(cudaMemsetAsync(h.status.p, 0, sizeof(uint32_t), st));
     MTPT_CUDA_TRY(cudaMemsetAsync(h.pair_counter.p, 0, sizeof(unsigned long long), st));
-    static double table[64];
-    static std::once_flag table_once;
-    std::call_once(table_once, []() {
-        for (int j = 0; j < 64; ++j) table[j] = double(exp2l(-static_cast<long double>(j) / 64.0L));
-    });
-    MTPT_CUDA_TRY(cudaMemcpyAsync(h.exp_table.p, table, sizeof(table), cudaMemcpyHostToDevice, st));
+    k_set_step<<<1, 1, 0, st>>>(h.step_dev.p, (unsigned long long)step);
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h.exp_table.p, exp_table_host(), 64 * sizeof(double),
+                                  cudaMemcpyHostToDevice, st));
+    // the one-entry realisation table and corner offsets for the corner kernel
+    static thread_local int first_host[2];
+    first_host[0] = 0;
+    first_host[1] = h.n_corners;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(params_dev, h.params, sizeof(RealParams), cudaMemcpyHostToDevice, st));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(corner_first, first_host, sizeof(first_host), cudaMemcpyHostToDevice, st));
     MTPT_CUDA_TRY(cudaMemcpyAsync(mass_in, mass_dev, size_t(n) * sizeof(double),
                                   cudaMemcpyDeviceToDevice, st));
     k_iota<<<grid_for(n), kBlock, 0, st>>>(int(n), id_in);
     MTPT_CUDA_TRY(cudaGetLastError());
-    MTPT_TRY(build_corners(&h));
+    MTPT_TRY(build_corners(&h, params_dev, corner_first));
     MTPT_TRY(dispatch_step(&h, MTPT_DO_WALK | MTPT_DO_TRANSFER));
     // masses back to the caller's order; positions are already there
     k_unpermute<double><<<grid_for(n), kBlock, 0, st>>>(int(n), h.cap, 1, h.id[h.cur].p,

@@ -38,6 +38,7 @@ EXPORTED = [
     "mtpt_get_masses_device", "mtpt_get_positions", "mtpt_get_positions_device",
     "mtpt_get_row_sums", "mtpt_get_pairs", "mtpt_get_info", "mtpt_set_step", "mtpt_sync",
     "mtpt_timing_enable", "mtpt_timing_read", "mtpt_timing_reset", "mtpt_step_noalloc",
+    "mtpt_create_batch", "mtpt_set_particles_batch", "mtpt_get_realisation_info",
     "mtpt_status_string",
 ]
 
@@ -132,6 +133,9 @@ def load():
     lib.mtpt_timing_enable.argtypes = [vp, ctypes.c_int32]
     lib.mtpt_timing_read.argtypes = [vp, ctypes.c_int32, P(_KernelStat), P(ctypes.c_int32)]
     lib.mtpt_timing_reset.argtypes = [vp]
+    lib.mtpt_create_batch.argtypes = [P(_Params), ctypes.c_int32, P(vp)]
+    lib.mtpt_set_particles_batch.argtypes = [vp, P(ctypes.c_int64), vp, vp]
+    lib.mtpt_get_realisation_info.argtypes = [vp, ctypes.c_int32, P(_Info)]
     lib.mtpt_step_noalloc.argtypes = [P(_Params), ctypes.c_int64, ctypes.c_uint64, vp, vp, vp]
     lib.mtpt_status_string.argtypes = [ctypes.c_int]
     lib.mtpt_status_string.restype = ctypes.c_char_p
@@ -181,6 +185,38 @@ def mtpt_create(params: Params) -> ctypes.c_void_p:
     return h
 
 
+def mtpt_create_batch(params_list) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    arr = (_Params * len(params_list))(*[p.c() for p in params_list])
+    _check(load().mtpt_create_batch(arr, len(params_list), ctypes.byref(h)), "mtpt_create_batch")
+    return h
+
+
+def mtpt_set_particles_batch(h, dim: int, counts, pos, mass) -> None:
+    counts = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+    mass = np.ascontiguousarray(np.asarray(mass, dtype=np.float64)).ravel()
+    total = int(counts.sum())
+    if mass.size != total:
+        raise ValueError(f"expected {total} masses, got {mass.size}")
+    pos = _host_f64(pos, (dim, total))
+    _check(load().mtpt_set_particles_batch(h, counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                           pos.ctypes.data, mass.ctypes.data),
+           "mtpt_set_particles_batch")
+
+
+def _info_dict(info) -> dict:
+    return {"n": info.n, "step": info.step, "pair_count": info.pair_count,
+            "D_RW": info.D_RW, "D_MT": info.D_MT, "sigma": info.sigma, "h2": info.h2,
+            "psi": info.psi, "psi2": info.psi2, "kernel_norm": info.kernel_norm,
+            "cells": tuple(info.cells), "cell_width": tuple(info.cell_width)}
+
+
+def mtpt_get_realisation_info(h, k: int) -> dict:
+    info = _Info()
+    _check(load().mtpt_get_realisation_info(h, k, ctypes.byref(info)), "mtpt_get_realisation_info")
+    return _info_dict(info)
+
+
 def mtpt_destroy(h) -> None:
     _check(load().mtpt_destroy(h), "mtpt_destroy")
 
@@ -216,10 +252,7 @@ def mtpt_step_ex(h, nsteps: int, flags: int) -> None:
 def mtpt_get_info(h) -> dict:
     info = _Info()
     _check(load().mtpt_get_info(h, ctypes.byref(info)), "mtpt_get_info")
-    return {"n": info.n, "step": info.step, "pair_count": info.pair_count,
-            "D_RW": info.D_RW, "D_MT": info.D_MT, "sigma": info.sigma, "h2": info.h2,
-            "psi": info.psi, "psi2": info.psi2, "kernel_norm": info.kernel_norm,
-            "cells": tuple(info.cells), "cell_width": tuple(info.cell_width)}
+    return _info_dict(info)
 
 
 def mtpt_get_masses(h, n: int) -> np.ndarray:
@@ -361,3 +394,31 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Batch(Simulation):
+    """Owning wrapper over a batch handle: realisation k uses params_list[k]
+    and the k-th block of the concatenated particle arrays."""
+
+    def __init__(self, params_list, counts=None, pos=None, mass=None):
+        self.params_list = list(params_list)
+        self.params = self.params_list[0]
+        self.h = mtpt_create_batch(self.params_list)
+        self.n = 0
+        self.counts = None
+        if counts is not None:
+            self.set_particles_batch(counts, pos, mass)
+
+    def set_particles_batch(self, counts, pos, mass):
+        mtpt_set_particles_batch(self.h, self.params.dim, counts, pos, mass)
+        self.counts = np.asarray(counts, dtype=np.int64)
+        self.n = int(self.counts.sum())
+
+    def realisation_info(self, k: int) -> dict:
+        return mtpt_get_realisation_info(self.h, k)
+
+    def split(self, arr):
+        """Split a concatenated per-particle array into per-realisation views
+        (the last axis is the particle axis)."""
+        edges = np.concatenate([[0], np.cumsum(self.counts)])
+        return [arr[..., edges[k]:edges[k + 1]] for k in range(len(self.counts))]

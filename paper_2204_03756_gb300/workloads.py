@@ -21,6 +21,11 @@ Workloads (sizes and parameters of the paper's test problem family, Sec. 2):
 Every workload takes kappa = 0.5, beta = 1 and lambda = 3 (cutoff
 psi = 3 sqrt(4 D_MT dt)), and may be scaled down (``n`` with the box scaled
 to keep the density) for tests.
+
+``ensemble_2d`` (see :func:`ensemble`) is a batch of independent 2-d
+realisations: counts log-uniform in [5,000, 200,000], densities uniform in
+[0.5, 2] (square box of side sqrt(N_k / rho_k)), D uniform in [0.1, 2],
+dt = 0.1, 200 steps, Heaviside mass (1 where x < L_k / 2), one seed each.
 """
 from __future__ import annotations
 
@@ -106,3 +111,42 @@ def initial_state(w: Workload):
 def get(name: str, n: int | None = None) -> Workload:
     w = WORKLOADS[name]
     return w if n is None or n == w.n else w.scaled(n)
+
+
+@dataclass
+class Ensemble:
+    """A batch of independent realisations: per-realisation workloads and
+    their concatenated initial state."""
+    name: str
+    members: list
+    steps: int
+
+    @property
+    def counts(self):
+        return np.array([w.n for w in self.members], dtype=np.int64)
+
+
+def ensemble(nreal: int = 512, n_min: int = 5_000, n_max: int = 200_000,
+             seed: int = SEED_BASE + 4, steps: int = 200) -> Ensemble:
+    """The ensemble workload: ``nreal`` 2-d realisations with log-uniform
+    particle counts, uniform densities in [0.5, 2] and D uniform in [0.1, 2]."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    logn = rng.uniform(np.log(n_min), np.log(n_max), size=nreal)
+    counts = np.round(np.exp(logn)).astype(np.int64)
+    rho = rng.uniform(0.5, 2.0, size=nreal)
+    D = rng.uniform(0.1, 2.0, size=nreal)
+    members = []
+    for k in range(nreal):
+        L = float(np.sqrt(counts[k] / rho[k]))
+        members.append(Workload(f"ensemble_2d[{k}]", 2, int(counts[k]), (0.0, 0.0), (L, L),
+                                float(D[k]), 0.5, 0.1, steps, "heaviside_left",
+                                seed=seed + 1 + k, mass_param=0.5 * L))
+    return Ensemble("ensemble_2d", members, steps)
+
+
+def ensemble_state(e: Ensemble):
+    """Concatenated initial positions (dim x total) and masses."""
+    parts = [initial_state(w) for w in e.members]
+    pos = np.concatenate([p for p, _ in parts], axis=1)
+    mass = np.concatenate([m for _, m in parts])
+    return pos, mass
