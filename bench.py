@@ -183,6 +183,61 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
     }
 
 
+def time_batched(steps, warmup, rank, world, dist, nreal=512, autotune_steps=4):
+    """The ensemble workload (independent 2-d realisations with uneven counts,
+    densities and D) in the precision form, one launch per kernel per step
+    over all realisations, autotuned, multi-step calls replayed as a CUDA
+    graph."""
+    import torch
+    e = workloads.ensemble(nreal=nreal)
+    pos, mass = workloads.ensemble_state(e)
+    params = [mtpt.Params(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
+                          lo=w.lo, hi=w.hi, seed=w.seed + 7919 * rank,
+                          precision=mtpt.MTPT_FP32W) for w in e.members]
+    stream = torch.cuda.Stream()
+    h = mtpt.mtpt_create_batch(params)
+    total = int(e.counts.sum())
+    try:
+        mtpt.mtpt_set_stream(h, stream.cuda_stream)
+        mtpt.mtpt_set_particles_batch(h, 2, e.counts, pos, mass)
+        tuning = mtpt.mtpt_autotune(h, autotune_steps)
+        mtpt.mtpt_step(h, warmup)
+        mtpt.mtpt_sync(h)
+        pairs0 = mtpt.mtpt_get_info(h)["pair_count"]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mtpt.mtpt_step(h, steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        pairs = mtpt.mtpt_get_info(h)["pair_count"] - pairs0
+        mtpt.mtpt_timing_reset(h)
+        mtpt.mtpt_timing_enable(h, True)
+        mtpt.mtpt_step(h, steps)
+        kstats = mtpt.mtpt_timing_read(h)
+        mtpt.mtpt_timing_enable(h, False)
+    finally:
+        mtpt.mtpt_destroy(h)
+    max_ms = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    sec = max_ms / 1e3
+    return {"form": "batched", "precision": "fp32w", "realisations": nreal,
+            "particles": total, "ms": max_ms, "ms_per_step": max_ms / steps,
+            "particle_steps_per_s": total * steps * world / sec,
+            "pair_interactions_per_s": pairs * world / sec,
+            "pairs_per_particle_step": pairs / (total * steps),
+            "tuning": tuning, "kernels": kstats,
+            "launches_per_step": sum(v[0] for v in kstats.values()) / steps,
+            "graph": "two-step CUDA graph replayed for the timed steps"}
+
+
 def roofline(w, res, peaks):
     kst = res["kernels"]
     name, (launches, total_ms) = max(kst.items(), key=lambda kv: kv[1][1])
@@ -293,7 +348,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
-    ap.add_argument("--forms", default="fp32w,fp64",
+    ap.add_argument("--forms", default="fp32w,fp64,batched",
                     help="comma list; the first is the headline value")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -324,9 +379,12 @@ def main():
         dist = tdist
     mtpt.load()
     pos, mass = workloads.initial_state(w)
-    forms = [f for f in args.forms.split(",") if f]
+    forms = [f for f in args.forms.split(",") if f and f != "batched"]
     results = {f: time_form(w, pos, mass, f, args.steps, args.warmup, rank, world, dist)
                for f in forms}
+    batched = None
+    if "batched" in args.forms.split(","):
+        batched = time_batched(args.steps, args.warmup, rank, world, dist)
     head = results[forms[0]]
     peaks = _peaks()
     e2e = e2e_form(w, pos, mass, forms[0], args.e2e_steps, rank)
@@ -353,6 +411,8 @@ def main():
     }
     for f, r in results.items():
         line["forms"][f]["roofline"] = roofline(w, r, peaks)
+    if batched is not None:
+        line["forms"]["batched"] = batched
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, pos, mass, forms[0])
     if rank == 0:

@@ -264,6 +264,32 @@ int mtpt_timing_reset(mtpt_handle* h);
 int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step, double* pos_dev,
                       double* mass_dev, void* stream);
 
+/* Launch tuning.  cell_scale >= 1 widens every cell to cell_scale x psi
+ * (fewer, fuller cells; more candidates per particle); pair_block is the
+ * thread-block size of the binary32 pair passes (128 or 256).  Results do not
+ * depend on the tuning beyond rounding (the neighbour sums visit the same
+ * pairs in a different order). */
+typedef struct mtpt_tuning {
+    double cell_scale;
+    int32_t pair_block;
+    int32_t pad;
+} mtpt_tuning;
+
+/* Apply a tuning (MTPT_ERR_INVALID_ARG outside the ranges above); the cell
+ * list is rebuilt on the next step. */
+int mtpt_set_tuning(mtpt_handle* h, const mtpt_tuning* t);
+
+/* Current tuning. */
+int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out);
+
+/* Autotuner: times `trial_steps` full steps (after one warm-up step) of the
+ * loaded particles for every cell_scale in {1, 1.25, 1.5, 2} and pair_block
+ * in {128, 256}, keeps the fastest, and restores the particles, masses, step
+ * counter and pair counter to their state before the call.  Allocates a
+ * temporary snapshot of the state.  *chosen (may be NULL) receives the pick.
+ * Synchronises. */
+int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen);
+
 /* Human-readable text of a status code (static storage). */
 const char* mtpt_status_string(int status);
 

@@ -687,8 +687,8 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
 
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
 // hardware ex2, compensated binary32 row sum, rounded to binary32 into rec.w.
-template <int DIM, class View>
-__global__ void __launch_bounds__(kBlock, 6)
+template <int DIM, class View, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)
 k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
              const __grid_constant__ View v, unsigned long long* __restrict__ pair_counter) {
@@ -717,8 +717,8 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, float4* __re
 // Pass 2, precision form: W = 2K / (r_s + r_j) in binary32 (symmetric bit for
 // bit), mass difference from the binary32 head/tail split (exactly
 // antisymmetric), flux accumulated with compensation, update in binary64.
-template <int DIM, class View>
-__global__ void __launch_bounds__(kBlock, 6)
+template <int DIM, class View, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
                const __grid_constant__ View v, const float2* __restrict__ msplit,

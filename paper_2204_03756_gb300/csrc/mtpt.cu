@@ -111,6 +111,8 @@ struct mtpt_handle {
     RealHost* reals = &real_inline;
     RealParams* params = &params_inline;
     bool any_transfer = false, any_walk = false;
+    double cell_scale = 1.0;          // tuning: cell width = cell_scale x psi (>= 1)
+    int pair_block = 256;             // tuning: block size of the binary32 pair passes
     cudaStream_t stream = nullptr;
     int64_t n = 0, cap = 0;
     int64_t n_cells = 0, n_cells_pad = 0;
@@ -265,7 +267,7 @@ void derive(RealHost& R, RealParams& P) {
 // dc = 3 u (B + L) / psi cells of the exact one (B = max(|lo|, |hi|)), so
 // cells of width w >= psi / (1 - 2 dc) keep every pair within psi in adjacent
 // cells.  Boxes where dc > 1e-3 (very many cells per axis) use binary64.
-int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base) {
+int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, double scale) {
     const mtpt_params& p = R.prm;
     Grid& g = P.g;
     const double u = std::ldexp(1.0, -24);
@@ -276,7 +278,7 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base) {
     }
     g.cell_f32 = (P.transfer && dc <= 1e-3) ? 1 : 0;
     const double widen = g.cell_f32 ? 1.0 / (1.0 - 2.0 * dc) : 1.0;
-    const double psi_eff = R.psi * widen * (1.0 + 1e-9);
+    const double psi_eff = R.psi * widen * scale * (1.0 + 1e-9);
     double ncell[3] = {1, 1, 1};
     for (int a = 0; a < p.dim; ++a) {
         const double L = p.hi[a] - p.lo[a];
@@ -352,7 +354,7 @@ int setup_grids(mtpt_handle* h) {
     h->any_transfer = false;
     h->any_walk = false;
     for (int k = 0; k < h->nreal; ++k) {
-        MTPT_TRY(setup_grid(h->reals[k], h->params[k], cell_base, corner_base));
+        MTPT_TRY(setup_grid(h->reals[k], h->params[k], cell_base, corner_base, h->cell_scale));
         cell_base += h->reals[k].n_cells;
         corner_base += h->reals[k].n_corners;
         h->any_transfer |= h->params[k].transfer != 0;
@@ -481,6 +483,23 @@ BatchView make_view<BatchView>(const mtpt_handle* h, int input_buf, int sorted_b
     return v;
 }
 
+template <int DIM, class View, int BLOCK>
+int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
+                     int o, int c) {
+    const int blocks = int((n + BLOCK - 1) / BLOCK);
+    {
+        MTPT_TIMED(h, "rowsum_f32");
+        k_rowsum_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->pair_counter.p);
+    }
+    MTPT_TIMED(h, "exchange_f32");
+    k_exchange_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
+        n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->msplit.p, h->mass[o].p,
+        h->mass[c].p);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
+}
+
 // Enqueues one time step (or part of it, per `flags`).  The step counter
 // lives on the device and advances inside the step, so the same launches can
 // be captured once and replayed.
@@ -562,17 +581,11 @@ int launch_step(mtpt_handle* h, int flags) {
             n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
             h->mass[o].p, h->mass[c].p);
     } else {
-        {
-            MTPT_TIMED(h, "rowsum_f32");
-            k_rowsum_f32<DIM, View><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p,
-                                                               h->cell.p, h->start.p, vs,
-                                                               h->pair_counter.p);
+        if (h->pair_block == 128) {
+            MTPT_TRY((launch_pairs_f32<DIM, View, 128>(h, n, stride, pos_s, vs, o, c)));
+        } else {
+            MTPT_TRY((launch_pairs_f32<DIM, View, 256>(h, n, stride, pos_s, vs, o, c)));
         }
-        MTPT_TIMED(h, "exchange_f32");
-        k_exchange_f32<DIM, View><<<blocks, kBlock, 0, st>>>(n, stride, pos_s, h->rec.p,
-                                                             h->cell.p, h->start.p, vs,
-                                                             h->msplit.p, h->mass[o].p,
-                                                             h->mass[c].p);
     }
     MTPT_CUDA_TRY(cudaGetLastError());
     // positions and ids live in o; the updated masses were written into c's
@@ -1111,6 +1124,122 @@ int mtpt_timing_reset(mtpt_handle* h) {
     MTPT_TRY(fold_timing(h));
     h->stats.clear();
     return MTPT_OK;
+}
+
+int mtpt_set_tuning(mtpt_handle* h, const mtpt_tuning* t) {
+    if (!h || !t) return MTPT_ERR_INVALID_ARG;
+    if (!(t->cell_scale >= 1.0 && t->cell_scale <= 8.0)) return MTPT_ERR_INVALID_ARG;
+    if (t->pair_block != 128 && t->pair_block != 256) return MTPT_ERR_INVALID_ARG;
+    const bool regrid = t->cell_scale != h->cell_scale;
+    h->cell_scale = t->cell_scale;
+    h->pair_block = t->pair_block;
+    drop_graph(h);
+    if (regrid && h->have_particles) {
+        MTPT_TRY(setup_grids(h));
+        if (h->any_transfer) MTPT_TRY(ensure_cells(h));
+        MTPT_TRY(upload_tables(h));
+        h->have_row_sums = false;
+    }
+    return MTPT_OK;
+}
+
+int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out) {
+    if (!h || !out) return MTPT_ERR_INVALID_ARG;
+    out->cell_scale = h->cell_scale;
+    out->pair_block = h->pair_block;
+    out->pad = 0;
+    return MTPT_OK;
+}
+
+int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
+    if (!h || trial_steps < 1) return MTPT_ERR_INVALID_ARG;
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    const bool timing0 = h->timing;
+    h->timing = false;
+    // snapshot of the current state (the trials step it)
+    const int64_t n = h->n;
+    const int d = h->dim;
+    DevBuf<double> spos, smass;
+    DevBuf<uint32_t> sid, srid;
+    MTPT_TRY(spos.ensure(size_t(d) * size_t(std::max<int64_t>(n, 1))));
+    MTPT_TRY(smass.ensure(size_t(std::max<int64_t>(n, 1))));
+    MTPT_TRY(sid.ensure(size_t(std::max<int64_t>(n, 1))));
+    if (h->batch) MTPT_TRY(srid.ensure(size_t(std::max<int64_t>(n, 1))));
+    const int c0 = h->cur;
+    auto copy_state = [&](bool save) -> int {
+        const size_t pitch = size_t(h->cap) * sizeof(double), row = size_t(n) * sizeof(double);
+        if (n == 0) return MTPT_OK;
+        if (save) {
+            MTPT_CUDA_TRY(cudaMemcpy2DAsync(spos.p, row, h->pos[c0].p, pitch, row, d,
+                                            cudaMemcpyDeviceToDevice, h->stream));
+            MTPT_CUDA_TRY(cudaMemcpyAsync(smass.p, h->mass[c0].p, row, cudaMemcpyDeviceToDevice, h->stream));
+            MTPT_CUDA_TRY(cudaMemcpyAsync(sid.p, h->id[c0].p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
+            if (h->batch)
+                MTPT_CUDA_TRY(cudaMemcpyAsync(srid.p, h->rid[c0].p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
+        } else {
+            h->cur = c0;
+            MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[c0].p, pitch, spos.p, row, row, d,
+                                            cudaMemcpyDeviceToDevice, h->stream));
+            MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[c0].p, smass.p, row, cudaMemcpyDeviceToDevice, h->stream));
+            MTPT_CUDA_TRY(cudaMemcpyAsync(h->id[c0].p, sid.p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
+            if (h->batch)
+                MTPT_CUDA_TRY(cudaMemcpyAsync(h->rid[c0].p, srid.p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
+        }
+        return MTPT_OK;
+    };
+    const uint64_t step0 = h->step;
+    unsigned long long pairs0 = 0;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&pairs0, h->pair_counter.p, sizeof(pairs0), cudaMemcpyDeviceToHost, h->stream));
+    MTPT_TRY(copy_state(true));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const double scales[] = {1.0, 1.25, 1.5, 2.0};
+    const int blocks[] = {128, 256};
+    mtpt_tuning best{1.0, 256, 0};
+    float best_ms = INFINITY;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MTPT_CUDA_TRY(cudaEventCreate(&e0));
+    MTPT_CUDA_TRY(cudaEventCreate(&e1));
+    int rc = MTPT_OK;
+    for (double sc : scales) {
+        for (int bl : blocks) {
+            mtpt_tuning t{sc, bl, 0};
+            rc = mtpt_set_tuning(h, &t);
+            if (rc == MTPT_OK) rc = run_steps(h, 1, MTPT_DO_WALK | MTPT_DO_TRANSFER);   // warm-up
+            if (rc == MTPT_OK && cudaEventRecord(e0, h->stream) != cudaSuccess) rc = MTPT_ERR_CUDA;
+            if (rc == MTPT_OK) rc = run_steps(h, trial_steps, MTPT_DO_WALK | MTPT_DO_TRANSFER);
+            if (rc == MTPT_OK && cudaEventRecord(e1, h->stream) != cudaSuccess) rc = MTPT_ERR_CUDA;
+            if (rc == MTPT_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = MTPT_ERR_CUDA;
+            float ms = 0.0f;
+            if (rc == MTPT_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = MTPT_ERR_CUDA;
+            if (rc == MTPT_OK) rc = copy_state(false);
+            if (rc != MTPT_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        if (rc != MTPT_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    if (rc == MTPT_OK) rc = mtpt_set_tuning(h, &best);
+    if (rc == MTPT_OK) rc = copy_state(false);
+    if (rc == MTPT_OK) rc = set_step_dev(h, step0);
+    if (rc == MTPT_OK) {
+        if (cudaMemcpyAsync(h->pair_counter.p, &pairs0, sizeof(pairs0), cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            rc = MTPT_ERR_CUDA;
+    }
+    h->have_row_sums = false;
+    h->timing = timing0;
+    spos.release();
+    smass.release();
+    sid.release();
+    srid.release();
+    if (rc == MTPT_OK && chosen) *chosen = best;
+    return rc;
 }
 
 const char* mtpt_status_string(int status) {

@@ -39,7 +39,7 @@ EXPORTED = [
     "mtpt_get_row_sums", "mtpt_get_pairs", "mtpt_get_info", "mtpt_set_step", "mtpt_sync",
     "mtpt_timing_enable", "mtpt_timing_read", "mtpt_timing_reset", "mtpt_step_noalloc",
     "mtpt_create_batch", "mtpt_set_particles_batch", "mtpt_get_realisation_info",
-    "mtpt_status_string",
+    "mtpt_set_tuning", "mtpt_get_tuning", "mtpt_autotune", "mtpt_status_string",
 ]
 
 
@@ -61,6 +61,11 @@ class _Params(ctypes.Structure):
 class _KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("cell_scale", ctypes.c_double), ("pair_block", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -133,6 +138,9 @@ def load():
     lib.mtpt_timing_enable.argtypes = [vp, ctypes.c_int32]
     lib.mtpt_timing_read.argtypes = [vp, ctypes.c_int32, P(_KernelStat), P(ctypes.c_int32)]
     lib.mtpt_timing_reset.argtypes = [vp]
+    lib.mtpt_set_tuning.argtypes = [vp, P(_Tuning)]
+    lib.mtpt_get_tuning.argtypes = [vp, P(_Tuning)]
+    lib.mtpt_autotune.argtypes = [vp, ctypes.c_int32, P(_Tuning)]
     lib.mtpt_create_batch.argtypes = [P(_Params), ctypes.c_int32, P(vp)]
     lib.mtpt_set_particles_batch.argtypes = [vp, P(ctypes.c_int64), vp, vp]
     lib.mtpt_get_realisation_info.argtypes = [vp, ctypes.c_int32, P(_Info)]
@@ -215,6 +223,23 @@ def mtpt_get_realisation_info(h, k: int) -> dict:
     info = _Info()
     _check(load().mtpt_get_realisation_info(h, k, ctypes.byref(info)), "mtpt_get_realisation_info")
     return _info_dict(info)
+
+
+def mtpt_set_tuning(h, cell_scale: float = 1.0, pair_block: int = 256) -> None:
+    t = _Tuning(cell_scale, pair_block, 0)
+    _check(load().mtpt_set_tuning(h, ctypes.byref(t)), "mtpt_set_tuning")
+
+
+def mtpt_get_tuning(h) -> dict:
+    t = _Tuning()
+    _check(load().mtpt_get_tuning(h, ctypes.byref(t)), "mtpt_get_tuning")
+    return {"cell_scale": t.cell_scale, "pair_block": t.pair_block}
+
+
+def mtpt_autotune(h, trial_steps: int = 4) -> dict:
+    t = _Tuning()
+    _check(load().mtpt_autotune(h, trial_steps, ctypes.byref(t)), "mtpt_autotune")
+    return {"cell_scale": t.cell_scale, "pair_block": t.pair_block}
 
 
 def mtpt_destroy(h) -> None:
@@ -374,6 +399,12 @@ class Simulation:
 
     def info(self) -> dict:
         return mtpt_get_info(self.h)
+
+    def autotune(self, trial_steps: int = 4) -> dict:
+        return mtpt_autotune(self.h, trial_steps)
+
+    def set_tuning(self, cell_scale: float = 1.0, pair_block: int = 256):
+        mtpt_set_tuning(self.h, cell_scale, pair_block)
 
     def set_step(self, step: int):
         mtpt_set_step(self.h, step)

@@ -100,3 +100,30 @@ def test_batch_rejects_mixed_dims_and_single_set_call():
             mtpt.mtpt_set_particles(h, 2, np.ones((2, 3)), np.ones(3))
     finally:
         mtpt.mtpt_destroy(h)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_tuned_grids_keep_parity_and_autotune_restores_state(form):
+    w = workloads.get("uniform_mass_2d", 20_000)
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w, precision=form)
+    xr, mr, npairs = O.run(oracle_params(p), pos, mass, 5)
+    for scale, block in ((2.0, 128), (1.25, 256)):
+        with mtpt.Simulation(p, pos, mass) as s:
+            s.set_tuning(scale, block)
+            s.step(5)
+            assert np.array_equal(s.positions(), xr)
+            assert s.info()["pair_count"] == npairs
+            assert rel_err(s.masses(), mr) <= TOL[form]
+    with mtpt.Simulation(p, pos, mass) as s:
+        s.step(2)
+        m2, x2, i2 = s.masses(), s.positions(), s.info()
+        t = s.autotune(trial_steps=4)
+        assert t["cell_scale"] in (1.0, 1.25, 1.5, 2.0) and t["pair_block"] in (128, 256)
+        assert np.array_equal(s.masses(), m2) and np.array_equal(s.positions(), x2)
+        i3 = s.info()
+        assert i3["step"] == i2["step"] and i3["pair_count"] == i2["pair_count"]
+        s.step(3)
+        xr5, mr5, _ = O.run(oracle_params(p), pos, mass, 5)
+        assert np.array_equal(s.positions(), xr5)
+        assert rel_err(s.masses(), mr5) <= TOL[form]
