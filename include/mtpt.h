@@ -264,6 +264,34 @@ int mtpt_timing_reset(mtpt_handle* h);
 int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step, double* pos_dev,
                       double* mass_dev, void* stream);
 
+/* Adjoint of a run (spec form 3; the paper has no gradient).  For a
+ * loss L(M_T) of the final masses, gives dL/dM_0 and dL/dD along the run's own
+ * random path (the normals xi stay fixed: pathwise derivative).  The mass
+ * update is linear, M_{t+1} = A_t M_t with A_t = I + beta (W_t - diag(W_t 1))
+ * symmetric, so dL/dM_0 = A_0 ... A_{T-1} dL/dM_T; D enters through the walk
+ * scale (positions) and the kernel bandwidth h^2, and bin or pair-set changes
+ * contribute zero almost everywhere.  Single-realisation handles with D > 0
+ * and D_MT > 0 only (MTPT_ERR_INVALID_ARG otherwise).  The adjoint passes run
+ * in binary64 in both precision forms (for MTPT_FP32W they differentiate the
+ * binary64 model at the run's positions, which are the same in both forms). */
+
+/* Advance nsteps full steps from the loaded state, as mtpt_step does, while
+ * recording a checkpoint of the state every `checkpoint_every` steps and the
+ * position tangents dX/dD.  Memory: (nsteps / checkpoint_every +
+ * checkpoint_every + 1) snapshots of (4 dim + 12) bytes per particle.
+ * Synchronises. */
+int mtpt_adjoint_forward(mtpt_handle* h, int64_t nsteps, int64_t checkpoint_every);
+
+/* Reverse sweep of the run recorded by mtpt_adjoint_forward: gmass_dev holds
+ * dL/dM_T (n doubles, DEVICE, input order); gmass0_dev receives dL/dM_0 (n
+ * doubles, DEVICE, input order); *dldD receives dL/dD (HOST).  Recomputes
+ * each segment forward from its checkpoint, then steps back through it.
+ * Leaves the handle in the final state of the forward run.  Deterministic
+ * (fixed summation orders).  Synchronises.  MTPT_ERR_STATE without a recorded
+ * run. */
+int mtpt_adjoint_backward(mtpt_handle* h, const double* gmass_dev, double* gmass0_dev,
+                          double* dldD);
+
 /* Launch tuning.  cell_scale >= 1 widens every cell to cell_scale x psi
  * (fewer, fuller cells; more candidates per particle); pair_block is the
  * thread-block size of the binary32 pair passes (128 or 256).  Results do not

@@ -72,6 +72,9 @@ struct RealParams {
     uint32_t cell_base;  // first global cell of the realisation
     int32_t transfer;    // 1 when D_MT > 0 (pair passes run)
     int32_t walk;        // 1 when sigma > 0
+    double dsigma_dD;    // d sigma / dD = sigma / (2 D) (adjoint)
+    double h2;           // 2 D_MT dt / beta (adjoint)
+    double inv_2D;       // 1 / (2 D) (adjoint)
 };
 
 struct SingleView {
@@ -160,6 +163,21 @@ __device__ __forceinline__ double reflect(double x, double lo, double hi) {
     return x < lo ? lo : (x > hi ? hi : x);
 }
 
+// As reflect(), also reporting the derivative of the result with respect to
+// the unreflected coordinate: -1 after an odd number of mirrors, +1 after an
+// even number, 0 when the coordinate was put on a wall.
+__device__ __forceinline__ double reflect_parity(double x, double lo, double hi, double* sign) {
+    double sg = 1.0;
+    for (int it = 0; it < 64; ++it) {
+        if (x < lo) x = __dsub_rn(__dmul_rn(2.0, lo), x);
+        else if (x > hi) x = __dsub_rn(__dmul_rn(2.0, hi), x);
+        else { *sign = sg; return x; }
+        sg = -sg;
+    }
+    *sign = 0.0;
+    return x < lo ? lo : (x > hi ? hi : x);
+}
+
 __device__ __forceinline__ int clamp_cell(float u, int n) {
     // u is finite here; truncation equals floor for u >= 0
     return u <= 0.0f ? 0 : (u >= float(n - 1) ? n - 1 : int(u));
@@ -188,12 +206,16 @@ __device__ __forceinline__ uint32_t cell_of(const double* x, const Grid& g, bool
     return lin;
 }
 
-template <int DIM, class View>
+// With TANGENT, also carries the pathwise derivative of the positions with
+// respect to D (tan, same layout as pos): the walk adds dsigma/dD xi and a
+// mirror flips the sign, exactly as it maps the coordinate.
+template <int DIM, class View, bool TANGENT = false>
 __global__ void __launch_bounds__(kBlock)
 k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __restrict__ id,
            const unsigned long long* __restrict__ step_dev, int do_walk, int do_key,
            const __grid_constant__ View v, uint32_t* __restrict__ key,
-           uint32_t* __restrict__ count, uint32_t* __restrict__ status) {
+           uint32_t* __restrict__ count, uint32_t* __restrict__ status,
+           double* __restrict__ tan = nullptr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint64_t step = *step_dev;
@@ -206,13 +228,22 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
         const float z[4] = {z4.x, z4.y, z4.z, z4.w};
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            double xv = __dadd_rn(x[a], __dmul_rn(P.sigma, f32_to_f64(z[a])));
+            const double za = f32_to_f64(z[a]);
+            double xv = __dadd_rn(x[a], __dmul_rn(P.sigma, za));
             const long long k = order_key(xv);
             // strictly inside in the integer order => inside in binary64, no
             // mirror needed; anything else (walls, outside, NaN) takes the
             // binary64 reflection
-            if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
-                xv = reflect(xv, P.box.lo[a], P.box.hi[a]);
+            if constexpr (TANGENT) {
+                double sign = 1.0;
+                if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
+                    xv = reflect_parity(xv, P.box.lo[a], P.box.hi[a], &sign);
+                const double t = __fma_rn(P.dsigma_dD, za, tan[a * stride + i]);
+                tan[a * stride + i] = __dmul_rn(sign, t);
+            } else {
+                if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
+                    xv = reflect(xv, P.box.lo[a], P.box.hi[a]);
+            }
             x[a] = xv;
             pos[a * stride + i] = xv;
         }
@@ -379,7 +410,7 @@ k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ 
 // binary32 offset from the cell corner (from the binary32 head/tail split of
 // the coordinate and of the corner: error below 2^-23 w, no binary64
 // instruction) and, in the precision form, the mass's head/tail split.
-template <int DIM, bool SPLIT_MASS, class View>
+template <int DIM, bool SPLIT_MASS, class View, bool TANGENT = false>
 __global__ void __launch_bounds__(kBlock)
 k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ key,
          const uint32_t* __restrict__ start, const uint32_t* __restrict__ id_in,
@@ -387,7 +418,8 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
          uint32_t* __restrict__ id_out, double* __restrict__ pos_out, double* __restrict__ mass_out,
          uint32_t* __restrict__ cell_out, float4* __restrict__ rec_out,
          float2* __restrict__ msplit_out, const float2* __restrict__ corners,
-         uint32_t* __restrict__ rid_out, const __grid_constant__ View v) {
+         uint32_t* __restrict__ rid_out, const __grid_constant__ View v,
+         const double* __restrict__ tan_in = nullptr, double* __restrict__ tan_out = nullptr) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t src = perm[s];
@@ -416,6 +448,7 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
         rest /= uint32_t(P.g.n[a]);
         const double x = pos_in[a * stride + src];
         pos_out[a * stride + dst] = x;
+        if constexpr (TANGENT) tan_out[a * stride + dst] = tan_in[a * stride + src];
         if (P.transfer) {
             float xh, xlo;
             split_double(x, &xh, &xlo);
@@ -770,6 +803,142 @@ k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float4
                                   out_j[k] = id[j];
                               }
                           });
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the step (binary64).  The mass update is M' = A M with
+// A = I + beta (W - diag(W 1)) symmetric, so the mass adjoint is
+// lambda_t = A lambda_{t+1}, the same pair sum with lambda in place of M.  The
+// derivative with respect to D follows the positions' pathwise tangents
+// (tan = dX/dD) and h^2 = 2 D_MT dt / beta (dh^2/dD = h^2 / D):
+//   dK_ij/dD = K_ij (-(x_i - x_j).(t_i - t_j) + d2_ij / (2 D)) / h^2,
+//   dr_i = sum_j dK_ij,
+//   dW_ij = 2 dK_ij / (r_i + r_j) - 2 K_ij (dr_i + dr_j) / (r_i + r_j)^2,
+// and step t adds beta sum_i lambda_{t+1,i} sum_j dW_ij (M_j - M_i) to dL/dD.
+// Pair-set and bin changes contribute zero almost everywhere.
+// ---------------------------------------------------------------------------
+template <int DIM>
+__device__ __forceinline__ void pair_terms(const double* __restrict__ pos,
+                                           const double* __restrict__ tan, int64_t stride,
+                                           uint32_t s, uint32_t j, const RealParams& P,
+                                           const double* table, double* K, double* dK) {
+    double d2 = 0.0, dot = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const double d = __dsub_rn(__ldg(pos + a * stride + s), __ldg(pos + a * stride + j));
+        const double dt = __dsub_rn(__ldg(tan + a * stride + s), __ldg(tan + a * stride + j));
+        const double sq = __dmul_rn(d, d);
+        d2 = (a == 0) ? sq : __dadd_rn(d2, sq);
+        dot = __fma_rn(d, dt, dot);
+    }
+    *K = exp_neg(__dmul_rn(d2, P.pp.a), table, P.pp.ec);
+    *dK = __dmul_rn(*K, __ddiv_rn(__fma_rn(d2, P.inv_2D, -dot), P.h2));
+}
+
+// Pass A: r_s = sum_j K_sj (self included) and dr_s = sum_j dK_sj / dD.
+template <int DIM, class View>
+__global__ void __launch_bounds__(kBlock)
+k_adj_rowsum(int n, int64_t stride, const double* __restrict__ pos, const double* __restrict__ tan,
+             const float4* __restrict__ rec, const uint32_t* __restrict__ cell,
+             const uint32_t* __restrict__ start, const double* __restrict__ exp_table,
+             const __grid_constant__ View v, double* __restrict__ r_out,
+             double* __restrict__ dr_out) {
+    __shared__ double table[64];
+    if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const RealParams& P = v.of_sorted(uint32_t(s));
+    double r = 1.0, dr = 0.0;
+    if (P.transfer) {
+        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
+                              [&](uint32_t j, float, const float4&) {
+                                  if (j == uint32_t(s)) return;
+                                  double K, dK;
+                                  pair_terms<DIM>(pos, tan, stride, uint32_t(s), j, P, table, &K, &dK);
+                                  r = __dadd_rn(r, K);
+                                  dr = __dadd_rn(dr, dK);
+                              });
+    }
+    r_out[s] = r;
+    dr_out[s] = dr;
+}
+
+// Pass B: lambda_t,s = lambda_s + beta sum_j W_sj (lambda_j - lambda_s) and the
+// step's D-gradient term g_s = beta lambda_s sum_j dW_sj (M_j - M_s), with M the
+// masses entering the step.
+template <int DIM, class View>
+__global__ void __launch_bounds__(kBlock)
+k_adj_exchange(int n, int64_t stride, const double* __restrict__ pos,
+               const double* __restrict__ tan, const float4* __restrict__ rec,
+               const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
+               const double* __restrict__ exp_table, const __grid_constant__ View v,
+               const double* __restrict__ r, const double* __restrict__ dr,
+               const double* __restrict__ mass, const double* __restrict__ lam,
+               double* __restrict__ lam_out, double* __restrict__ gD) {
+    __shared__ double table[64];
+    if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
+    __syncthreads();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const RealParams& P = v.of_sorted(uint32_t(s));
+    const double ls = lam[s];
+    double lacc = 0.0, gacc = 0.0;
+    if (P.transfer) {
+        const double rs = r[s], drs = dr[s], ms = mass[s];
+        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
+                              [&](uint32_t j, float, const float4&) {
+                                  if (j == uint32_t(s)) return;
+                                  double K, dK;
+                                  pair_terms<DIM>(pos, tan, stride, uint32_t(s), j, P, table, &K, &dK);
+                                  const double rsum = __dadd_rn(rs, __ldg(r + j));
+                                  const double inv = __ddiv_rn(1.0, rsum);
+                                  const double W = __dmul_rn(__dmul_rn(2.0, K), inv);
+                                  const double dW = __dmul_rn(
+                                      __dmul_rn(2.0, inv),
+                                      __fma_rn(-__dmul_rn(K, inv), __dadd_rn(drs, __ldg(dr + j)), dK));
+                                  lacc = __fma_rn(W, __dsub_rn(__ldg(lam + j), ls), lacc);
+                                  gacc = __fma_rn(dW, __dsub_rn(__ldg(mass + j), ms), gacc);
+                              });
+    }
+    lam_out[s] = __fma_rn(P.pp.beta, lacc, ls);
+    gD[s] = __dmul_rn(__dmul_rn(P.pp.beta, ls), gacc);
+}
+
+// Deterministic sum of x[0..n): fixed-size blocks reduce their slice in a fixed
+// tree, then one block adds the block sums in index order to *acc.
+constexpr int kReduceThreads = 512;
+
+__global__ void __launch_bounds__(kReduceThreads)
+k_block_sums(int n, const double* __restrict__ x, double* __restrict__ partial) {
+    __shared__ double buf[kReduceThreads];
+    const int i = blockIdx.x * kReduceThreads + threadIdx.x;
+    buf[threadIdx.x] = i < n ? x[i] : 0.0;
+    __syncthreads();
+    for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) buf[threadIdx.x] = __dadd_rn(buf[threadIdx.x], buf[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = buf[0];
+}
+
+__global__ void k_sum_into(int nparts, const double* __restrict__ partial, double* __restrict__ acc) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int k = 0; k < nparts; ++k) s = __dadd_rn(s, partial[k]);
+    *acc = __dadd_rn(*acc, s);
+}
+
+// Input-order <-> cell-order moves of a per-particle binary64 array.
+__global__ void k_take_by_id(int n, const uint32_t* __restrict__ id, const double* __restrict__ src,
+                             double* __restrict__ dst) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) dst[s] = src[id[s]];
+}
+__global__ void k_put_by_id(int n, const uint32_t* __restrict__ id, const double* __restrict__ src,
+                            double* __restrict__ dst) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) dst[id[s]] = src[s];
 }
 
 // Row sums in input order and in the paper's units:

@@ -139,6 +139,17 @@ struct mtpt_handle {
     DevBuf<unsigned long long> pair_counter, step_dev;
     DevBuf<unsigned long long> emit_counter;
     DevBuf<uint32_t> emit_i, emit_j;
+    // adjoint: position tangents dX/dD (double-buffered like pos), state
+    // snapshots (checkpoints every `adj_every` steps, the tape of one segment
+    // and the final state), adjoint vectors
+    bool tangent_on = false;
+    DevBuf<double> tan[2];
+    DevBuf<unsigned char> snaps;
+    size_t snap_bytes = 0;
+    int64_t adj_steps = 0, adj_every = 0, adj_nck = 0;
+    uint64_t adj_step0 = 0;
+    bool adj_ready = false;
+    DevBuf<double> dr64, lam_in, lam_s, lam_new, gD, partial, acc;
     // captured two-step graph (valid for `graph_cur`, `graph_flags`)
     cudaGraphExec_t graph = nullptr;
     int graph_cur = -1, graph_flags = -1;
@@ -247,6 +258,9 @@ void derive(RealHost& R, RealParams& P) {
     P.kernel_norm = R.h2 > 0.0 ? std::pow(2.0 * M_PI * R.h2, -0.5 * p.dim) : 0.0;
     P.transfer = R.h2 > 0.0 ? 1 : 0;
     P.walk = P.sigma > 0.0 ? 1 : 0;
+    P.h2 = R.h2;
+    P.dsigma_dD = p.D > 0.0 ? P.sigma / (2.0 * p.D) : 0.0;
+    P.inv_2D = p.D > 0.0 ? 1.0 / (2.0 * p.D) : 0.0;
     P.seed = p.seed;
     for (int a = 0; a < 3; ++a) {
         P.box.lo[a] = a < p.dim ? p.lo[a] : 0.0;
@@ -483,6 +497,42 @@ BatchView make_view<BatchView>(const mtpt_handle* h, int input_buf, int sorted_b
     return v;
 }
 
+// Gather from buffer c into buffer o in cell order (tangents too when on).
+template <int DIM, class View>
+int launch_gather(mtpt_handle* h, int c, int o, const View& vin) {
+    const int n = int(h->n);
+    const int blocks = grid_for(n);
+    const int64_t stride = h->cap;
+    uint32_t* rid_out = View::kBatch ? h->rid[o].p : nullptr;
+    float2* msplit = h->precision == MTPT_FP32W ? h->msplit.p : nullptr;
+    MTPT_TIMED(h, "gather");
+    if (h->precision == MTPT_FP32W) {
+        if (h->tangent_on)
+            k_gather<DIM, true, View, true><<<blocks, kBlock, 0, h->stream>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
+                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
+                msplit, h->corners.p, rid_out, vin, h->tan[c].p, h->tan[o].p);
+        else
+            k_gather<DIM, true, View><<<blocks, kBlock, 0, h->stream>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
+                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
+                msplit, h->corners.p, rid_out, vin);
+    } else {
+        if (h->tangent_on)
+            k_gather<DIM, false, View, true><<<blocks, kBlock, 0, h->stream>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
+                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
+                nullptr, h->corners.p, rid_out, vin, h->tan[c].p, h->tan[o].p);
+        else
+            k_gather<DIM, false, View><<<blocks, kBlock, 0, h->stream>>>(
+                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
+                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
+                nullptr, h->corners.p, rid_out, vin);
+    }
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
+}
+
 template <int DIM, class View, int BLOCK>
 int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
                      int o, int c) {
@@ -516,9 +566,14 @@ int launch_step(mtpt_handle* h, int flags) {
     const View vin = make_view<View>(h, c, c);
     if (walk || transfer) {
         MTPT_TIMED(h, "walk_key");
-        k_walk_key<DIM, View><<<blocks, kBlock, 0, st>>>(
-            n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0, transfer ? 1 : 0,
-            vin, h->key.p, h->count.p, h->status.p);
+        if (h->tangent_on)
+            k_walk_key<DIM, View, true><<<blocks, kBlock, 0, st>>>(
+                n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0,
+                transfer ? 1 : 0, vin, h->key.p, h->count.p, h->status.p, h->tan[c].p);
+        else
+            k_walk_key<DIM, View><<<blocks, kBlock, 0, st>>>(
+                n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0,
+                transfer ? 1 : 0, vin, h->key.p, h->count.p, h->status.p);
         MTPT_CUDA_TRY(cudaGetLastError());
     }
     const bool advance = (flags & MTPT_DO_WALK) != 0;
@@ -552,20 +607,7 @@ int launch_step(mtpt_handle* h, int flags) {
     }
     const bool split = h->precision == MTPT_FP32W;
     uint32_t* rid_out = View::kBatch ? h->rid[o].p : nullptr;
-    {
-        MTPT_TIMED(h, "gather");
-        if (split)
-            k_gather<DIM, true, View><<<blocks, kBlock, 0, st>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
-                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
-                h->msplit.p, h->corners.p, rid_out, vin);
-        else
-            k_gather<DIM, false, View><<<blocks, kBlock, 0, st>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
-                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
-                nullptr, h->corners.p, rid_out, vin);
-    }
-    MTPT_CUDA_TRY(cudaGetLastError());
+    MTPT_TRY((launch_gather<DIM, View>(h, c, o, vin)));
     // state now lives in buffer o (cell order); masses are updated into c
     const View vs = make_view<View>(h, o, o);
     const double* pos_s = h->pos[o].p;
@@ -652,7 +694,7 @@ int capture_two_steps(mtpt_handle* h, int flags) {
 }
 
 int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {
-    const bool use_graph = nsteps >= kGraphMinSteps && !h->timing && h->n > 0;
+    const bool use_graph = nsteps >= kGraphMinSteps && !h->timing && !h->tangent_on && h->n > 0;
     int64_t done = 0;
     if (use_graph) {
         if (!h->graph || h->graph_cur != h->cur || h->graph_flags != flags)
@@ -744,6 +786,7 @@ int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, con
     MTPT_TRY(set_step_dev(h, 0));
     h->have_row_sums = false;
     h->have_particles = true;
+    h->adj_ready = false;
     return MTPT_OK;
 }
 
@@ -894,9 +937,169 @@ int launch_check_domain(mtpt_handle* h) {
     return MTPT_OK;
 }
 
+// --- adjoint -----------------------------------------------------------------
+
+size_t snap_size(const mtpt_handle* h) {
+    const size_t n = size_t(h->n), d = size_t(h->dim);
+    return 2 * d * n * sizeof(double) + n * sizeof(double) + n * sizeof(uint32_t) + 64;
+}
+
+// Copies the current state (positions, tangents, masses, ids of buffer cur)
+// into snapshot slot k, or back into buffer 0 (then current).
+int snapshot(mtpt_handle* h, int64_t k, bool save) {
+    const size_t n = size_t(h->n), d = size_t(h->dim);
+    if (n == 0) return MTPT_OK;
+    unsigned char* base = h->snaps.p + size_t(k) * h->snap_bytes;
+    double* spos = reinterpret_cast<double*>(base);
+    double* stan = spos + d * n;
+    double* smass = stan + d * n;
+    uint32_t* sid = reinterpret_cast<uint32_t*>(smass + n);
+    const size_t pitch = size_t(h->cap) * sizeof(double), row = n * sizeof(double);
+    const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+    if (save) {
+        const int c = h->cur;
+        MTPT_CUDA_TRY(cudaMemcpy2DAsync(spos, row, h->pos[c].p, pitch, row, d, dd, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpy2DAsync(stan, row, h->tan[c].p, pitch, row, d, dd, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(smass, h->mass[c].p, row, dd, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(sid, h->id[c].p, n * sizeof(uint32_t), dd, h->stream));
+    } else {
+        h->cur = 0;
+        MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[0].p, pitch, spos, row, row, d, dd, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->tan[0].p, pitch, stan, row, row, d, dd, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[0].p, smass, row, dd, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->id[0].p, sid, n * sizeof(uint32_t), dd, h->stream));
+    }
+    return MTPT_OK;
+}
+
+// One backward step: walk (with tangents) and sort exactly as forward step t
+// did, then the adjoint passes, lambda kept in input order between steps.
+template <int DIM>
+int launch_adjoint_step(mtpt_handle* h) {
+    const int n = int(h->n);
+    const int64_t stride = h->cap;
+    const int blocks = grid_for(n);
+    cudaStream_t st = h->stream;
+    const int c = h->cur, o = 1 - h->cur;
+    const SingleView v = make_view<SingleView>(h, c, c);
+    k_walk_key<DIM, SingleView, true><<<blocks, kBlock, 0, st>>>(
+        n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, h->any_walk ? 1 : 0, 1, v, h->key.p,
+        h->count.p, h->status.p, h->tan[c].p);
+    const int ntiles = int(h->n_cells_pad / kScanTile);
+    const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
+    k_scan_tile_sums<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p);
+    k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(h->tile_sums.p, ntiles, h->step_dev.p, 1);
+    k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p,
+                                                  reinterpret_cast<uint4*>(h->start.p));
+    k_scatter<<<blocks, kBlock, 0, st>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    MTPT_TRY((launch_gather<DIM, SingleView>(h, c, o, v)));
+    k_take_by_id<<<blocks, kBlock, 0, st>>>(n, h->id[o].p, h->lam_in.p, h->lam_s.p);
+    k_adj_rowsum<DIM, SingleView><<<blocks, kBlock, 0, st>>>(
+        n, stride, h->pos[o].p, h->tan[o].p, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, v,
+        h->r64.p, h->dr64.p);
+    k_adj_exchange<DIM, SingleView><<<blocks, kBlock, 0, st>>>(
+        n, stride, h->pos[o].p, h->tan[o].p, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, v,
+        h->r64.p, h->dr64.p, h->mass[o].p, h->lam_s.p, h->lam_new.p, h->gD.p);
+    k_put_by_id<<<blocks, kBlock, 0, st>>>(n, h->id[o].p, h->lam_new.p, h->lam_in.p);
+    const int nparts = (n + kReduceThreads - 1) / kReduceThreads;
+    k_block_sums<<<nparts, kReduceThreads, 0, st>>>(n, h->gD.p, h->partial.p);
+    k_sum_into<<<1, 1, 0, st>>>(nparts, h->partial.p, h->acc.p);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    h->cur = o;
+    return MTPT_OK;
+}
+
+int dispatch_adjoint_step(mtpt_handle* h) {
+    switch (h->dim) {
+        case 1: return launch_adjoint_step<1>(h);
+        case 2: return launch_adjoint_step<2>(h);
+        default: return launch_adjoint_step<3>(h);
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+int mtpt_adjoint_forward(mtpt_handle* h, int64_t nsteps, int64_t checkpoint_every) {
+    if (!h || nsteps < 1 || checkpoint_every < 1) return MTPT_ERR_INVALID_ARG;
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    if (h->nreal != 1 || !h->any_transfer || !(h->reals[0].prm.D > 0.0)) return MTPT_ERR_INVALID_ARG;
+    const int64_t n = h->n;
+    const size_t cap = size_t(std::max<int64_t>(h->cap, 1));
+    for (int b = 0; b < 2; ++b) MTPT_TRY(h->tan[b].ensure(size_t(h->dim) * cap));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->tan[h->cur].p, 0, size_t(h->dim) * cap * sizeof(double), h->stream));
+    const int64_t nck = (nsteps + checkpoint_every - 1) / checkpoint_every;
+    const int64_t seg = std::min(checkpoint_every, nsteps);
+    h->snap_bytes = (snap_size(h) + 255) & ~size_t(255);
+    MTPT_TRY(h->snaps.ensure(size_t(nck + seg + 1) * h->snap_bytes));
+    for (auto* b : {&h->dr64, &h->lam_in, &h->lam_s, &h->lam_new, &h->gD})
+        MTPT_TRY(b->ensure(cap));
+    MTPT_TRY(h->r64.ensure(cap));
+    MTPT_TRY(h->partial.ensure(size_t((n + kReduceThreads - 1) / kReduceThreads + 1)));
+    MTPT_TRY(h->acc.ensure(1));
+    h->tangent_on = true;
+    h->adj_step0 = h->step;
+    int rc = MTPT_OK;
+    for (int64_t t = 0; t < nsteps && rc == MTPT_OK; ++t) {
+        if (t % checkpoint_every == 0) rc = snapshot(h, t / checkpoint_every, true);
+        if (rc == MTPT_OK) rc = dispatch_step(h, MTPT_DO_WALK | MTPT_DO_TRANSFER);
+    }
+    if (rc == MTPT_OK) rc = snapshot(h, nck + seg, true);   // final state
+    h->tangent_on = false;
+    if (rc != MTPT_OK) return rc;
+    h->step += uint64_t(nsteps);
+    h->adj_steps = nsteps;
+    h->adj_every = checkpoint_every;
+    h->adj_nck = nck;
+    h->adj_ready = true;
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MTPT_OK;
+}
+
+int mtpt_adjoint_backward(mtpt_handle* h, const double* gmass_dev, double* gmass0_dev,
+                          double* dldD) {
+    if (!h || (h->n > 0 && (!gmass_dev || !gmass0_dev)) || !dldD) return MTPT_ERR_INVALID_ARG;
+    if (!h->adj_ready) return MTPT_ERR_STATE;
+    const int64_t n = h->n, K = h->adj_every, T = h->adj_steps, nck = h->adj_nck;
+    const int64_t seg = std::min(K, T);
+    const int64_t final_slot = nck + seg;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h->lam_in.p, gmass_dev, size_t(n) * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, h->stream));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->acc.p, 0, sizeof(double), h->stream));
+    drop_graph(h);
+    h->tangent_on = true;
+    int rc = MTPT_OK;
+    for (int64_t k = nck - 1; k >= 0 && rc == MTPT_OK; --k) {
+        const int64_t t0 = k * K, t1 = std::min(t0 + K, T);
+        // forward over the segment from its checkpoint, recording the state
+        // before every step on the tape
+        rc = snapshot(h, k, false);
+        if (rc == MTPT_OK) rc = set_step_dev(h, h->adj_step0 + uint64_t(t0));
+        for (int64_t t = t0; t < t1 && rc == MTPT_OK; ++t) {
+            rc = snapshot(h, nck + (t - t0), true);
+            if (rc == MTPT_OK && t + 1 < t1) rc = dispatch_step(h, MTPT_DO_WALK | MTPT_DO_TRANSFER);
+        }
+        // backward through the tape
+        for (int64_t t = t1 - 1; t >= t0 && rc == MTPT_OK; --t) {
+            rc = snapshot(h, nck + (t - t0), false);
+            if (rc == MTPT_OK) rc = set_step_dev(h, h->adj_step0 + uint64_t(t));
+            if (rc == MTPT_OK) rc = dispatch_adjoint_step(h);
+        }
+    }
+    h->tangent_on = false;
+    // leave the handle in its final forward state
+    if (rc == MTPT_OK) rc = snapshot(h, final_slot, false);
+    if (rc == MTPT_OK) rc = set_step_dev(h, h->adj_step0 + uint64_t(T));
+    h->have_row_sums = false;
+    if (rc != MTPT_OK) return rc;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(gmass0_dev, h->lam_in.p, size_t(n) * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, h->stream));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(dldD, h->acc.p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
 
 int mtpt_create(const mtpt_params* params, mtpt_handle** out) {
     return create_common(params, 1, false, out);
@@ -923,6 +1126,9 @@ int mtpt_destroy(mtpt_handle* h) {
     h->r64.release(); h->msplit.release(); h->out_tmp.release(); h->exp_table.release();
     h->status.release(); h->pair_counter.release(); h->step_dev.release();
     h->emit_counter.release(); h->emit_i.release(); h->emit_j.release();
+    h->tan[0].release(); h->tan[1].release(); h->snaps.release(); h->dr64.release();
+    h->lam_in.release(); h->lam_s.release(); h->lam_new.release(); h->gD.release();
+    h->partial.release(); h->acc.release();
     for (auto& pe : h->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);

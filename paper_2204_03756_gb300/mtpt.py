@@ -39,7 +39,8 @@ EXPORTED = [
     "mtpt_get_row_sums", "mtpt_get_pairs", "mtpt_get_info", "mtpt_set_step", "mtpt_sync",
     "mtpt_timing_enable", "mtpt_timing_read", "mtpt_timing_reset", "mtpt_step_noalloc",
     "mtpt_create_batch", "mtpt_set_particles_batch", "mtpt_get_realisation_info",
-    "mtpt_set_tuning", "mtpt_get_tuning", "mtpt_autotune", "mtpt_status_string",
+    "mtpt_set_tuning", "mtpt_get_tuning", "mtpt_autotune", "mtpt_adjoint_forward",
+    "mtpt_adjoint_backward", "mtpt_status_string",
 ]
 
 
@@ -138,6 +139,8 @@ def load():
     lib.mtpt_timing_enable.argtypes = [vp, ctypes.c_int32]
     lib.mtpt_timing_read.argtypes = [vp, ctypes.c_int32, P(_KernelStat), P(ctypes.c_int32)]
     lib.mtpt_timing_reset.argtypes = [vp]
+    lib.mtpt_adjoint_forward.argtypes = [vp, ctypes.c_int64, ctypes.c_int64]
+    lib.mtpt_adjoint_backward.argtypes = [vp, vp, vp, P(ctypes.c_double)]
     lib.mtpt_set_tuning.argtypes = [vp, P(_Tuning)]
     lib.mtpt_get_tuning.argtypes = [vp, P(_Tuning)]
     lib.mtpt_autotune.argtypes = [vp, ctypes.c_int32, P(_Tuning)]
@@ -240,6 +243,21 @@ def mtpt_autotune(h, trial_steps: int = 4) -> dict:
     t = _Tuning()
     _check(load().mtpt_autotune(h, trial_steps, ctypes.byref(t)), "mtpt_autotune")
     return {"cell_scale": t.cell_scale, "pair_block": t.pair_block}
+
+
+def mtpt_adjoint_forward(h, nsteps: int, checkpoint_every: int) -> None:
+    _check(load().mtpt_adjoint_forward(h, nsteps, checkpoint_every), "mtpt_adjoint_forward")
+
+
+def mtpt_adjoint_backward(h, gmass, gmass0) -> float:
+    """gmass: dL/dM_T, gmass0: output dL/dM_0 (CUDA float64 tensors, input
+    order).  Returns dL/dD."""
+    out = ctypes.c_double()
+    n = gmass.numel()
+    _check(load().mtpt_adjoint_backward(h, _dev_ptr(gmass, "float64", n),
+                                        _dev_ptr(gmass0, "float64", n), ctypes.byref(out)),
+           "mtpt_adjoint_backward")
+    return float(out.value)
 
 
 def mtpt_destroy(h) -> None:

@@ -150,3 +150,17 @@ def ensemble_state(e: Ensemble):
     pos = np.concatenate([p for p, _ in parts], axis=1)
     mass = np.concatenate([m for _, m in parts])
     return pos, mass
+
+
+def target_field(nbins, lo, hi, seed: int = SEED_BASE + 6) -> np.ndarray:
+    """Seeded smooth target concentration on an nbins[0] x nbins[1] grid of
+    bin centres over the box: 0.5 + 0.25 sin(2 pi (x/Lx + a)) cos(2 pi (y/Ly + b))
+    with phases a, b drawn from the seed (the misfit target of the
+    differentiable workload)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    a, b = rng.uniform(0.0, 1.0, size=2)
+    Lx, Ly = hi[0] - lo[0], hi[1] - lo[1]
+    xc = lo[0] + (np.arange(nbins[0]) + 0.5) * Lx / nbins[0]
+    yc = lo[1] + (np.arange(nbins[1]) + 0.5) * Ly / nbins[1]
+    X, Y = np.meshgrid(xc, yc, indexing="ij")
+    return 0.5 + 0.25 * np.sin(2 * np.pi * (X / Lx + a)) * np.cos(2 * np.pi * (Y / Ly + b))
