@@ -62,6 +62,27 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
     return float(table.get(kernel, 0))
 
 
+# DRAM bytes per particle of each kernel from one ncu capture
+# (profiles/step_kernels_gaussian_2d_8M_full.md, gaussian_2d scaled to 8e6
+# particles; traffic grows in proportion to the particles a launch processes,
+# so it is scaled to the bench's launch).  Valid only for the kernel source it
+# was measured on: a different hash of kernels.cuh reports traffic as null.
+TRAFFIC_SOURCE_SHA1 = "47b64f28dfb4"
+TRAFFIC_BYTES_PER_PARTICLE = {
+    "walk_key": (177.798144e6 + 117.535232e6) / 8e6,
+    "gather": (305.847296e6 + 394.810368e6) / 8e6,
+    "rowsum_f32": (177.878784e6 + 70.140416e6) / 8e6,
+    "exchange_f32": (305.834752e6 + 54.230016e6) / 8e6,
+}
+
+
+def _kernel_source_sha1() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2204_03756_gb300", "csrc", "kernels.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling while the timed region runs."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -238,15 +259,88 @@ def time_batched(steps, warmup, rank, world, dist, nreal=512, autotune_steps=4):
             "graph": "two-step CUDA graph replayed for the timed steps"}
 
 
+def time_adjoint(rank, nbins=(100, 100), checkpoint_every=20):
+    """The differentiable workload (250,000 particles in [0,500]^2, masses
+    U(0,1), D = 0.5, dt = 0.1, 200 steps): forward run with checkpoints every
+    20 steps in the precision form, then the adjoint sweep (binary64 adjoint
+    passes) for the gradient of the 100 x 100 binned-concentration misfit
+    against a seeded target with respect to the initial masses and D."""
+    import torch
+    from paper_2204_03756_gb300.autograd import binned_concentration
+    w = workloads.get("uniform_mass_2d")
+    pos, mass = workloads.initial_state(w)
+    p = mtpt.Params(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
+                    lo=w.lo, hi=w.hi, seed=w.seed + rank, precision=mtpt.MTPT_FP32W)
+    target = torch.from_numpy(workloads.target_field(nbins, w.lo, w.hi)).cuda()
+    h = mtpt.mtpt_create(p)
+    try:
+        mtpt.mtpt_set_particles(h, w.dim, pos, mass)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mtpt.mtpt_adjoint_forward(h, w.steps, checkpoint_every)
+        t1 = time.perf_counter()
+        mT = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        xT = torch.empty(w.dim * w.n, dtype=torch.float64, device="cuda")
+        mtpt.mtpt_get_masses_device(h, mT)
+        mtpt.mtpt_get_positions_device(h, xT)
+        mtpt.mtpt_sync(h)
+        mT.requires_grad_(True)
+        C = binned_concentration(xT.view(w.dim, w.n), mT, w.lo, w.hi, nbins)
+        loss = ((C - target) ** 2).sum()
+        loss.backward()
+        g = mT.grad.contiguous()
+        g0 = torch.empty_like(g)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        dldD = mtpt.mtpt_adjoint_backward(h, g, g0)
+        t3 = time.perf_counter()
+    finally:
+        mtpt.mtpt_destroy(h)
+    fwd, bwd = t1 - t0, t3 - t2
+    return {"form": "adjoint", "workload": "uniform_mass_2d", "n": w.n, "steps": w.steps,
+            "checkpoint_every": checkpoint_every, "forward_s": fwd, "backward_s": bwd,
+            "gradient_particle_steps_per_s": w.n * w.steps / (fwd + bwd),
+            "loss": float(loss.item()), "dL_dD": dldD,
+            "dL_dM0_norm": float(g0.norm().item()),
+            "precision": "forward fp32w, adjoint passes f64"}
+
+
+# binary64 instructions per accepted ordered pair of the binary64 pair passes
+# (exact squared distance 3d - 1, exp by Tang's table method 11, the scaling
+# by a 1, the row-sum add 1; exchange adds 2K, r_i + r_j, the IEEE division
+# (8 on GB300, measured), the mass difference and the product)
+def _f64_ops_per_pair(kernel: str, dim: int) -> float:
+    d2 = 3 * dim - 1
+    return {"rowsum_f64": d2 + 1 + 11 + 1, "exchange_f64": d2 + 1 + 11 + 2 + 8 + 2}[kernel]
+
+
+# GB300 binary64 issue rate: 2 binary64 operations per clock per SM (recipe's
+# 1.25 TFLOP/s counts an fma as two) x 152 SMs x 2.07 GHz
+F64_PEAK_OPS = 2 * 152 * 2.07e9
+
+
 def roofline(w, res, peaks):
     kst = res["kernels"]
     name, (launches, total_ms) = max(kst.items(), key=lambda kv: kv[1][1])
     per_launch_s = total_ms / launches / 1e3
+    share = total_ms / sum(v[1] for v in kst.values())
+    if name in ("rowsum_f64", "exchange_f64"):
+        pairs = res["pairs_per_particle_step"] * w.n
+        ops = _f64_ops_per_pair(name, w.dim) * pairs
+        achieved = ops / per_launch_s / 1e9
+        return {"bound": "alu", "kernel": name, "achieved": achieved,
+                "peak": F64_PEAK_OPS / 1e9, "unit": "G binary64 op/s",
+                "frac": achieved / (F64_PEAK_OPS / 1e9), "traffic": None,
+                "algorithmic_ops_per_launch": ops, "launch_ms": per_launch_s * 1e3,
+                "share_of_step": share,
+                "peak_source": "derived: 2 binary64 ops/clk/SM x 152 SMs x 2.07 GHz"}
     algo = _algo_bytes_per_particle(name, w.dim, res["form"]) * w.n
     achieved = algo / per_launch_s / 1e9
-    share = total_ms / sum(v[1] for v in kst.values())
+    traffic = None
+    if name in TRAFFIC_BYTES_PER_PARTICLE and _kernel_source_sha1() == TRAFFIC_SOURCE_SHA1:
+        traffic = TRAFFIC_BYTES_PER_PARTICLE[name] * w.n
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "algorithmic_bytes_per_launch": algo, "launch_ms": per_launch_s * 1e3,
             "share_of_step": share, "peak_source": peaks["source"]}
 
@@ -348,7 +442,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
-    ap.add_argument("--forms", default="fp32w,fp64,batched",
+    ap.add_argument("--forms", default="fp32w,fp64,batched,adjoint",
                     help="comma list; the first is the headline value")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -379,14 +473,34 @@ def main():
         dist = tdist
     mtpt.load()
     pos, mass = workloads.initial_state(w)
-    forms = [f for f in args.forms.split(",") if f and f != "batched"]
+    forms = [f for f in args.forms.split(",") if f and f not in ("batched", "adjoint")]
     results = {f: time_form(w, pos, mass, f, args.steps, args.warmup, rank, world, dist)
                for f in forms}
     batched = None
     if "batched" in args.forms.split(","):
         batched = time_batched(args.steps, args.warmup, rank, world, dist)
-    head = results[forms[0]]
+    adjoint = time_adjoint(rank) if "adjoint" in args.forms.split(",") else None
     peaks = _peaks()
+    if not forms:                        # only batched / adjoint requested
+        line = {"metric": "particle-steps/s", "unit": "particle-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc",
+                "data": "synthetic", "forms": {}}
+        if batched is not None:
+            line.update(value=batched["particle_steps_per_s"], ms_per_step=batched["ms_per_step"],
+                        config={"workload": "ensemble_2d", "realisations": batched["realisations"],
+                                "n": batched["particles"]},
+                        gpu_launches=int(round(batched["launches_per_step"] * args.steps)))
+            line["forms"]["batched"] = batched
+        if adjoint is not None:
+            line["forms"]["adjoint"] = adjoint
+        if rank == 0:
+            print(json.dumps(line))
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+    head = results[forms[0]]
     e2e = e2e_form(w, pos, mass, forms[0], args.e2e_steps, rank)
     line = {
         "metric": "particle-steps/s", "value": head["particle_steps_per_s"],
@@ -413,6 +527,8 @@ def main():
         line["forms"][f]["roofline"] = roofline(w, r, peaks)
     if batched is not None:
         line["forms"]["batched"] = batched
+    if adjoint is not None:
+        line["forms"]["adjoint"] = adjoint
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, pos, mass, forms[0])
     if rank == 0:
