@@ -144,6 +144,34 @@ def _params(w, form: str, rank: int) -> mtpt.Params:
                        lo=w.lo, hi=w.hi, seed=w.seed + rank, precision=FORMS[form])
 
 
+def workload_config(w, form: str, world: int) -> dict:
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": w.name, "n": w.n, "dim": w.dim, "box": list(w.hi),
+            "D": w.D, "kappa": w.kappa, "dt": w.dt, "lambda": w.lam,
+            "form": form, "steps_in_config": w.steps,
+            "l2": "inputs larger than L2 (per-step working set > 300 MB)",
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
+def reduce_over_ranks(ms: float, pairs: float, dist, device: str = "cuda"):
+    """Whole-job timing of replicas: the slowest rank's time and the sum of
+    every rank's neighbour pairs (each rank steps its own realisation)."""
+    if dist is None:
+        return ms, pairs
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    pt = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    dist.all_reduce(pt, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(pt.item())
+
+
+def job_throughput(n_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Particle-steps per second of the whole job (all ranks' particles over
+    the slowest rank's time)."""
+    return n_per_rank * steps * world / (max_ms / 1e3)
+
+
 def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
     import torch
     p = _params(w, form, rank)
@@ -184,18 +212,11 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
         mtpt.mtpt_timing_enable(h, False)
     finally:
         mtpt.mtpt_destroy(h)
-    max_ms = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
-        pt = torch.tensor([float(pairs)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
-        pairs = pt.item()
+    max_ms, pairs = reduce_over_ranks(ms, pairs, dist)
     sec = max_ms / 1e3
     return {
         "form": form, "ms": max_ms, "ms_per_step": max_ms / steps,
-        "particle_steps_per_s": w.n * steps * world / sec,
+        "particle_steps_per_s": job_throughput(w.n, steps, world, max_ms),
         "pair_interactions_per_s": pairs / sec,
         "pairs_per_particle_step": pairs / (w.n * steps * world),
         "mass_drift_rel": abs(m_after - m_before) / abs(m_before),
@@ -243,16 +264,12 @@ def time_batched(steps, warmup, rank, world, dist, nreal=512, autotune_steps=4):
         mtpt.mtpt_timing_enable(h, False)
     finally:
         mtpt.mtpt_destroy(h)
-    max_ms = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
+    max_ms, pairs_all = reduce_over_ranks(ms, pairs, dist)
     sec = max_ms / 1e3
     return {"form": "batched", "precision": "fp32w", "realisations": nreal,
             "particles": total, "ms": max_ms, "ms_per_step": max_ms / steps,
-            "particle_steps_per_s": total * steps * world / sec,
-            "pair_interactions_per_s": pairs * world / sec,
+            "particle_steps_per_s": job_throughput(total, steps, world, max_ms),
+            "pair_interactions_per_s": pairs_all / sec,
             "pairs_per_particle_step": pairs / (total * steps),
             "tuning": tuning, "kernels": kstats,
             "launches_per_step": sum(v[0] for v in kstats.values()) / steps,
@@ -427,7 +444,7 @@ def reference_arm(args, w, pos, mass):
             "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "dim": w.dim, "steps_in_config": w.steps},
+            "config": workload_config(w, args.forms.split(",")[0], 1),
             "pair_interactions_per_s": pairs / sec,
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
                              "kind": "oracle", "sample": sample},
@@ -508,11 +525,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[forms[0]], "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "dim": w.dim, "box": list(w.hi),
-                   "D": w.D, "kappa": w.kappa, "dt": w.dt, "lambda": w.lam,
-                   "form": forms[0], "steps_in_config": w.steps,
-                   "l2": "inputs larger than L2 (per-step working set > 300 MB)",
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "config": workload_config(w, forms[0], world),
         "pair_interactions_per_s": head["pair_interactions_per_s"],
         "pairs_per_particle_step": head["pairs_per_particle_step"],
         "mass_drift_rel": head["mass_drift_rel"],
