@@ -612,6 +612,20 @@ struct DenseLists {
     uint32_t j[kWarpsPerBlock][kDenseCap];
     double v[kWarpsPerBlock][kDenseCap];
     uint8_t owner[kWarpsPerBlock][kDenseCap];
+    uint32_t off[kWarpsPerBlock][32];
+};
+
+// Binary64 neighbour lists: pass 1 stores each accepted neighbour j != s and
+// its kernel value K_sj (binary64) in slot k of s (entry at k * stride + s),
+// up to `cap` slots; count[s] is the full number.  Pass 2 of a warp whose
+// lanes all fit their lists reads them instead of searching and re-evaluating
+// exp; otherwise the warp searches.  Both paths visit the same pairs in the
+// same order with the same values.
+struct NbList64 {
+    uint32_t* j;
+    double* k;
+    uint32_t* count;
+    int cap;           // 0: no list
 };
 
 // Runs phases A-C for the calling warp.  eval(owner_s, j) returns the binary64
@@ -623,7 +637,7 @@ __device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t 
                                                 const uint32_t* __restrict__ cell,
                                                 const uint32_t* __restrict__ start,
                                                 const RealParams& P, DenseLists& L, Eval&& eval,
-                                                Add&& add) {
+                                                Add&& add, NbList64 store = NbList64{}) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t my_cell = valid ? cell[s] : 0u;
     uint32_t cnt = 0;
@@ -633,6 +647,11 @@ __device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t 
     uint32_t total;
     const uint32_t off = warp_exclusive_scan(cnt, &total);
     const uint32_t warp_s0 = s - uint32_t(lane);
+    if (store.cap > 0) {
+        L.off[warp][lane] = off;
+        if (valid) store.count[s] = cnt;
+        __syncwarp();
+    }
     for (uint32_t chunk = 0; chunk < total; chunk += kDenseCap) {
         const uint32_t chunk_end = chunk + kDenseCap;
         if (valid && cnt > 0 && off < chunk_end && off + cnt > chunk) {
@@ -649,8 +668,19 @@ __device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t 
         }
         __syncwarp();
         const uint32_t m = min(total - chunk, uint32_t(kDenseCap));
-        for (uint32_t e = uint32_t(lane); e < m; e += 32)
-            L.v[warp][e] = eval(warp_s0 + L.owner[warp][e], L.j[warp][e]);
+        for (uint32_t e = uint32_t(lane); e < m; e += 32) {
+            const uint32_t o = L.owner[warp][e], j = L.j[warp][e];
+            const double val = eval(warp_s0 + o, j);
+            L.v[warp][e] = val;
+            if (store.cap > 0) {
+                const uint32_t k = chunk + e - L.off[warp][o];
+                if (k < uint32_t(store.cap)) {
+                    const int64_t at = int64_t(k) * stride + (warp_s0 + o);
+                    store.j[at] = j;
+                    store.k[at] = val;
+                }
+            }
+        }
         __syncwarp();
         if (valid) {
             const uint32_t q0 = max(off, chunk), q1 = min(off + cnt, chunk_end);
@@ -661,6 +691,41 @@ __device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t 
     return cnt;
 }
 
+// Phases B-C over stored lists (the warp's lanes all fit their lists):
+// eval(owner_s, j, K) returns the binary64 pair term.
+template <class Eval, class Add>
+__device__ __forceinline__ void dense_listed(bool valid, uint32_t s, int64_t stride,
+                                             uint32_t cnt, const NbList64& nb, DenseLists& L,
+                                             Eval&& eval, Add&& add) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t total;
+    const uint32_t off = warp_exclusive_scan(cnt, &total);
+    const uint32_t warp_s0 = s - uint32_t(lane);
+    for (uint32_t chunk = 0; chunk < total; chunk += kDenseCap) {
+        const uint32_t chunk_end = chunk + kDenseCap;
+        if (valid) {
+            const uint32_t q0 = max(off, chunk), q1 = min(off + cnt, chunk_end);
+            for (uint32_t q = q0; q < q1; ++q) {
+                L.owner[warp][q - chunk] = uint8_t(lane);
+                L.j[warp][q - chunk] = q - off;          // slot index within the owner
+            }
+        }
+        __syncwarp();
+        const uint32_t m = min(total - chunk, uint32_t(kDenseCap));
+        for (uint32_t e = uint32_t(lane); e < m; e += 32) {
+            const uint32_t so = warp_s0 + L.owner[warp][e];
+            const int64_t at = int64_t(L.j[warp][e]) * stride + so;
+            L.v[warp][e] = eval(so, __ldg(nb.j + at), __ldg(nb.k + at));
+        }
+        __syncwarp();
+        if (valid) {
+            const uint32_t q0 = max(off, chunk), q1 = min(off + cnt, chunk_end);
+            for (uint32_t q = q0; q < q1; ++q) add(L.v[warp][q - chunk]);
+        }
+        __syncwarp();
+    }
+}
+
 // Pass 1, binary64 form: r_s = 1 + sum_{j != s} exp(-a d2_sj) (the kernel
 // without its constant factor, which cancels in W; the self term is 1), and
 // the ordered pair count.
@@ -669,7 +734,8 @@ __global__ void __launch_bounds__(kBlock)
 k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
              const double* __restrict__ exp_table, const __grid_constant__ View v,
-             double* __restrict__ r_out, unsigned long long* __restrict__ pair_counter) {
+             double* __restrict__ r_out, unsigned long long* __restrict__ pair_counter,
+             NbList64 nb) {
     __shared__ double table[64];
     __shared__ DenseLists lists;
     if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
@@ -684,8 +750,9 @@ k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4
             const RealParams& Po = v.of_sorted(so);
             return exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), Po.pp.a), table, Po.pp.ec);
         },
-        [&](double K) { r = __dadd_rn(r, K); });
+        [&](double K) { r = __dadd_rn(r, K); }, nb);
     if (s < n) r_out[s] = r;
+    if (nb.cap > 0 && s < n && !valid) nb.count[s] = 0u;
     add_pair_count(valid ? cnt : 0u, pair_counter);
 }
 
@@ -696,7 +763,7 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
                const double* __restrict__ exp_table, const __grid_constant__ View v,
                const double* __restrict__ r, const double* __restrict__ mass,
-               double* __restrict__ mass_out) {
+               double* __restrict__ mass_out, NbList64 nb) {
     __shared__ double table[64];
     __shared__ DenseLists lists;
     if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
@@ -705,16 +772,26 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
     const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
     const bool valid = s < n && P.transfer;
     double acc = 0.0;
-    dense_pairs<DIM>(
-        valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
-        [&](uint32_t so, uint32_t j) {
-            const RealParams& Po = v.of_sorted(so);
-            const double K = exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), Po.pp.a), table,
-                                     Po.pp.ec);
-            const double W = __ddiv_rn(__dmul_rn(2.0, K), __dadd_rn(__ldg(r + so), __ldg(r + j)));
-            return __dmul_rn(__dsub_rn(__ldg(mass + j), __ldg(mass + so)), W);
-        },
-        [&](double f) { acc = __dadd_rn(acc, f); });
+    auto flux = [&](uint32_t so, uint32_t j, double K) {
+        const double W = __ddiv_rn(__dmul_rn(2.0, K), __dadd_rn(__ldg(r + so), __ldg(r + j)));
+        return __dmul_rn(__dsub_rn(__ldg(mass + j), __ldg(mass + so)), W);
+    };
+    const uint32_t listed = (nb.cap > 0 && valid) ? nb.count[s] : 0u;
+    const bool fits = nb.cap > 0 && __all_sync(0xffffffffu, listed <= uint32_t(nb.cap));
+    if (fits) {
+        dense_listed(valid, uint32_t(s), stride, listed, nb, lists, flux,
+                     [&](double f) { acc = __dadd_rn(acc, f); });
+    } else {
+        dense_pairs<DIM>(
+            valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
+            [&](uint32_t so, uint32_t j) {
+                const RealParams& Po = v.of_sorted(so);
+                const double K = exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), Po.pp.a),
+                                         table, Po.pp.ec);
+                return flux(so, j, K);
+            },
+            [&](double f) { acc = __dadd_rn(acc, f); });
+    }
     if (s < n) mass_out[s] = valid ? __dadd_rn(mass[s], __dmul_rn(P.pp.beta, acc)) : mass[s];
 }
 

@@ -133,6 +133,9 @@ struct mtpt_handle {
     DevBuf<RealParams> params_dev;
     DevBuf<double> r64;
     DevBuf<float2> msplit;
+    DevBuf<uint32_t> nb_j, nb_count;      // binary64 form neighbour lists
+    DevBuf<double> nb_k;
+    int nb_cap = 0;
     DevBuf<double> out_tmp;
     DevBuf<double> exp_table;
     DevBuf<uint32_t> status;
@@ -375,6 +378,21 @@ int setup_grids(mtpt_handle* h) {
         h->any_walk |= h->params[k].walk != 0;
     }
     if (cell_base > int64_t(0xffffffffLL) - kScanTile) return MTPT_ERR_INVALID_ARG;
+    // binary64 neighbour-list slots: the expected neighbour count of the
+    // densest realisation (density x volume of the cutoff ball) plus four
+    // standard deviations of its Poisson spread plus 4, within [8, 64]
+    double expect = 0.0;
+    for (int k = 0; k < h->nreal; ++k) {
+        const mtpt_params& p = h->reals[k].prm;
+        double vol = 1.0;
+        for (int a = 0; a < p.dim; ++a) vol *= p.hi[a] - p.lo[a];
+        const double ball = p.dim == 1 ? 2.0 : (p.dim == 2 ? M_PI : 4.0 * M_PI / 3.0);
+        expect = std::max(expect, double(h->reals[k].n) / vol * ball *
+                                      std::pow(h->reals[k].psi, double(p.dim)));
+    }
+    h->nb_cap = h->precision == MTPT_FP64
+                    ? int(std::min(64.0, std::max(8.0, std::ceil(expect + 4.0 * std::sqrt(expect) + 4.0))))
+                    : 0;
     h->n_cells = cell_base;
     h->n_corners = corner_base;
     h->n_cells_pad = ((h->n_cells + 1 + kScanTile - 1) / kScanTile) * kScanTile;
@@ -438,6 +456,13 @@ int ensure_cells(mtpt_handle* h) {
     }
     if (size_t(std::max(h->n_corners, 1)) > h->corners.count) drop_graph(h);
     MTPT_TRY(h->corners.ensure(size_t(std::max(h->n_corners, 1))));
+    if (h->nb_cap > 0) {
+        const size_t slots = size_t(h->nb_cap) * size_t(h->cap);
+        if (slots > h->nb_j.count || size_t(h->cap) > h->nb_count.count) drop_graph(h);
+        MTPT_TRY(h->nb_j.ensure(slots));
+        MTPT_TRY(h->nb_k.ensure(slots));
+        MTPT_TRY(h->nb_count.ensure(size_t(h->cap)));
+    }
     // counts start (and, after each scatter, end) at zero
     MTPT_CUDA_TRY(cudaMemsetAsync(h->count.p, 0, padded * sizeof(uint32_t), h->stream));
     return MTPT_OK;
@@ -616,12 +641,12 @@ int launch_step(mtpt_handle* h, int flags) {
             MTPT_TIMED(h, "rowsum_f64");
             k_rowsum_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
                 n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
-                h->pair_counter.p);
+                h->pair_counter.p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap});
         }
         MTPT_TIMED(h, "exchange_f64");
         k_exchange_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
             n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
-            h->mass[o].p, h->mass[c].p);
+            h->mass[o].p, h->mass[c].p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap});
     } else {
         if (h->pair_block == 128) {
             MTPT_TRY((launch_pairs_f32<DIM, View, 128>(h, n, stride, pos_s, vs, o, c)));
@@ -1129,6 +1154,7 @@ int mtpt_destroy(mtpt_handle* h) {
     h->tan[0].release(); h->tan[1].release(); h->snaps.release(); h->dr64.release();
     h->lam_in.release(); h->lam_s.release(); h->lam_new.release(); h->gD.release();
     h->partial.release(); h->acc.release();
+    h->nb_j.release(); h->nb_k.release(); h->nb_count.release();
     for (auto& pe : h->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
@@ -1539,6 +1565,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.reals[0].n = n;
     h.params[0].id_offset = 0;
     MTPT_TRY(setup_grids(&h));
+    h.nb_cap = 0;                        // no neighbour lists: pass 2 searches
     const int d = h.dim;
     const size_t cells_pad = size_t(h.n_cells_pad);
 
