@@ -12,8 +12,8 @@
 //   mass[s], id[s]       binary64 mass, uint32 input index (keys the walk)
 //   cell[s]              linear cell index of particle s
 //   rec[s]               float4: binary32 offsets of the particle from its
-//                        cell's lower corner (x, y, z), and in .w the
-//                        precision form's row sum r_s once pass 1 has run
+//                        cell's lower corner (x, y, z), and in .w the cell's
+//                        x index (a small integer, exact in binary32)
 //   start[c]             first particle of cell c (exclusive prefix sum)
 // Cells are row-major (x fastest), so the three cells (cx-1..cx+1) of one
 // neighbour row are one contiguous particle range.
@@ -456,7 +456,7 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
             off[a] = __fadd_rn(__fsub_rn(xh, cr.x), __fsub_rn(xlo, cr.y));
         }
     }
-    rec_out[dst] = make_float4(off[0], off[1], off[2], 0.0f);
+    rec_out[dst] = make_float4(off[0], off[1], off[2], float((c - P.cell_base) % uint32_t(P.g.n[0])));
 }
 
 // ---------------------------------------------------------------------------
@@ -531,17 +531,73 @@ __device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int6
             const uint32_t row = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
                                                 uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
             const uint32_t j0 = __ldg(start + row + xlo);
-            const uint32_t b1 = __ldg(start + row + c[0]);
-            const uint32_t b2 = __ldg(start + row + c[0] + 1);
             const uint32_t j3 = __ldg(start + row + xhi + 1);
 #pragma unroll 2
             for (uint32_t j = j0; j < j3; ++j) {
                 const float4 o = __ldg(rec + j);
-                const float sx = j < b1 ? -wx : (j < b2 ? 0.0f : wx);
+                // (cx_j - cx_s) w: -w, 0 or w, exactly antisymmetric in the pair
+                const float sx = __fmul_rn(__fsub_rn(o.w, me.w), wx);
                 const float d2f = d2_f32<DIM>(me, o, sx, sy, sz);
                 if (d2f > pp.band_hi) continue;
                 if (d2f >= pp.band_lo && exact_d2<DIM>(pos, stride, s, j) > pp.psi2) continue;
                 visit(j, d2f, o);
+            }
+        }
+    }
+}
+
+// The exact binary64 test as a real call, so the compiler cannot if-convert
+// it into every candidate's path (it runs only inside the narrow band).
+template <int DIM>
+__device__ __noinline__ bool exact_within(const double* __restrict__ pos, int64_t stride,
+                                          uint32_t s, uint32_t j, double psi2) {
+    return exact_d2<DIM>(pos, stride, s, j) <= psi2;
+}
+
+// As visit_neighbours, but calls visit(j, d2f, accept) for every candidate
+// (the pass bodies run without a branch on the cutoff; the rare band case
+// takes the exact binary64 test).
+template <int DIM, class Visit>
+__device__ __forceinline__ void scan_neighbours(uint32_t s, uint32_t cell, int64_t stride,
+                                                const float4* __restrict__ rec,
+                                                const double* __restrict__ pos,
+                                                const uint32_t* __restrict__ start,
+                                                const RealParams& P, Visit&& visit) {
+    const Grid& g = P.g;
+    const PairParams& pp = P.pp;
+    int c[3] = {0, 0, 0};
+    {
+        uint32_t rest = cell - P.cell_base;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = int(rest % uint32_t(g.n[a]));
+            rest /= uint32_t(g.n[a]);
+        }
+    }
+    const float4 me = rec[s];
+    const int xlo = c[0] > 0 ? c[0] - 1 : 0;
+    const int xhi = c[0] < g.n[0] - 1 ? c[0] + 1 : c[0];
+    const int zlo = DIM == 3 ? (c[2] > 0 ? -1 : 0) : 0;
+    const int zhi = DIM == 3 ? (c[2] < g.n[2] - 1 ? 1 : 0) : 0;
+    const int ylo = DIM >= 2 ? (c[1] > 0 ? -1 : 0) : 0;
+    const int yhi = DIM >= 2 ? (c[1] < g.n[1] - 1 ? 1 : 0) : 0;
+    const float wx = g.wf[0];
+    for (int dz = zlo; dz <= zhi; ++dz) {
+        const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
+        for (int dy = ylo; dy <= yhi; ++dy) {
+            const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
+            const uint32_t row = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
+                                                uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
+            const uint32_t j0 = __ldg(start + row + xlo);
+            const uint32_t j3 = __ldg(start + row + xhi + 1);
+            for (uint32_t j = j0; j < j3; ++j) {
+                const float4 o = __ldg(rec + j);
+                const float sx = __fmul_rn(__fsub_rn(o.w, me.w), wx);
+                const float d2f = d2_f32<DIM>(me, o, sx, sy, sz);
+                bool accept = d2f < pp.band_lo;
+                if (d2f >= pp.band_lo && d2f <= pp.band_hi)
+                    accept = exact_within<DIM>(pos, stride, s, j, pp.psi2);
+                visit(j, d2f, accept);
             }
         }
     }
@@ -799,9 +855,10 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
 // hardware ex2, compensated binary32 row sum, rounded to binary32 into rec.w.
 template <int DIM, class View, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)
-k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, float4* __restrict__ rec,
+k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
-             const __grid_constant__ View v, unsigned long long* __restrict__ pair_counter) {
+             const __grid_constant__ View v, float* __restrict__ r_out,
+             unsigned long long* __restrict__ pair_counter) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cnt = 0;
     if (s < n) {
@@ -809,17 +866,21 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, float4* __re
         float rsum = 0.0f, rc = 0.0f;
         if (P.transfer) {
             const float na = -P.pp.a_log2e;
-            visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
-                                  [&](uint32_t, float d2f, const float4&) {
-                                      kahan_add(rsum, rc, ex2_approx(na * d2f));
-                                      ++cnt;
-                                  });
+            scan_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
+                                 [&](uint32_t, float d2f, bool accept) {
+                                     // Kahan step, kept only for accepted pairs
+                                     const float y = __fsub_rn(ex2_approx(na * d2f), rc);
+                                     const float t = __fadd_rn(rsum, y);
+                                     const float cn = __fsub_rn(__fsub_rn(t, rsum), y);
+                                     rsum = accept ? t : rsum;
+                                     rc = accept ? cn : rc;
+                                     cnt += accept ? 1u : 0u;
+                                 });
             cnt -= 1;   // the self pair
         } else {
             rsum = 1.0f;
         }
-        // only .w changes; concurrent readers of this record use .x-.z
-        reinterpret_cast<float*>(rec + s)[3] = __fsub_rn(rsum, rc);
+        r_out[s] = __fsub_rn(rsum, rc);
     }
     add_pair_count(cnt, pair_counter);
 }
@@ -831,8 +892,9 @@ template <int DIM, class View, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
-               const __grid_constant__ View v, const float2* __restrict__ msplit,
-               const double* __restrict__ mass, double* __restrict__ mass_out) {
+               const __grid_constant__ View v, const float* __restrict__ r,
+               const float2* __restrict__ msplit, const double* __restrict__ mass,
+               double* __restrict__ mass_out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const RealParams& P = v.of_sorted(uint32_t(s));
@@ -840,19 +902,20 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
         mass_out[s] = mass[s];
         return;
     }
-    const float rs = rec[s].w;
+    const float rs = r[s];
     const float2 ms = msplit[s];
     float acc = 0.0f, comp = 0.0f;
     const float na = -P.pp.a_log2e;
     const float two_beta = float(2.0 * P.pp.beta);   // beta folded into W (still symmetric)
-    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
-                          [&](uint32_t j, float d2f, const float4& o) {
-                              const float K = ex2_approx(na * d2f);
-                              const float W = __fdividef(two_beta * K, __fadd_rn(rs, o.w));
-                              const float2 mj = __ldg(msplit + j);
-                              const float dm = __fadd_rn(__fsub_rn(mj.x, ms.x), __fsub_rn(mj.y, ms.y));
-                              neumaier_add(acc, comp, __fmul_rn(dm, W));
-                          });
+    scan_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
+                         [&](uint32_t j, float d2f, bool accept) {
+                             const float K = ex2_approx(na * d2f);
+                             const float W = __fdividef(two_beta * K, __fadd_rn(rs, __ldg(r + j)));
+                             const float2 mj = __ldg(msplit + j);
+                             const float dm = __fadd_rn(__fsub_rn(mj.x, ms.x), __fsub_rn(mj.y, ms.y));
+                             // a rejected candidate adds an exact zero: no change
+                             neumaier_add(acc, comp, accept ? __fmul_rn(dm, W) : 0.0f);
+                         });
     // two binary64 additions per particle: acc + comp is exact in binary64
     const double delta = __dadd_rn(f32_to_f64(acc), f32_to_f64(comp));
     mass_out[s] = __dadd_rn(mass[s], delta);

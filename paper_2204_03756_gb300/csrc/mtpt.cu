@@ -132,6 +132,7 @@ struct mtpt_handle {
     DevBuf<uint32_t> id_first;
     DevBuf<RealParams> params_dev;
     DevBuf<double> r64;
+    DevBuf<float> r32;
     DevBuf<float2> msplit;
     DevBuf<uint32_t> nb_j, nb_count;      // binary64 form neighbour lists
     DevBuf<double> nb_k;
@@ -437,6 +438,7 @@ int ensure_capacity(mtpt_handle* h, int64_t n) {
             MTPT_TRY(h->r64.ensure(cap));
         } else {
             MTPT_TRY(h->msplit.ensure(cap));
+            MTPT_TRY(h->r32.ensure(cap));
         }
         h->cap = cap;
     }
@@ -565,12 +567,12 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
     {
         MTPT_TIMED(h, "rowsum_f32");
         k_rowsum_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
-            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->pair_counter.p);
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->r32.p, h->pair_counter.p);
     }
     MTPT_TIMED(h, "exchange_f32");
     k_exchange_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
-        n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->msplit.p, h->mass[o].p,
-        h->mass[c].p);
+        n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->r32.p, h->msplit.p,
+        h->mass[o].p, h->mass[c].p);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -1148,7 +1150,8 @@ int mtpt_destroy(mtpt_handle* h) {
     h->key.release(); h->perm.release(); h->cell.release(); h->count.release();
     h->start.release(); h->tile_sums.release(); h->rec.release(); h->corners.release();
     h->corner_first.release(); h->id_first.release(); h->params_dev.release();
-    h->r64.release(); h->msplit.release(); h->out_tmp.release(); h->exp_table.release();
+    h->r64.release(); h->r32.release(); h->msplit.release(); h->out_tmp.release();
+    h->exp_table.release();
     h->status.release(); h->pair_counter.release(); h->step_dev.release();
     h->emit_counter.release(); h->emit_i.release(); h->emit_j.release();
     h->tan[0].release(); h->tan[1].release(); h->snaps.release(); h->dr64.release();
@@ -1258,9 +1261,8 @@ int mtpt_get_row_sums(mtpt_handle* h, double* out) {
             if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, double>(h, h->r64.p, 1)));
             else MTPT_TRY((launch_row_sums_out<SingleView, double>(h, h->r64.p, 1)));
         } else {
-            const float* rw = reinterpret_cast<const float*>(h->rec.p) + 3;
-            if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, float>(h, rw, 4)));
-            else MTPT_TRY((launch_row_sums_out<SingleView, float>(h, rw, 4)));
+            if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, float>(h, h->r32.p, 1)));
+            else MTPT_TRY((launch_row_sums_out<SingleView, float>(h, h->r32.p, 1)));
         }
     }
     return copy_out_host(h, 1, out);
@@ -1583,6 +1585,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
         h.r64.p = cv.take<double>(size_t(n));
     } else {
         h.msplit.p = cv.take<float2>(size_t(n));
+        h.r32.p = cv.take<float>(size_t(n));
     }
     h.corners.p = cv.take<float2>(size_t(std::max(h.n_corners, 1)));
     h.count.p = cv.take<uint32_t>(cells_pad);
