@@ -322,13 +322,15 @@ def time_adjoint(rank, nbins=(100, 100), checkpoint_every=20):
             "precision": "forward fp32w, adjoint passes f64"}
 
 
-# binary64 instructions per accepted ordered pair of the binary64 pair passes
-# (exact squared distance 3d - 1, exp by Tang's table method 11, the scaling
-# by a 1, the row-sum add 1; exchange adds 2K, r_i + r_j, the IEEE division
-# (8 on GB300, measured), the mass difference and the product)
+# binary64 instructions per accepted ordered pair of the binary64 pair passes:
+# rowsum -- squared distance 2d (a difference and a multiply or fma per axis),
+# the kernel exponential 7 (2 fma reduction, 4 fma polynomial, 1 table
+# multiply; the reduction index and the 2^-q scaling are integer/binary32),
+# the row-sum add 1; exchange (kernel values read back from the neighbour
+# lists) -- r_i + r_j 1, the quotient 5 (Newton step 2, product 1,
+# correction 2), the mass difference, the product and the flux add 3.
 def _f64_ops_per_pair(kernel: str, dim: int) -> float:
-    d2 = 3 * dim - 1
-    return {"rowsum_f64": d2 + 1 + 11 + 1, "exchange_f64": d2 + 1 + 11 + 2 + 8 + 2}[kernel]
+    return {"rowsum_f64": 2 * dim + 7 + 1, "exchange_f64": 1 + 5 + 3}[kernel]
 
 
 # GB300 binary64 issue rate: 2 binary64 operations per clock per SM (recipe's

@@ -74,7 +74,10 @@ enum {
  * dt > 0; beta > 0 (the paper takes 1); lambda > 0 (the paper's Eq. "cutoff"
  * prints 6, its cost analysis uses 3 in this notation; see the design notes);
  * lo[a] < hi[a] for a < dim (entries a >= dim are ignored); seed keys the
- * counter-based generator of the walk. */
+ * counter-based generator of the walk.  The create and set calls also reject
+ * (MTPT_ERR_INVALID_ARG) lambda > 20, |lo[a]| or |hi[a]| above 1e15, and a
+ * kernel variance h^2 = 2 (1 - kappa) D dt / beta that is positive but below
+ * 1e-35. */
 typedef struct mtpt_params {
     int32_t dim;
     int32_t precision;      /* an mtpt_precision */

@@ -1,46 +1,76 @@
-// expneg.cuh -- exp(-t) in binary64 for the pair kernel K = exp(-|dx|^2 / (2 h^2)).
+// expneg.cuh -- K = exp(-a d2) in binary64 for the pair kernel (Eq. 4 with
+// a = 1 / (2 h^2)).
 //
 // Table-driven method of P. T. P. Tang, "Table-driven implementation of the
 // exponential function in IEEE floating-point arithmetic", ACM TOMS 15(2),
-// 1989: write t = (64 q + j) ln2/64 + r with |r| <= ln2/128, j in [0, 64),
-// so exp(-t) = 2^-q * 2^(-j/64) * exp(-r).  2^(-j/64) comes from a 64-entry
-// table computed on the host, exp(-r) from its Taylor series through r^5
-// (the first omitted term is below 4e-17 relative), and 2^-q is applied to
-// the exponent field.  r is formed with ln2/64 split in two parts and fused
-// multiply-adds, so its absolute error stays below 1e-18.  Valid for
-// 0 <= t <= 700 (the result stays a normal number); the pair kernel only
-// evaluates t <= lambda^2 (1 + 1e-4).
+// 1989, arranged so that only the parts that set the accuracy use binary64
+// (GB300 runs binary64 at about 1/70 of the binary32 rate):
 //
-// Cost: 10 binary64 operations (1 mul, 2 add, 7 fma/mul) against the ~2x
-// longer general-purpose exp; on GB300 every binary64 operation costs about
-// 70 binary32 ones, so this is the pair loop's dominant arithmetic.
+//   t = a d2 = k ln2/256 + a r,   k = round(t 256 / ln 2),
+//   exp(-t) = 2^-(k >> 8) * 2^(-(k & 255)/256) * exp(-a r).
+//
+// * k comes from the binary32 head of d2 (bit truncation, no binary64
+//   instruction) times a 256 / ln 2 in binary32: it is within 0.53 of
+//   t 256 / ln 2 for t <= 400, so |a r| <= 0.53 ln2 / 256 < 1.44e-3.  Any k
+//   gives a correct reduction; only the bound on r depends on it.
+// * r = d2 - k c with c = ln 2 / (256 a) held as c_hi + c_lo, c_hi with 32
+//   significant bits so k c_hi is exact for k < 2^21; two fma.
+// * exp(-a r) is its Taylor series through (a r)^4 with a folded into the
+//   coefficients p_m = (-a)^m / m! (four fma on r; the first omitted term is
+//   below 5e-17 relative), so no binary64 multiply forms a r or t.
+// * 2^(-j/256) is a 256-entry host table; 2^-(k >> 8) goes into the exponent
+//   field with an integer subtraction.
+//
+// Cost: 7 binary64 operations (2 + 4 fma, 1 mul) and integer/binary32 work.
+// Valid for 0 <= a d2 <= 400.1 (lambda <= 20 with the band margin: the
+// result stays normal) and a <= 5e34: the binary32 scale and p_4 stay finite,
+// and a d2 whose head underflows binary32 (d2 < 2^-126, so k = 0) has
+// a d2 < 6e-4, inside the polynomial's range.  The host rejects parameters
+// outside.  Error: within 1.5 ulp of exp(-a d2) for the binary64 a and d2.
 #pragma once
 #include <cstdint>
 
 namespace mtpt {
 
+constexpr int kExpTable = 256;
+
 struct ExpNegConsts {
-    double inv_step;   // 64 / ln 2
-    double step_hi;    // ln 2 / 64, leading part
-    double step_lo;    // ln 2 / 64 - step_hi
+    float k_scale;      // a * 256 / ln 2 in binary32
+    double c_hi, c_lo;  // ln 2 / (256 a) = c_hi + c_lo
+    double p1, p2, p3, p4;   // (-a)^m / m!
 };
 
-__device__ __forceinline__ double exp_neg(double t, const double* __restrict__ table,
-                                          const ExpNegConsts& c) {
-    constexpr double kRound = 6755399441055744.0;   // 1.5 * 2^52: adding it rounds to an integer
-    const double y = __dadd_rn(__dmul_rn(t, c.inv_step), kRound);
-    const int k = __double2loint(y);                 // round(t * 64 / ln 2), >= 0
-    const double kd = __dsub_rn(y, kRound);
-    double r = __fma_rn(-kd, c.step_hi, t);
-    r = __fma_rn(-kd, c.step_lo, r);
-    const double s = -r;
-    double p = __fma_rn(s, 1.0 / 120.0, 1.0 / 24.0);
-    p = __fma_rn(s, p, 1.0 / 6.0);
-    p = __fma_rn(s, p, 0.5);
-    p = __fma_rn(s, p, 1.0);
-    p = __fma_rn(s, p, 1.0);
-    const double v = __dmul_rn(table[k & 63], p);
-    const long long scaled = __double_as_longlong(v) - (static_cast<long long>(k >> 6) << 52);
+// Head of a binary64 x >= 0 with x < 2^128 as binary32, truncated (integer
+// operations only); 0 below 2^-126.
+__device__ __forceinline__ float head_f32(double x) {
+    const uint32_t whi = uint32_t(__double2hiint(x));
+    const uint32_t wlo = uint32_t(__double2loint(x));
+    const int e = int(whi >> 20);
+    const uint32_t bits = (uint32_t(e - 896) << 23) | ((whi & 0xfffffu) << 3) | (wlo >> 29);
+    return e < 897 ? 0.0f : __uint_as_float(bits);
+}
+
+// Exact binary64 image of 0 <= k < 2^31 from integer operations.
+__device__ __forceinline__ double small_uint_to_f64(uint32_t k) {
+    const int m = 31 - __clz(int(k | 1u));
+    const uint64_t mant = (uint64_t(k) << (52 - m)) & 0xfffffffffffffull;
+    const double v = __longlong_as_double((long long)((uint64_t(1023 + m) << 52) | mant));
+    return k == 0u ? 0.0 : v;
+}
+
+__device__ __forceinline__ double gauss_exp(double d2, const double* __restrict__ table,
+                                            const ExpNegConsts& c) {
+    const float yk = __fmaf_rn(head_f32(d2), c.k_scale, 12582912.0f);   // + 1.5 * 2^23
+    const uint32_t k = uint32_t(__float_as_int(yk) - 0x4b400000);
+    const double kd = small_uint_to_f64(k);
+    double r = __fma_rn(-kd, c.c_hi, d2);
+    r = __fma_rn(-kd, c.c_lo, r);
+    double p = __fma_rn(c.p4, r, c.p3);
+    p = __fma_rn(p, r, c.p2);
+    p = __fma_rn(p, r, c.p1);
+    p = __fma_rn(p, r, 1.0);
+    const double v = __dmul_rn(table[k & (kExpTable - 1)], p);
+    const long long scaled = __double_as_longlong(v) - (static_cast<long long>(k >> 8) << 52);
     return __longlong_as_double(scaled);
 }
 

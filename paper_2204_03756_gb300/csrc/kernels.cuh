@@ -143,6 +143,21 @@ __device__ __forceinline__ double f32_to_f64(float f) {
     return __hiloint2double(int(sign | ((e + 896u) << 20) | (m >> 3)), int(m << 29));
 }
 
+// num / den for num >= 0 and 1 <= den < 2^127 with binary64 fma only: a
+// binary32 reciprocal seed (relative error below 2^-21 after the head
+// truncation), one Newton-Raphson step for 1/den (error below 2^-41), then
+// the quotient and one residual correction q + (num - den q) / den (P.
+// Markstein, "IA-64 and Elementary Functions", 2000, ch. 8), which leaves an
+// error below one unit in the last place.  Five binary64 operations.
+__device__ __forceinline__ double quot_pos(double num, double den) {
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(head_f32(den)));
+    double y = f32_to_f64(y0);
+    y = __fma_rn(y, __fma_rn(-den, y, 1.0), y);
+    const double q = __dmul_rn(num, y);
+    return __fma_rn(__fma_rn(-den, q, num), y, q);
+}
+
 // True when x is an infinity or a NaN (integer test on the exponent field).
 __device__ __forceinline__ bool not_finite(double x) {
     return (uint32_t(__double2hiint(x)) & 0x7ff00000u) == 0x7ff00000u;
@@ -487,6 +502,21 @@ __device__ __forceinline__ double exact_d2(const double* __restrict__ pos, int64
     return d2;
 }
 
+// Squared distance for the kernel value (not for the pair test): one fma per
+// axis after the first.  Symmetric in (i, j) bit for bit (the differences
+// only change sign), and within 2 ulp of the exact square sum.
+template <int DIM>
+__device__ __forceinline__ double kernel_d2(const double* __restrict__ pos, int64_t stride,
+                                            uint32_t i, uint32_t j) {
+    double d2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const double d = __dsub_rn(__ldg(pos + a * stride + i), __ldg(pos + a * stride + j));
+        d2 = (a == 0) ? __dmul_rn(d, d) : __fma_rn(d, d, d2);
+    }
+    return d2;
+}
+
 template <int DIM>
 __device__ __forceinline__ float d2_f32(const float4& me, const float4& o, float sx, float sy,
                                         float sz) {
@@ -792,9 +822,9 @@ k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4
              const double* __restrict__ exp_table, const __grid_constant__ View v,
              double* __restrict__ r_out, unsigned long long* __restrict__ pair_counter,
              NbList64 nb) {
-    __shared__ double table[64];
+    __shared__ double table[kExpTable];
     __shared__ DenseLists lists;
-    if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
+    for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
@@ -804,7 +834,7 @@ k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4
         valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
         [&](uint32_t so, uint32_t j) {
             const RealParams& Po = v.of_sorted(so);
-            return exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), Po.pp.a), table, Po.pp.ec);
+            return gauss_exp(kernel_d2<DIM>(pos, stride, so, j), table, Po.pp.ec);
         },
         [&](double K) { r = __dadd_rn(r, K); }, nb);
     if (s < n) r_out[s] = r;
@@ -820,16 +850,19 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
                const double* __restrict__ exp_table, const __grid_constant__ View v,
                const double* __restrict__ r, const double* __restrict__ mass,
                double* __restrict__ mass_out, NbList64 nb) {
-    __shared__ double table[64];
+    __shared__ double table[kExpTable];
     __shared__ DenseLists lists;
-    if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
+    for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
     const bool valid = s < n && P.transfer;
     double acc = 0.0;
     auto flux = [&](uint32_t so, uint32_t j, double K) {
-        const double W = __ddiv_rn(__dmul_rn(2.0, K), __dadd_rn(__ldg(r + so), __ldg(r + j)));
+        // 2K by an exponent increment (K is a positive normal), so
+        // W = 2K / (r_s + r_j) rounds once
+        const double K2 = __longlong_as_double(__double_as_longlong(K) + (1LL << 52));
+        const double W = quot_pos(K2, __dadd_rn(__ldg(r + so), __ldg(r + j)));
         return __dmul_rn(__dsub_rn(__ldg(mass + j), __ldg(mass + so)), W);
     };
     const uint32_t listed = (nb.cap > 0 && valid) ? nb.count[s] : 0u;
@@ -842,8 +875,7 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
             valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
             [&](uint32_t so, uint32_t j) {
                 const RealParams& Po = v.of_sorted(so);
-                const double K = exp_neg(__dmul_rn(exact_d2<DIM>(pos, stride, so, j), Po.pp.a),
-                                         table, Po.pp.ec);
+                const double K = gauss_exp(kernel_d2<DIM>(pos, stride, so, j), table, Po.pp.ec);
                 return flux(so, j, K);
             },
             [&](double f) { acc = __dadd_rn(acc, f); });
@@ -967,11 +999,10 @@ __device__ __forceinline__ void pair_terms(const double* __restrict__ pos,
     for (int a = 0; a < DIM; ++a) {
         const double d = __dsub_rn(__ldg(pos + a * stride + s), __ldg(pos + a * stride + j));
         const double dt = __dsub_rn(__ldg(tan + a * stride + s), __ldg(tan + a * stride + j));
-        const double sq = __dmul_rn(d, d);
-        d2 = (a == 0) ? sq : __dadd_rn(d2, sq);
+        d2 = (a == 0) ? __dmul_rn(d, d) : __fma_rn(d, d, d2);   // as kernel_d2
         dot = __fma_rn(d, dt, dot);
     }
-    *K = exp_neg(__dmul_rn(d2, P.pp.a), table, P.pp.ec);
+    *K = gauss_exp(d2, table, P.pp.ec);
     *dK = __dmul_rn(*K, __ddiv_rn(__fma_rn(d2, P.inv_2D, -dot), P.h2));
 }
 
@@ -983,8 +1014,8 @@ k_adj_rowsum(int n, int64_t stride, const double* __restrict__ pos, const double
              const uint32_t* __restrict__ start, const double* __restrict__ exp_table,
              const __grid_constant__ View v, double* __restrict__ r_out,
              double* __restrict__ dr_out) {
-    __shared__ double table[64];
-    if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
+    __shared__ double table[kExpTable];
+    for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -1016,8 +1047,8 @@ k_adj_exchange(int n, int64_t stride, const double* __restrict__ pos,
                const double* __restrict__ r, const double* __restrict__ dr,
                const double* __restrict__ mass, const double* __restrict__ lam,
                double* __restrict__ lam_out, double* __restrict__ gD) {
-    __shared__ double table[64];
-    if (threadIdx.x < 64) table[threadIdx.x] = exp_table[threadIdx.x];
+    __shared__ double table[kExpTable];
+    for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;

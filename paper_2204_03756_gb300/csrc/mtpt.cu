@@ -234,6 +234,11 @@ int validate_params(const mtpt_params* p) {
     if (!(p->dt > 0.0) || !std::isfinite(p->dt)) return MTPT_ERR_INVALID_ARG;
     if (!(p->beta > 0.0) || !std::isfinite(p->beta)) return MTPT_ERR_INVALID_ARG;
     if (!(p->lambda > 0.0 && p->lambda <= 20.0)) return MTPT_ERR_INVALID_ARG;
+    // kernel variance h^2 = 2 (1 - kappa) D dt / beta: 0 (no transfer) or at
+    // least 1e-35, so a = 1 / (2 h^2) <= 5e34 stays within the range of the
+    // binary64 kernel exponential
+    const double h2 = 2.0 * (1.0 - p->kappa) * p->D * p->dt / p->beta;
+    if (h2 > 0.0 && h2 < 1e-35) return MTPT_ERR_INVALID_ARG;
     for (int a = 0; a < p->dim; ++a) {
         if (!std::isfinite(p->lo[a]) || !std::isfinite(p->hi[a]) || !(p->lo[a] < p->hi[a]))
             return MTPT_ERR_INVALID_ARG;
@@ -356,11 +361,23 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
     pp.a = R.h2 > 0.0 ? 1.0 / (2.0 * R.h2) : 0.0;
     pp.a_log2e = float(pp.a * 1.4426950408889634);
     pp.beta = p.beta;
-    // ln 2 = ln2_hi + ln2_lo (leading and trailing binary64 parts)
-    const double ln2_hi = 6.93147180559945286227e-01, ln2_lo = 2.31904681384629955842e-17;
-    pp.ec.inv_step = 64.0 / ln2_hi;
-    pp.ec.step_hi = ln2_hi / 64.0;
-    pp.ec.step_lo = ln2_lo / 64.0;
+    // Constants of the binary64 kernel exponential exp(-a d2) (reduction step
+    // c = ln 2 / (256 a), c_hi with 32 significant bits; Taylor coefficients
+    // (-a)^m / m!), formed in long double.
+    pp.ec = ExpNegConsts{};
+    if (pp.a > 0.0) {
+        const long double ln2 = std::log(2.0L), a = pp.a;
+        const long double c = ln2 / (256.0L * a);
+        int e = 0;
+        const double m = std::frexp(double(c), &e);
+        pp.ec.c_hi = std::ldexp(std::nearbyint(std::ldexp(m, 32)), e - 32);
+        pp.ec.c_lo = double(c - (long double)pp.ec.c_hi);
+        pp.ec.k_scale = float(256.0L * a / ln2);
+        pp.ec.p1 = double(-a);
+        pp.ec.p2 = double(a * a / 2.0L);
+        pp.ec.p3 = double(-a * a * a / 6.0L);
+        pp.ec.p4 = double(a * a * a * a / 24.0L);
+    }
     return MTPT_OK;
 }
 
@@ -401,10 +418,11 @@ int setup_grids(mtpt_handle* h) {
 }
 
 double* exp_table_host() {
-    static double table[64];
+    static double table[kExpTable];
     static std::once_flag once;
     std::call_once(once, []() {
-        for (int j = 0; j < 64; ++j) table[j] = double(exp2l(-static_cast<long double>(j) / 64.0L));
+        for (int j = 0; j < kExpTable; ++j)
+            table[j] = double(exp2l(-static_cast<long double>(j) / static_cast<long double>(kExpTable)));
     });
     return table;
 }
@@ -789,8 +807,8 @@ int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, con
     if (h->any_transfer) MTPT_TRY(ensure_cells(h));
     drop_graph(h);
     if (!h->exp_table.p) {
-        MTPT_TRY(h->exp_table.ensure(64));
-        MTPT_CUDA_TRY(cudaMemcpyAsync(h->exp_table.p, exp_table_host(), 64 * sizeof(double),
+        MTPT_TRY(h->exp_table.ensure(kExpTable));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->exp_table.p, exp_table_host(), kExpTable * sizeof(double),
                                       cudaMemcpyHostToDevice, h->stream));
     }
     MTPT_TRY(upload_tables(h));
@@ -1591,7 +1609,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.count.p = cv.take<uint32_t>(cells_pad);
     h.start.p = cv.take<uint32_t>(cells_pad);
     h.tile_sums.p = cv.take<uint32_t>(cells_pad / kScanTile);
-    h.exp_table.p = cv.take<double>(64);
+    h.exp_table.p = cv.take<double>(kExpTable);
     h.status.p = cv.take<uint32_t>(1);
     h.pair_counter.p = cv.take<unsigned long long>(1);
     h.step_dev.p = cv.take<unsigned long long>(1);
@@ -1618,7 +1636,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     MTPT_CUDA_TRY(cudaMemsetAsync(h.status.p, 0, sizeof(uint32_t), st));
     MTPT_CUDA_TRY(cudaMemsetAsync(h.pair_counter.p, 0, sizeof(unsigned long long), st));
     k_set_step<<<1, 1, 0, st>>>(h.step_dev.p, (unsigned long long)step);
-    MTPT_CUDA_TRY(cudaMemcpyAsync(h.exp_table.p, exp_table_host(), 64 * sizeof(double),
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h.exp_table.p, exp_table_host(), kExpTable * sizeof(double),
                                   cudaMemcpyHostToDevice, st));
     // the one-entry realisation table and corner offsets for the corner kernel
     static thread_local int first_host[2];

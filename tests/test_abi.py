@@ -40,11 +40,12 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_parameter_validation_without_gpu(lib):
     good = dict(dim=2, D=1.0, kappa=0.5, dt=0.1, lo=(0, 0), hi=(10, 10))
-    h = mtpt.mtpt_create(mtpt.Params(**good))
-    mtpt.mtpt_destroy(h)
+    for ok in (good, dict(good, D=0.0), dict(good, kappa=1.0), dict(good, D=1e-31, dt=1e-3)):
+        mtpt.mtpt_destroy(mtpt.mtpt_create(mtpt.Params(**ok)))   # h^2 = 0 or >= 1e-35
     bad = [dict(dim=0), dict(dim=4), dict(kappa=1.5), dict(dt=0.0), dict(D=-1.0),
            dict(lo=(5, 0), hi=(1, 10)), dict(beta=0.0), dict(lam=0.0), dict(precision=7),
-           dict(D=float("nan"))]
+           dict(D=float("nan")), dict(lam=20.5), dict(lo=(-2e15, 0)),
+           dict(D=1e-33, dt=1e-3)]          # h^2 = 1e-36: below the kernel range
     for b in bad:
         kw = dict(good)
         kw.update(b)
