@@ -122,7 +122,11 @@ int mtpt_set_stream(mtpt_handle* h, void* stream);
 
 /* Load n particles from HOST buffers: pos (dim x n, SoA float64) and mass (n
  * float64).  Every coordinate must be finite and inside [lo, hi] of its axis
- * (MTPT_ERR_OUT_OF_DOMAIN otherwise, and the handle keeps its old state).
+ * (MTPT_ERR_OUT_OF_DOMAIN otherwise) and every mass finite, in the precision
+ * form at most 1e30 in magnitude (MTPT_ERR_INVALID_ARG otherwise); on either
+ * error the handle keeps its old state.  The buffers are copied into a device
+ * staging area (kept by the handle, (dim + 1) n float64) and checked there;
+ * the call returns once the host buffers are no longer read.
  * Particle ids are 0..n-1 in input order; they key the walk's generator.
  * Resets the step counter and pair counter to 0.  n = 0 is allowed. */
 int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass);

@@ -52,6 +52,8 @@ struct PairParams {
     double psi2;       // cutoff squared: the exact binary64 test d2 <= psi2
     float band_lo;     // binary32 d2 below this: certainly a neighbour
     float band_hi;     // binary32 d2 above this: certainly not a neighbour
+    float reach2;      // band_hi (1 + 2^-16): bounds dx^2 + dy^2 (+ dz^2) of a neighbour
+    float trim_eps;    // slack of the per-row candidate windows (see row_window)
     double a;          // 1 / (2 h^2)
     float a_log2e;     // a * log2(e) in binary32 (precision form)
     double beta;
@@ -272,6 +274,41 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
     }
 }
 
+// Check of host-loaded input in its device staging copy (positions dim x n
+// with stride n, then n masses): a position outside its realisation's box
+// [lo, hi] (NaN included) sets bit 1, a mass that is not finite or above
+// mass_limit in magnitude sets bit 2.  box holds lo[3], hi[3] per
+// realisation; first[k] is realisation k's first particle (first[nreal] = n).
+template <int DIM>
+__global__ void __launch_bounds__(kBlock)
+k_check_input(int n, int nreal, const double* __restrict__ pos, const double* __restrict__ mass,
+              const double* __restrict__ box, const uint32_t* __restrict__ first,
+              double mass_limit, uint32_t* __restrict__ flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t bad = 0;
+    if (i < n) {
+        int k = 0;
+        if (nreal > 1) {   // last k with first[k] <= i
+            int lo = 0, hi = nreal - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (first[mid] <= uint32_t(i)) lo = mid; else hi = mid - 1;
+            }
+            k = lo;
+        }
+        const double* b = box + 6 * k;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const double x = pos[int64_t(a) * n + i];
+            if (!(x >= b[a] && x <= b[3 + a])) bad |= 1u;
+        }
+        const double m = mass[i];
+        if (not_finite(m) || !(fabs(m) <= mass_limit)) bad |= 2u;
+    }
+    const uint32_t any = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && any) atomicOr(flags, any);
+}
+
 // Domain check of positions loaded from device memory.
 template <int DIM, class View>
 __global__ void k_check_domain(int n, int64_t stride, const double* __restrict__ pos,
@@ -420,8 +457,10 @@ k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ 
 }
 
 // Step 2c: gather into cell order.  The slot order the atomics gave inside a
-// cell is replaced by the rank of the particle id, so the layout (and every
-// sum over it) is identical run to run.  Also writes the particle's cell, its
+// cell is replaced by the rank of (x, id) -- binary64 x in its integer order,
+// the id breaking ties -- so the layout (and every sum over it) is identical
+// run to run, and each neighbour row (cells cx-1..cx+1 of one y (, z)) is
+// sorted by x up to the cells' rounding slack, which the pair search uses.  Also writes the particle's cell, its
 // binary32 offset from the cell corner (from the binary32 head/tail split of
 // the coordinate and of the corner: error below 2^-23 w, no binary64
 // instruction) and, in the precision form, the mass's head/tail split.
@@ -441,8 +480,13 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
     const uint32_t c = key[src];
     const uint32_t b = start[c], e = start[c + 1];
     const uint32_t my_id = id_in[src];
+    const long long my_x = order_key(pos_in[src]);
     uint32_t rank = 0;
-    for (uint32_t k = b; k < e; ++k) rank += (id_in[perm[k]] < my_id) ? 1u : 0u;
+    for (uint32_t k = b; k < e; ++k) {
+        const uint32_t o = perm[k];
+        const long long xo = order_key(pos_in[o]);
+        rank += (xo < my_x || (xo == my_x && id_in[o] < my_id)) ? 1u : 0u;
+    }
     const uint32_t dst = b + rank;
     id_out[dst] = my_id;
     cell_out[dst] = c;
@@ -475,8 +519,10 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Steps 2-5: neighbour visits.  For particle s (cell order) every particle j
-// in the 3^DIM surrounding cells is a candidate, s itself included.  The
+// Steps 2-5: neighbour visits.  For particle s (cell order) the candidates
+// are the particles of the 3^DIM surrounding cells, s itself included, each
+// neighbour row cut to the window of x that can reach the cutoff (see
+// for_each_row).  The
 // binary32 squared distance from the cell offsets decides every candidate
 // outside a narrow band around psi^2; inside the band the exact binary64 test
 // dx*dx + dy*dy (+ dz*dz) <= psi^2 (no fma, dx = x_i - x_j) decides.  The
@@ -517,10 +563,16 @@ __device__ __forceinline__ double kernel_d2(const double* __restrict__ pos, int6
     return d2;
 }
 
+// Binary32 x difference of candidate o from particle me (cells cx_o - cx_me
+// apart, |cx_o - cx_me| <= 1 so the shift is exact): changes sign exactly
+// when the pair swaps.
+__device__ __forceinline__ float dx_f32(const float4& me, const float4& o, float wx) {
+    return __fadd_rn(__fsub_rn(o.x, me.x), __fmul_rn(__fsub_rn(o.w, me.w), wx));
+}
+
 template <int DIM>
-__device__ __forceinline__ float d2_f32(const float4& me, const float4& o, float sx, float sy,
+__device__ __forceinline__ float d2_f32(float dx, const float4& me, const float4& o, float sy,
                                         float sz) {
-    const float dx = __fadd_rn(__fsub_rn(o.x, me.x), sx);
     if (DIM == 1) return __fmul_rn(dx, dx);
     const float dy = __fadd_rn(__fsub_rn(o.y, me.y), sy);
     if (DIM == 2) return __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
@@ -528,13 +580,25 @@ __device__ __forceinline__ float d2_f32(const float4& me, const float4& o, float
     return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
 }
 
-// visit(j, d2f, rec_j) is called for every neighbour j of s (s included).
-template <int DIM, class Visit>
-__device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int64_t stride,
-                                                 const float4* __restrict__ rec,
-                                                 const double* __restrict__ pos,
-                                                 const uint32_t* __restrict__ start,
-                                                 const RealParams& P, Visit&& visit) {
+// Per-row candidate windows.  Row (dy, dz) of particle s is the particle
+// range [j0, j3) of cells cx-1..cx+1 at y index cy+dy (z index cz+dz); the
+// gather sorts it by x up to a slack.  Every accepted candidate has
+// d2f <= band_hi, so with g a lower bound of |dy_f| (and |dz_f|) over the row
+// its binary32 dx satisfies dx^2 <= reach2 - g^2 (reach2 carries the
+// roundings).  The row is skipped when that is negative; otherwise
+//   rx = sqrt(reach2 - g^2) + trim_eps
+// where trim_eps (host) bounds the sqrt rounding plus the row's departure from
+// x order (two dx errors and twice the cell-index error dc w).  A bisection
+// finds the first j with dx_j >= -rx: every earlier candidate then has
+// dx < -rx + trim_eps, too far left.  The caller's loop stops at the first
+// dx_j > rx: every later one has dx > rx - trim_eps.  Neither bound drops a
+// neighbour, so the accepted set is the exact binary64 one as before.
+// row(j0, j3, rx, sy, sz) is called for every row that can hold a neighbour.
+template <int DIM, class Row>
+__device__ __forceinline__ void for_each_row(uint32_t cell, const float4& me,
+                                             const float4* __restrict__ rec,
+                                             const uint32_t* __restrict__ start,
+                                             const RealParams& P, Row&& row) {
     const Grid& g = P.g;
     const PairParams& pp = P.pp;
     int c[3] = {0, 0, 0};
@@ -546,34 +610,67 @@ __device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int6
             rest /= uint32_t(g.n[a]);
         }
     }
-    const float4 me = rec[s];
     const int xlo = c[0] > 0 ? c[0] - 1 : 0;
     const int xhi = c[0] < g.n[0] - 1 ? c[0] + 1 : c[0];
     const int zlo = DIM == 3 ? (c[2] > 0 ? -1 : 0) : 0;
     const int zhi = DIM == 3 ? (c[2] < g.n[2] - 1 ? 1 : 0) : 0;
     const int ylo = DIM >= 2 ? (c[1] > 0 ? -1 : 0) : 0;
     const int yhi = DIM >= 2 ? (c[1] < g.n[1] - 1 ? 1 : 0) : 0;
+    const float eps = pp.trim_eps;
+    // lower bounds of |dy_f| over the rows below and above (likewise z): a
+    // row below holds offsets <= w, one above offsets >= 0, up to the slack
+    const float gy_below = DIM >= 2 ? fmaxf(__fsub_rn(me.y, eps), 0.0f) : 0.0f;
+    const float gy_above = DIM >= 2 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[1], me.y), eps), 0.0f) : 0.0f;
+    const float gz_below = DIM == 3 ? fmaxf(__fsub_rn(me.z, eps), 0.0f) : 0.0f;
+    const float gz_above = DIM == 3 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[2], me.z), eps), 0.0f) : 0.0f;
     const float wx = g.wf[0];
     for (int dz = zlo; dz <= zhi; ++dz) {
         const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
+        const float gz = dz < 0 ? gz_below : (dz > 0 ? gz_above : 0.0f);
         for (int dy = ylo; dy <= yhi; ++dy) {
             const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
-            const uint32_t row = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
-                                                uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
-            const uint32_t j0 = __ldg(start + row + xlo);
-            const uint32_t j3 = __ldg(start + row + xhi + 1);
-#pragma unroll 2
-            for (uint32_t j = j0; j < j3; ++j) {
-                const float4 o = __ldg(rec + j);
-                // (cx_j - cx_s) w: -w, 0 or w, exactly antisymmetric in the pair
-                const float sx = __fmul_rn(__fsub_rn(o.w, me.w), wx);
-                const float d2f = d2_f32<DIM>(me, o, sx, sy, sz);
-                if (d2f > pp.band_hi) continue;
-                if (d2f >= pp.band_lo && exact_d2<DIM>(pos, stride, s, j) > pp.psi2) continue;
-                visit(j, d2f, o);
+            const float gy = dy < 0 ? gy_below : (dy > 0 ? gy_above : 0.0f);
+            const float r2 = __fsub_rn(pp.reach2, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
+            if (r2 < 0.0f) continue;
+            const float rx = __fadd_rn(__fsqrt_rn(r2), eps);
+            const uint32_t rowc = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
+                                                 uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
+            uint32_t lo = __ldg(start + rowc + xlo);
+            uint32_t hi = __ldg(start + rowc + xhi + 1);
+            const uint32_t j3 = hi;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (dx_f32(me, __ldg(rec + mid), wx) < -rx) lo = mid + 1;
+                else hi = mid;
             }
+            row(lo, j3, rx, sy, sz);
         }
     }
+}
+
+// visit(j, d2f, rec_j) is called for every neighbour j of s (s included).
+template <int DIM, class Visit>
+__device__ __forceinline__ void visit_neighbours(uint32_t s, uint32_t cell, int64_t stride,
+                                                 const float4* __restrict__ rec,
+                                                 const double* __restrict__ pos,
+                                                 const uint32_t* __restrict__ start,
+                                                 const RealParams& P, Visit&& visit) {
+    const PairParams& pp = P.pp;
+    const float4 me = rec[s];
+    const float wx = P.g.wf[0];
+    for_each_row<DIM>(cell, me, rec, start, P,
+                      [&](uint32_t j0, uint32_t j3, float rx, float sy, float sz) {
+#pragma unroll 2
+        for (uint32_t j = j0; j < j3; ++j) {
+            const float4 o = __ldg(rec + j);
+            const float dx = dx_f32(me, o, wx);
+            if (dx > rx) break;
+            const float d2f = d2_f32<DIM>(dx, me, o, sy, sz);
+            if (d2f > pp.band_hi) continue;
+            if (d2f >= pp.band_lo && exact_d2<DIM>(pos, stride, s, j) > pp.psi2) continue;
+            visit(j, d2f, o);
+        }
+    });
 }
 
 // The exact binary64 test as a real call, so the compiler cannot if-convert
@@ -584,53 +681,31 @@ __device__ __noinline__ bool exact_within(const double* __restrict__ pos, int64_
     return exact_d2<DIM>(pos, stride, s, j) <= psi2;
 }
 
-// As visit_neighbours, but calls visit(j, d2f, accept) for every candidate
-// (the pass bodies run without a branch on the cutoff; the rare band case
-// takes the exact binary64 test).
+// As visit_neighbours, but calls visit(j, d2f, accept) for every candidate of
+// the windows (the pass bodies run without a branch on the cutoff; the rare
+// band case takes the exact binary64 test).
 template <int DIM, class Visit>
 __device__ __forceinline__ void scan_neighbours(uint32_t s, uint32_t cell, int64_t stride,
                                                 const float4* __restrict__ rec,
                                                 const double* __restrict__ pos,
                                                 const uint32_t* __restrict__ start,
                                                 const RealParams& P, Visit&& visit) {
-    const Grid& g = P.g;
     const PairParams& pp = P.pp;
-    int c[3] = {0, 0, 0};
-    {
-        uint32_t rest = cell - P.cell_base;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            c[a] = int(rest % uint32_t(g.n[a]));
-            rest /= uint32_t(g.n[a]);
-        }
-    }
     const float4 me = rec[s];
-    const int xlo = c[0] > 0 ? c[0] - 1 : 0;
-    const int xhi = c[0] < g.n[0] - 1 ? c[0] + 1 : c[0];
-    const int zlo = DIM == 3 ? (c[2] > 0 ? -1 : 0) : 0;
-    const int zhi = DIM == 3 ? (c[2] < g.n[2] - 1 ? 1 : 0) : 0;
-    const int ylo = DIM >= 2 ? (c[1] > 0 ? -1 : 0) : 0;
-    const int yhi = DIM >= 2 ? (c[1] < g.n[1] - 1 ? 1 : 0) : 0;
-    const float wx = g.wf[0];
-    for (int dz = zlo; dz <= zhi; ++dz) {
-        const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
-        for (int dy = ylo; dy <= yhi; ++dy) {
-            const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
-            const uint32_t row = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
-                                                uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
-            const uint32_t j0 = __ldg(start + row + xlo);
-            const uint32_t j3 = __ldg(start + row + xhi + 1);
-            for (uint32_t j = j0; j < j3; ++j) {
-                const float4 o = __ldg(rec + j);
-                const float sx = __fmul_rn(__fsub_rn(o.w, me.w), wx);
-                const float d2f = d2_f32<DIM>(me, o, sx, sy, sz);
-                bool accept = d2f < pp.band_lo;
-                if (d2f >= pp.band_lo && d2f <= pp.band_hi)
-                    accept = exact_within<DIM>(pos, stride, s, j, pp.psi2);
-                visit(j, d2f, accept);
-            }
+    const float wx = P.g.wf[0];
+    for_each_row<DIM>(cell, me, rec, start, P,
+                      [&](uint32_t j0, uint32_t j3, float rx, float sy, float sz) {
+        for (uint32_t j = j0; j < j3; ++j) {
+            const float4 o = __ldg(rec + j);
+            const float dx = dx_f32(me, o, wx);
+            if (dx > rx) break;
+            const float d2f = d2_f32<DIM>(dx, me, o, sy, sz);
+            bool accept = d2f < pp.band_lo;
+            if (d2f >= pp.band_lo && d2f <= pp.band_hi)
+                accept = exact_within<DIM>(pos, stride, s, j, pp.psi2);
+            visit(j, d2f, accept);
         }
-    }
+    });
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {

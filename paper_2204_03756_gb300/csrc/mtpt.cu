@@ -138,6 +138,9 @@ struct mtpt_handle {
     DevBuf<double> nb_k;
     int nb_cap = 0;
     DevBuf<double> out_tmp;
+    // staging copy of host-loaded input and its check tables
+    DevBuf<double> stage, chk_box;
+    DevBuf<uint32_t> chk_first, chk_flag;
     DevBuf<double> exp_table;
     DevBuf<uint32_t> status;
     DevBuf<unsigned long long> pair_counter, step_dev;
@@ -358,6 +361,24 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
     pp.psi2 = R.psi2;
     pp.band_lo = std::nextafter(float(R.psi2 * (1.0 - eta)), 0.0f);
     pp.band_hi = std::nextafter(float(R.psi2 * (1.0 + eta)), INFINITY);
+    // Candidate windows: reach2 bounds dx^2 + g^2 of every accepted candidate
+    // with the binary32 roundings of d2f and of the window arithmetic
+    // (2^-16 relative is far above them).  trim_eps covers the sqrt rounding,
+    // two dx errors (7 u w (1 + dc) + 2^-44 B each) and the row's departure
+    // from x order (a particle sits within dc cells of its cell, dc as above
+    // for binary32 cell indices and 2^-29 of it for binary64 ones), with a
+    // factor 2 to spare.
+    pp.reach2 = std::nextafter(float(double(pp.band_hi) * (1.0 + std::ldexp(1.0, -16))), INFINITY);
+    {
+        const double dc_cells = g.cell_f32 ? dc : std::ldexp(dc, -29);
+        double eps = 0.0;
+        for (int a = 0; a < p.dim; ++a) {
+            const double B = std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a])) + g.w[a];
+            eps = std::max(eps, 2.0 * (2.0 * dc_cells * g.w[a] + std::ldexp(g.w[a], -16) +
+                                       std::ldexp(B, -40)));
+        }
+        pp.trim_eps = std::nextafter(float(eps), INFINITY);
+    }
     pp.a = R.h2 > 0.0 ? 1.0 / (2.0 * R.h2) : 0.0;
     pp.a_log2e = float(pp.a * 1.4426950408889634);
     pp.beta = p.beta;
@@ -835,27 +856,74 @@ int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, con
     return MTPT_OK;
 }
 
-int check_host_particles(const mtpt_handle* h, const int64_t* counts, const double* pos,
-                         const double* mass) {
+// Host loads are copied into a device staging area and checked there
+// (k_check_input: positions inside their realisation's box, masses finite and,
+// in the precision form, at most 1e30 in magnitude) before the handle's state
+// is touched, so a rejected load leaves the old state in place.  On success
+// *pos_dev / *mass_dev point at the staged copy (positions dim x n).
+int stage_host_particles(mtpt_handle* h, const int64_t* counts, const double* pos,
+                         const double* mass, const double** pos_dev, const double** mass_dev) {
     int64_t n = 0;
     for (int k = 0; k < h->nreal; ++k) {
         if (counts[k] < 0) return MTPT_ERR_INVALID_ARG;
         n += counts[k];
     }
+    if (n > int64_t(0x7fffffff) - kBlock) return MTPT_ERR_INVALID_ARG;
     if (n > 0 && (!pos || !mass)) return MTPT_ERR_INVALID_ARG;
-    int64_t off = 0;
-    for (int k = 0; k < h->nreal; ++k) {
-        const mtpt_params& p = h->reals[k].prm;
-        for (int a = 0; a < h->dim; ++a) {
-            const double* x = pos + size_t(a) * size_t(n) + size_t(off);
-            for (int64_t i = 0; i < counts[k]; ++i)
-                if (!(x[i] >= p.lo[a] && x[i] <= p.hi[a])) return MTPT_ERR_OUT_OF_DOMAIN;
-        }
-        off += counts[k];
+    *pos_dev = nullptr;
+    *mass_dev = nullptr;
+    if (n == 0) return MTPT_OK;
+    const int d = h->dim;
+    MTPT_TRY(h->stage.ensure(size_t(d + 1) * size_t(n)));
+    MTPT_TRY(h->chk_flag.ensure(1));
+    if (!h->chk_box.p) {
+        std::vector<double> box(size_t(6) * size_t(h->nreal), 0.0);
+        for (int k = 0; k < h->nreal; ++k)
+            for (int a = 0; a < d; ++a) {
+                box[size_t(6) * k + a] = h->reals[k].prm.lo[a];
+                box[size_t(6) * k + 3 + a] = h->reals[k].prm.hi[a];
+            }
+        MTPT_TRY(h->chk_box.ensure(box.size()));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->chk_box.p, box.data(), box.size() * sizeof(double),
+                                      cudaMemcpyHostToDevice, h->stream));
+        MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
     }
+    if (h->nreal > 1) {
+        std::vector<uint32_t> first(size_t(h->nreal) + 1, 0u);
+        for (int k = 0; k < h->nreal; ++k) first[k + 1] = first[k] + uint32_t(counts[k]);
+        MTPT_TRY(h->chk_first.ensure(first.size()));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->chk_first.p, first.data(), first.size() * sizeof(uint32_t),
+                                      cudaMemcpyHostToDevice, h->stream));
+        MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));   // `first` is a local
+    }
+    double* st = h->stage.p;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(st, pos, size_t(d) * size_t(n) * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->stream));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(st + size_t(d) * size_t(n), mass, size_t(n) * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->stream));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->chk_flag.p, 0, sizeof(uint32_t), h->stream));
     const double mass_limit = h->precision == MTPT_FP32W ? 1e30 : HUGE_VAL;
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(mass[i]) || std::fabs(mass[i]) > mass_limit) return MTPT_ERR_INVALID_ARG;
+    const double* sp = st;
+    const double* sm = st + size_t(d) * size_t(n);
+    switch (d) {
+        case 1: k_check_input<1><<<grid_for(n), kBlock, 0, h->stream>>>(
+                    int(n), h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit, h->chk_flag.p);
+                break;
+        case 2: k_check_input<2><<<grid_for(n), kBlock, 0, h->stream>>>(
+                    int(n), h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit, h->chk_flag.p);
+                break;
+        default: k_check_input<3><<<grid_for(n), kBlock, 0, h->stream>>>(
+                    int(n), h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit, h->chk_flag.p);
+                break;
+    }
+    MTPT_CUDA_TRY(cudaGetLastError());
+    uint32_t flag = 0;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&flag, h->chk_flag.p, sizeof(flag), cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (flag & 1u) return MTPT_ERR_OUT_OF_DOMAIN;
+    if (flag & 2u) return MTPT_ERR_INVALID_ARG;
+    *pos_dev = sp;
+    *mass_dev = sm;
     return MTPT_OK;
 }
 
@@ -1170,6 +1238,7 @@ int mtpt_destroy(mtpt_handle* h) {
     h->corner_first.release(); h->id_first.release(); h->params_dev.release();
     h->r64.release(); h->r32.release(); h->msplit.release(); h->out_tmp.release();
     h->exp_table.release();
+    h->stage.release(); h->chk_box.release(); h->chk_first.release(); h->chk_flag.release();
     h->status.release(); h->pair_counter.release(); h->step_dev.release();
     h->emit_counter.release(); h->emit_i.release(); h->emit_j.release();
     h->tan[0].release(); h->tan[1].release(); h->snaps.release(); h->dr64.release();
@@ -1194,19 +1263,17 @@ int mtpt_set_stream(mtpt_handle* h, void* stream) {
 int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass) {
     if (!h || h->nreal != 1) return MTPT_ERR_INVALID_ARG;
     if (n < 0) return MTPT_ERR_INVALID_ARG;
-    MTPT_TRY(check_host_particles(h, &n, pos, mass));
-    MTPT_TRY(load_particles(h, &n, pos, mass, cudaMemcpyHostToDevice));
-    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return MTPT_OK;
+    const double *pd = nullptr, *md = nullptr;
+    MTPT_TRY(stage_host_particles(h, &n, pos, mass, &pd, &md));
+    return load_particles(h, &n, pd, md, cudaMemcpyDeviceToDevice);
 }
 
 int mtpt_set_particles_batch(mtpt_handle* h, const int64_t* counts, const double* pos,
                              const double* mass) {
     if (!h || !counts) return MTPT_ERR_INVALID_ARG;
-    MTPT_TRY(check_host_particles(h, counts, pos, mass));
-    MTPT_TRY(load_particles(h, counts, pos, mass, cudaMemcpyHostToDevice));
-    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return MTPT_OK;
+    const double *pd = nullptr, *md = nullptr;
+    MTPT_TRY(stage_host_particles(h, counts, pos, mass, &pd, &md));
+    return load_particles(h, counts, pd, md, cudaMemcpyDeviceToDevice);
 }
 
 int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,

@@ -68,21 +68,6 @@ def test_calls_before_particles_are_rejected(lib):
         mtpt.mtpt_destroy(h)
 
 
-def test_out_of_domain_host_input_is_rejected_before_any_device_work(lib):
-    import numpy as np
-    h = mtpt.mtpt_create(mtpt.Params(dim=2, lo=(0, 0), hi=(10, 10)))
-    try:
-        pos = np.array([[1.0, 11.0], [1.0, 1.0]])
-        with pytest.raises(mtpt.MtptError) as e:
-            mtpt.mtpt_set_particles(h, 2, pos, [1.0, 1.0])
-        assert e.value.code == mtpt.MTPT_ERR_OUT_OF_DOMAIN
-        pos = np.array([[1.0, np.nan], [1.0, 1.0]])
-        with pytest.raises(mtpt.MtptError):
-            mtpt.mtpt_set_particles(h, 2, pos, [1.0, 1.0])
-    finally:
-        mtpt.mtpt_destroy(h)
-
-
 def test_status_strings(lib):
     for code in range(7):
         assert mtpt.mtpt_status_string(code)
