@@ -742,18 +742,25 @@ __device__ __forceinline__ void add_pair_count(uint32_t cnt, unsigned long long*
 }
 
 // ---------------------------------------------------------------------------
-// Binary64 form.  GB300's binary64 unit is narrow: a warp instruction costs
-// the same there whether 32 lanes or 3 are active, so evaluating the pair
-// kernel inside the divergent candidate loop wastes most of it.  Each warp
-// therefore (A) finds its accepted pairs with the binary32 prefilter --
-// counting first, then writing them lane-major into a shared-memory list --
-// (B) evaluates the binary64 pair terms with all 32 lanes, one list entry per
-// lane, and (C) lets each lane add its own entries in list order, so every
-// sum runs in candidate order and results repeat bit for bit.  Lists longer
-// than kDenseCap entries are processed in chunks (candidates re-enumerated
-// per chunk), so any density is handled.
+// Binary64 pair passes.  A thread per particle walks its candidate windows,
+// whose lengths differ from lane to lane, so work done inside that loop runs
+// at a fraction of the warp's lanes, and GB300's binary64 unit charges a warp
+// instruction the same whether 32 lanes or 3 are active.  These passes
+// therefore split the work per warp:
+//  (A) each lane walks its windows once with the binary32 prefilter and
+//      appends every accepted neighbour j != s (and its binary32 d2) to its
+//      own kSeg-entry segment in shared memory;
+//  (B) when a lane's segment is full (checked at window ends) or the walk is
+//      over, the warp evaluates the pair terms of all segments with all 32
+//      lanes, one entry per lane, in lane-major order;
+//  (C) each lane then adds its own results in the order it found them.
+// Every sum therefore runs in candidate order and repeats bit for bit, the
+// divergent loop holds only the prefilter, and the binary64 arithmetic runs
+// at full width.  (The binary32 passes below keep the pair arithmetic inside
+// the candidate loop: there the segment traffic costs more than the
+// divergence it removes, measured at 1.5x their time.)
 // ---------------------------------------------------------------------------
-constexpr int kDenseCap = 256;            // list entries per warp per chunk
+constexpr int kSeg = 12;                   // segment entries per lane
 constexpr int kWarpsPerBlock = kBlock / 32;
 
 __device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t v, uint32_t* total) {
@@ -768,12 +775,16 @@ __device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t v, uint32_t* to
     return inc - v;
 }
 
-// Shared state of the dense binary64 passes.
-struct DenseLists {
-    uint32_t j[kWarpsPerBlock][kDenseCap];
-    double v[kWarpsPerBlock][kDenseCap];
-    uint8_t owner[kWarpsPerBlock][kDenseCap];
-    uint32_t off[kWarpsPerBlock][32];
+// Shared state of one block's warps.  V: type of the pair terms; D2: keep the
+// binary32 d2 of each entry (binary32 passes).
+template <int NW, class V, bool D2>
+struct SegShared {
+    uint32_t j[NW][kSeg][32];          // lane-owned segments, entry k of lane l at [k][l]
+    float d2[NW][D2 ? kSeg : 1][32];
+    V v[NW][kSeg * 32];                // phase-B results, lane-major
+    uint8_t owner[NW][kSeg * 32];      // lane of each lane-major entry
+    uint32_t off[NW][32];              // first lane-major entry of each lane
+    uint32_t base[NW][32];             // entries each lane had before this flush
 };
 
 // Binary64 neighbour lists: pass 1 stores each accepted neighbour j != s and
@@ -789,99 +800,160 @@ struct NbList64 {
     int cap;           // 0: no list
 };
 
-// Runs phases A-C for the calling warp.  eval(owner_s, j) returns the binary64
-// pair term; add(term) is called by each lane for its own entries in order.
-template <int DIM, class Eval, class Add>
-__device__ __forceinline__ uint32_t dense_pairs(bool valid, uint32_t s, int64_t stride,
-                                                const float4* __restrict__ rec,
-                                                const double* __restrict__ pos,
-                                                const uint32_t* __restrict__ cell,
-                                                const uint32_t* __restrict__ start,
-                                                const RealParams& P, DenseLists& L, Eval&& eval,
-                                                Add&& add, NbList64 store = NbList64{}) {
+// Phases A-C for the calling warp (every lane of the warp must call it; lanes
+// with valid = false walk nothing).  eval(owner_s, j, d2f) returns the pair
+// term (d2f is 0 unless D2); add(term) is called by each lane for its own
+// entries in order.  Returns the lane's number of accepted neighbours j != s.
+template <int DIM, int NW, class V, bool D2, class Eval, class Add>
+__device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t stride,
+                                              const float4* __restrict__ rec,
+                                              const double* __restrict__ pos,
+                                              const uint32_t* __restrict__ cell,
+                                              const uint32_t* __restrict__ start,
+                                              const RealParams& P, SegShared<NW, V, D2>& S,
+                                              Eval&& eval, Add&& add,
+                                              NbList64 store = NbList64{}) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t my_cell = valid ? cell[s] : 0u;
-    uint32_t cnt = 0;
-    if (valid)
-        visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, P,
-                              [&](uint32_t j, float, const float4&) { cnt += (j != s) ? 1u : 0u; });
-    uint32_t total;
-    const uint32_t off = warp_exclusive_scan(cnt, &total);
     const uint32_t warp_s0 = s - uint32_t(lane);
-    if (store.cap > 0) {
-        L.off[warp][lane] = off;
-        if (valid) store.count[s] = cnt;
+    uint32_t cnt = 0, done = 0;
+    auto flush = [&]() {
+        uint32_t total;
+        const uint32_t off = warp_exclusive_scan(cnt, &total);
+        S.off[warp][lane] = off;
+        S.base[warp][lane] = done;
+        for (uint32_t k = 0; k < cnt; ++k) S.owner[warp][off + k] = uint8_t(lane);
         __syncwarp();
-    }
-    for (uint32_t chunk = 0; chunk < total; chunk += kDenseCap) {
-        const uint32_t chunk_end = chunk + kDenseCap;
-        if (valid && cnt > 0 && off < chunk_end && off + cnt > chunk) {
-            uint32_t k = off;
-            visit_neighbours<DIM>(s, my_cell, stride, rec, pos, start, P,
-                                  [&](uint32_t j, float, const float4&) {
-                                      if (j == s) return;
-                                      if (k >= chunk && k < chunk_end) {
-                                          L.j[warp][k - chunk] = j;
-                                          L.owner[warp][k - chunk] = uint8_t(lane);
-                                      }
-                                      ++k;
-                                  });
-        }
-        __syncwarp();
-        const uint32_t m = min(total - chunk, uint32_t(kDenseCap));
-        for (uint32_t e = uint32_t(lane); e < m; e += 32) {
-            const uint32_t o = L.owner[warp][e], j = L.j[warp][e];
-            const double val = eval(warp_s0 + o, j);
-            L.v[warp][e] = val;
+        for (uint32_t e = uint32_t(lane); e < total; e += 32) {
+            const uint32_t o = S.owner[warp][e];
+            const uint32_t k = e - S.off[warp][o];
+            const uint32_t j = S.j[warp][k][o];
+            const V val = eval(warp_s0 + o, j, D2 ? S.d2[warp][D2 ? k : 0][o] : 0.0f);
+            S.v[warp][e] = val;
             if (store.cap > 0) {
-                const uint32_t k = chunk + e - L.off[warp][o];
-                if (k < uint32_t(store.cap)) {
-                    const int64_t at = int64_t(k) * stride + (warp_s0 + o);
+                const uint32_t slot = S.base[warp][o] + k;
+                if (slot < uint32_t(store.cap)) {
+                    const int64_t at = int64_t(slot) * stride + (warp_s0 + o);
                     store.j[at] = j;
                     store.k[at] = val;
                 }
             }
         }
         __syncwarp();
-        if (valid) {
-            const uint32_t q0 = max(off, chunk), q1 = min(off + cnt, chunk_end);
-            for (uint32_t q = q0; q < q1; ++q) add(L.v[warp][q - chunk]);
-        }
+        for (uint32_t k = 0; k < cnt; ++k) add(S.v[warp][off + k]);
+        done += cnt;
+        cnt = 0;
         __syncwarp();
+    };
+
+    const Grid& g = P.g;
+    const PairParams& pp = P.pp;
+    const float4 me = valid ? rec[s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int c[3] = {0, 0, 0};
+    if (valid) {
+        uint32_t rest = cell[s] - P.cell_base;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = int(rest % uint32_t(g.n[a]));
+            rest /= uint32_t(g.n[a]);
+        }
     }
-    return cnt;
+    const int xlo = c[0] > 0 ? c[0] - 1 : 0;
+    const int xhi = c[0] < g.n[0] - 1 ? c[0] + 1 : c[0];
+    const float eps = pp.trim_eps;
+    const float gy_below = DIM >= 2 ? fmaxf(__fsub_rn(me.y, eps), 0.0f) : 0.0f;
+    const float gy_above = DIM >= 2 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[1], me.y), eps), 0.0f) : 0.0f;
+    const float gz_below = DIM == 3 ? fmaxf(__fsub_rn(me.z, eps), 0.0f) : 0.0f;
+    const float gz_above = DIM == 3 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[2], me.z), eps), 0.0f) : 0.0f;
+    const float wx = g.wf[0];
+    // rows in a fixed order for the whole warp; a lane whose row is outside
+    // the grid or beyond the cutoff (see for_each_row) gets an empty window
+#pragma unroll 1
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+#pragma unroll 1
+        for (int dy = (DIM >= 2 ? -1 : 0); dy <= (DIM >= 2 ? 1 : 0); ++dy) {
+            const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
+            const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
+            uint32_t j = 0, j3 = 0;
+            float rx = 0.0f;
+            const bool in_grid = valid && (DIM < 2 || (c[1] + dy >= 0 && c[1] + dy < g.n[1])) &&
+                                 (DIM < 3 || (c[2] + dz >= 0 && c[2] + dz < g.n[2]));
+            if (in_grid) {
+                const float gy = dy < 0 ? gy_below : (dy > 0 ? gy_above : 0.0f);
+                const float gz = dz < 0 ? gz_below : (dz > 0 ? gz_above : 0.0f);
+                const float r2 = __fsub_rn(pp.reach2, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
+                if (r2 >= 0.0f) {
+                    rx = __fadd_rn(__fsqrt_rn(r2), eps);
+                    const uint32_t rowc = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
+                                                         uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
+                    uint32_t lo = __ldg(start + rowc + xlo);
+                    uint32_t hi = __ldg(start + rowc + xhi + 1);
+                    j3 = hi;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi) >> 1;
+                        if (dx_f32(me, __ldg(rec + mid), wx) < -rx) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    j = lo;
+                }
+            }
+            do {
+                while (j < j3 && cnt < uint32_t(kSeg)) {
+                    const float4 o = __ldg(rec + j);
+                    const float dx = dx_f32(me, o, wx);
+                    if (dx > rx) {
+                        j = j3;
+                        break;
+                    }
+                    const float d2f = d2_f32<DIM>(dx, me, o, sy, sz);
+                    bool accept = d2f < pp.band_lo;
+                    if (d2f >= pp.band_lo && d2f <= pp.band_hi)
+                        accept = exact_within<DIM>(pos, stride, s, j, pp.psi2);
+                    if (accept && j != s) {
+                        S.j[warp][cnt][lane] = j;
+                        if (D2) S.d2[warp][D2 ? cnt : 0][lane] = d2f;
+                        ++cnt;
+                    }
+                    ++j;
+                }
+                if (__any_sync(0xffffffffu, cnt == uint32_t(kSeg))) flush();
+            } while (__any_sync(0xffffffffu, j < j3));
+        }
+    }
+    if (__any_sync(0xffffffffu, cnt > 0)) flush();
+    return done;
 }
 
-// Phases B-C over stored lists (the warp's lanes all fit their lists):
-// eval(owner_s, j, K) returns the binary64 pair term.
-template <class Eval, class Add>
+// Phases B-C over stored binary64 lists (the warp's lanes all fit their
+// lists): eval(owner_s, j, K) returns the pair term, add(term) as above.
+template <int NW, class Eval, class Add>
 __device__ __forceinline__ void dense_listed(bool valid, uint32_t s, int64_t stride,
-                                             uint32_t cnt, const NbList64& nb, DenseLists& L,
-                                             Eval&& eval, Add&& add) {
+                                             uint32_t cnt, const NbList64& nb,
+                                             SegShared<NW, double, false>& S, Eval&& eval,
+                                             Add&& add) {
+    constexpr uint32_t kChunk = kSeg * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t total;
-    const uint32_t off = warp_exclusive_scan(cnt, &total);
+    const uint32_t off = warp_exclusive_scan(valid ? cnt : 0u, &total);
+    S.off[warp][lane] = off;
     const uint32_t warp_s0 = s - uint32_t(lane);
-    for (uint32_t chunk = 0; chunk < total; chunk += kDenseCap) {
-        const uint32_t chunk_end = chunk + kDenseCap;
+    for (uint32_t chunk = 0; chunk < total; chunk += kChunk) {
+        const uint32_t chunk_end = chunk + kChunk;
         if (valid) {
             const uint32_t q0 = max(off, chunk), q1 = min(off + cnt, chunk_end);
-            for (uint32_t q = q0; q < q1; ++q) {
-                L.owner[warp][q - chunk] = uint8_t(lane);
-                L.j[warp][q - chunk] = q - off;          // slot index within the owner
-            }
+            for (uint32_t q = q0; q < q1; ++q) S.owner[warp][q - chunk] = uint8_t(lane);
         }
         __syncwarp();
-        const uint32_t m = min(total - chunk, uint32_t(kDenseCap));
+        const uint32_t m = min(total - chunk, kChunk);
         for (uint32_t e = uint32_t(lane); e < m; e += 32) {
-            const uint32_t so = warp_s0 + L.owner[warp][e];
-            const int64_t at = int64_t(L.j[warp][e]) * stride + so;
-            L.v[warp][e] = eval(so, __ldg(nb.j + at), __ldg(nb.k + at));
+            const uint32_t o = S.owner[warp][e];
+            const uint32_t so = warp_s0 + o;
+            const int64_t at = int64_t(chunk + e - S.off[warp][o]) * stride + so;
+            S.v[warp][e] = eval(so, __ldg(nb.j + at), __ldg(nb.k + at));
         }
         __syncwarp();
         if (valid) {
             const uint32_t q0 = max(off, chunk), q1 = min(off + cnt, chunk_end);
-            for (uint32_t q = q0; q < q1; ++q) add(L.v[warp][q - chunk]);
+            for (uint32_t q = q0; q < q1; ++q) add(S.v[warp][q - chunk]);
         }
         __syncwarp();
     }
@@ -898,22 +970,22 @@ k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4
              double* __restrict__ r_out, unsigned long long* __restrict__ pair_counter,
              NbList64 nb) {
     __shared__ double table[kExpTable];
-    __shared__ DenseLists lists;
+    __shared__ SegShared<kWarpsPerBlock, double, false> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
     const bool valid = s < n && P.transfer;
     double r = 1.0;
-    const uint32_t cnt = dense_pairs<DIM>(
-        valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
-        [&](uint32_t so, uint32_t j) {
+    const uint32_t cnt = seg_pairs<DIM>(
+        valid, uint32_t(s), stride, rec, pos, cell, start, P, seg,
+        [&](uint32_t so, uint32_t j, float) {
             const RealParams& Po = v.of_sorted(so);
             return gauss_exp(kernel_d2<DIM>(pos, stride, so, j), table, Po.pp.ec);
         },
         [&](double K) { r = __dadd_rn(r, K); }, nb);
     if (s < n) r_out[s] = r;
-    if (nb.cap > 0 && s < n && !valid) nb.count[s] = 0u;
+    if (nb.cap > 0 && s < n) nb.count[s] = valid ? cnt : 0u;
     add_pair_count(valid ? cnt : 0u, pair_counter);
 }
 
@@ -926,7 +998,7 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
                const double* __restrict__ r, const double* __restrict__ mass,
                double* __restrict__ mass_out, NbList64 nb) {
     __shared__ double table[kExpTable];
-    __shared__ DenseLists lists;
+    __shared__ SegShared<kWarpsPerBlock, double, false> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -943,12 +1015,12 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
     const uint32_t listed = (nb.cap > 0 && valid) ? nb.count[s] : 0u;
     const bool fits = nb.cap > 0 && __all_sync(0xffffffffu, listed <= uint32_t(nb.cap));
     if (fits) {
-        dense_listed(valid, uint32_t(s), stride, listed, nb, lists, flux,
+        dense_listed(valid, uint32_t(s), stride, listed, nb, seg, flux,
                      [&](double f) { acc = __dadd_rn(acc, f); });
     } else {
-        dense_pairs<DIM>(
-            valid, uint32_t(s), stride, rec, pos, cell, start, P, lists,
-            [&](uint32_t so, uint32_t j) {
+        seg_pairs<DIM>(
+            valid, uint32_t(s), stride, rec, pos, cell, start, P, seg,
+            [&](uint32_t so, uint32_t j, float) {
                 const RealParams& Po = v.of_sorted(so);
                 const double K = gauss_exp(kernel_d2<DIM>(pos, stride, so, j), table, Po.pp.ec);
                 return flux(so, j, K);
