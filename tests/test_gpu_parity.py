@@ -293,3 +293,51 @@ def test_device_buffers_through_torch():
         assert e.value.code == mtpt.MTPT_ERR_OUT_OF_DOMAIN
     finally:
         mtpt.mtpt_destroy(h)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("case", ["far_f32_cells", "far_f64_cells", "sparse_wide_cells",
+                                  "one_cell_high", "on_cell_corners"])
+def test_pair_windows_on_adversarial_boxes(form, case):
+    """The per-row candidate windows rest on a slack derived from the
+    binary32 cell-index and offset error bounds: boxes far from the origin
+    (binary32 cell indices near their limit, and binary64 ones beyond it),
+    cells much wider than psi, a single cell row and particles on cell
+    corners must all keep the exact pair set -- in the emitted pairs and in
+    the pair counts of both pair passes."""
+    cases = ["far_f32_cells", "far_f64_cells", "sparse_wide_cells", "one_cell_high",
+             "on_cell_corners"]
+    rng = np.random.default_rng(11 + cases.index(case))
+    n = 2500
+    if case == "far_f32_cells":
+        lo = np.array([4800.0, -5000.0]); L = np.array([45.0, 38.0])
+    elif case == "far_f64_cells":
+        lo = np.array([2.0e6, -3.5e6]); L = np.array([45.0, 38.0])
+    elif case == "sparse_wide_cells":              # cells ~14 psi wide (count capped)
+        n = 40
+        lo = np.array([0.0, 0.0]); L = np.array([200.0, 150.0])
+    elif case == "one_cell_high":
+        lo = np.array([0.0, 0.0]); L = np.array([900.0, 1.0])
+    else:
+        lo = np.array([0.0, 0.0]); L = np.array([30.0, 30.0])
+    pos = lo[:, None] + rng.uniform(0, 1, size=(2, n)) * L[:, None]
+    p = mtpt.Params(dim=2, D=1.0, kappa=0.0, dt=0.1, lo=tuple(lo), hi=tuple(lo + L),
+                    seed=9, precision=form)
+    if case == "sparse_wide_cells":
+        pos[:, :20] = lo[:, None] + np.array([[30.0], [40.0]]) + rng.uniform(0, 3, size=(2, 20))
+    if case == "on_cell_corners":
+        psi = O.derived(oracle_params(p))["psi"]
+        ncell = np.floor(L / (psi * (1 + 1e-6)))
+        w = L / ncell
+        k = rng.integers(0, ncell[0], size=400), rng.integers(0, ncell[1], size=400)
+        pos[0, :400] = lo[0] + k[0] * w[0]
+        pos[1, :400] = lo[1] + k[1] * w[1]
+        pos[:, 400:800] = pos[:, :400] + rng.choice([-1e-12, 0.0, 1e-12], size=(2, 400))
+        pos = np.clip(pos, lo[:, None], (lo + L)[:, None])
+    psi2 = O.derived(oracle_params(p))["psi2"]
+    bi, bj = O.pairs(pos, psi2, "brute")
+    gi, gj = _pairs_gpu(p, pos)
+    assert np.array_equal(gi, bi) and np.array_equal(gj, bj)
+    with mtpt.Simulation(p, pos, rng.uniform(0, 1, n)) as sim:
+        sim.step(1)                                    # kappa = 0: transfer only
+        assert sim.info()["pair_count"] == len(bi)
