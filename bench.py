@@ -67,12 +67,12 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # particles; traffic grows in proportion to the particles a launch processes,
 # so it is scaled to the bench's launch).  Valid only for the kernel source it
 # was measured on: a different hash of kernels.cuh reports traffic as null.
-TRAFFIC_SOURCE_SHA1 = "47b64f28dfb4"
+TRAFFIC_SOURCE_SHA1 = "f55d983c9b11"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (177.798144e6 + 117.535232e6) / 8e6,
-    "gather": (305.847296e6 + 394.810368e6) / 8e6,
-    "rowsum_f32": (177.878784e6 + 70.140416e6) / 8e6,
-    "exchange_f32": (305.834752e6 + 54.230016e6) / 8e6,
+    "walk_key": (177.794816e6 + 117.469440e6) / 8e6,
+    "gather": (305.862912e6 + 395.149312e6) / 8e6,
+    "rowsum_f32": (177.818112e6 + 24.458752e6) / 8e6,
+    "exchange_f32": (337.840896e6 + 56.212480e6) / 8e6,
 }
 
 

@@ -4,7 +4,8 @@
 // conversions) at about 1/70 of the binary32 rate, so the kernels keep
 // binary64 to the operations whose results must match the binary64 method
 // bit for bit (the walk's x + sigma xi, and the pair test inside a narrow
-// band around the cutoff) and do everything else in binary32 and integer
+// band around the cutoff) or carry the binary64 form's accuracy (its pair
+// terms and sums), and do everything else in binary32 and integer
 // arithmetic.
 //
 // Data layout (structure of arrays, `stride` = capacity >= n):
@@ -16,7 +17,8 @@
 //                        x index (a small integer, exact in binary32)
 //   start[c]             first particle of cell c (exclusive prefix sum)
 // Cells are row-major (x fastest), so the three cells (cx-1..cx+1) of one
-// neighbour row are one contiguous particle range.
+// neighbour row are one contiguous particle range; inside a cell particles
+// are ordered by x (then id), so that range is sorted by x up to rounding.
 #pragma once
 #include <cstdint>
 
@@ -1271,7 +1273,12 @@ __global__ void k_row_sums_out(int n, const uint32_t* __restrict__ id, const T* 
     out[id[s]] = __dmul_rn(double(src[int64_t(s) * src_step]), P.kernel_norm);
 }
 
-// Outputs in input order: out[a * n + id[s]] = src[a * stride + s] * scale.
+// Outputs in input order: out[a * n + id[s]] = src[a * stride + s] * scale
+// (binary32 sources widened exactly by integer operations; no multiply when
+// scale is 1).
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float x) { return f32_to_f64(x); }
+
 template <typename T>
 __global__ void k_unpermute(int n, int64_t stride, int naxes, const uint32_t* __restrict__ id,
                             const T* __restrict__ src, int src_step, double scale,
@@ -1279,8 +1286,10 @@ __global__ void k_unpermute(int n, int64_t stride, int naxes, const uint32_t* __
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t k = id[s];
-    for (int a = 0; a < naxes; ++a)
-        out[int64_t(a) * n + k] = __dmul_rn(double(src[(a * stride + s) * src_step]), scale);
+    for (int a = 0; a < naxes; ++a) {
+        const double x = widen(src[(a * stride + s) * src_step]);
+        out[int64_t(a) * n + k] = scale == 1.0 ? x : __dmul_rn(x, scale);
+    }
 }
 
 }  // namespace mtpt
