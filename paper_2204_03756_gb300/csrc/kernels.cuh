@@ -21,6 +21,7 @@
 // are ordered by x (then id), so that range is sorted by x up to rounding.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "expneg.cuh"
 #include "rng.cuh"
@@ -79,6 +80,7 @@ struct RealParams {
     double dsigma_dD;    // d sigma / dD = sigma / (2 D) (adjoint)
     double h2;           // 2 D_MT dt / beta (adjoint)
     double inv_2D;       // 1 / (2 D) (adjoint)
+    double inv_h2;       // 1 / h^2 (adjoint)
 };
 
 struct SingleView {
@@ -779,12 +781,13 @@ __device__ __forceinline__ uint32_t warp_exclusive_scan(uint32_t v, uint32_t* to
 
 // Shared state of one block's warps.  V: type of the pair terms; D2: keep the
 // binary32 d2 of each entry (binary32 passes).
-template <int NW, class V, bool D2>
+template <int NW, class V, bool D2, int SEG = kSeg>
 struct SegShared {
-    uint32_t j[NW][kSeg][32];          // lane-owned segments, entry k of lane l at [k][l]
-    float d2[NW][D2 ? kSeg : 1][32];
-    V v[NW][kSeg * 32];                // phase-B results, lane-major
-    uint8_t owner[NW][kSeg * 32];      // lane of each lane-major entry
+    static constexpr int kCap = SEG;   // entries per lane
+    uint32_t j[NW][SEG][32];           // lane-owned segments, entry k of lane l at [k][l]
+    float d2[NW][D2 ? SEG : 1][32];
+    V v[NW][SEG * 32];                 // phase-B results, lane-major
+    uint8_t owner[NW][SEG * 32];       // lane of each lane-major entry
     uint32_t off[NW][32];              // first lane-major entry of each lane
     uint32_t base[NW][32];             // entries each lane had before this flush
 };
@@ -806,13 +809,13 @@ struct NbList64 {
 // with valid = false walk nothing).  eval(owner_s, j, d2f) returns the pair
 // term (d2f is 0 unless D2); add(term) is called by each lane for its own
 // entries in order.  Returns the lane's number of accepted neighbours j != s.
-template <int DIM, int NW, class V, bool D2, class Eval, class Add>
+template <int DIM, int NW, class V, bool D2, int SEG, class Eval, class Add>
 __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t stride,
                                               const float4* __restrict__ rec,
                                               const double* __restrict__ pos,
                                               const uint32_t* __restrict__ cell,
                                               const uint32_t* __restrict__ start,
-                                              const RealParams& P, SegShared<NW, V, D2>& S,
+                                              const RealParams& P, SegShared<NW, V, D2, SEG>& S,
                                               Eval&& eval, Add&& add,
                                               NbList64 store = NbList64{}) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -831,12 +834,14 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
             const uint32_t j = S.j[warp][k][o];
             const V val = eval(warp_s0 + o, j, D2 ? S.d2[warp][D2 ? k : 0][o] : 0.0f);
             S.v[warp][e] = val;
-            if (store.cap > 0) {
-                const uint32_t slot = S.base[warp][o] + k;
-                if (slot < uint32_t(store.cap)) {
-                    const int64_t at = int64_t(slot) * stride + (warp_s0 + o);
-                    store.j[at] = j;
-                    store.k[at] = val;
+            if constexpr (std::is_same<V, double>::value) {
+                if (store.cap > 0) {
+                    const uint32_t slot = S.base[warp][o] + k;
+                    if (slot < uint32_t(store.cap)) {
+                        const int64_t at = int64_t(slot) * stride + (warp_s0 + o);
+                        store.j[at] = j;
+                        store.k[at] = val;
+                    }
                 }
             }
         }
@@ -899,7 +904,7 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
                 }
             }
             do {
-                while (j < j3 && cnt < uint32_t(kSeg)) {
+                while (j < j3 && cnt < uint32_t(SEG)) {
                     const float4 o = __ldg(rec + j);
                     const float dx = dx_f32(me, o, wx);
                     if (dx > rx) {
@@ -917,7 +922,7 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
                     }
                     ++j;
                 }
-                if (__any_sync(0xffffffffu, cnt == uint32_t(kSeg))) flush();
+                if (__any_sync(0xffffffffu, cnt == uint32_t(SEG))) flush();
             } while (__any_sync(0xffffffffu, j < j3));
         }
     }
@@ -927,12 +932,12 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
 
 // Phases B-C over stored binary64 lists (the warp's lanes all fit their
 // lists): eval(owner_s, j, K) returns the pair term, add(term) as above.
-template <int NW, class Eval, class Add>
+template <int NW, int SEG, class Eval, class Add>
 __device__ __forceinline__ void dense_listed(bool valid, uint32_t s, int64_t stride,
                                              uint32_t cnt, const NbList64& nb,
-                                             SegShared<NW, double, false>& S, Eval&& eval,
+                                             SegShared<NW, double, false, SEG>& S, Eval&& eval,
                                              Add&& add) {
-    constexpr uint32_t kChunk = kSeg * 32;
+    constexpr uint32_t kChunk = SEG * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t total;
     const uint32_t off = warp_exclusive_scan(valid ? cnt : 0u, &total);
@@ -1152,8 +1157,12 @@ __device__ __forceinline__ void pair_terms(const double* __restrict__ pos,
         dot = __fma_rn(d, dt, dot);
     }
     *K = gauss_exp(d2, table, P.pp.ec);
-    *dK = __dmul_rn(*K, __ddiv_rn(__fma_rn(d2, P.inv_2D, -dot), P.h2));
+    *dK = __dmul_rn(*K, __dmul_rn(__fma_rn(d2, P.inv_2D, -dot), P.inv_h2));
 }
+
+// The adjoint passes run on the segment engine with two binary64 terms per
+// pair (smaller segments: two values per entry).
+constexpr int kAdjSeg = 8;
 
 // Pass A: r_s = sum_j K_sj (self included) and dr_s = sum_j dK_sj / dD.
 template <int DIM, class View>
@@ -1164,24 +1173,28 @@ k_adj_rowsum(int n, int64_t stride, const double* __restrict__ pos, const double
              const __grid_constant__ View v, double* __restrict__ r_out,
              double* __restrict__ dr_out) {
     __shared__ double table[kExpTable];
+    __shared__ SegShared<kWarpsPerBlock, double2, false, kAdjSeg> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const RealParams& P = v.of_sorted(uint32_t(s));
+    const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
+    const bool valid = s < n && P.transfer;
     double r = 1.0, dr = 0.0;
-    if (P.transfer) {
-        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
-                              [&](uint32_t j, float, const float4&) {
-                                  if (j == uint32_t(s)) return;
-                                  double K, dK;
-                                  pair_terms<DIM>(pos, tan, stride, uint32_t(s), j, P, table, &K, &dK);
-                                  r = __dadd_rn(r, K);
-                                  dr = __dadd_rn(dr, dK);
-                              });
+    seg_pairs<DIM>(
+        valid, uint32_t(s), stride, rec, pos, cell, start, P, seg,
+        [&](uint32_t so, uint32_t j, float) {
+            double K, dK;
+            pair_terms<DIM>(pos, tan, stride, so, j, v.of_sorted(so), table, &K, &dK);
+            return make_double2(K, dK);
+        },
+        [&](double2 t) {
+            r = __dadd_rn(r, t.x);
+            dr = __dadd_rn(dr, t.y);
+        });
+    if (s < n) {
+        r_out[s] = r;
+        dr_out[s] = dr;
     }
-    r_out[s] = r;
-    dr_out[s] = dr;
 }
 
 // Pass B: lambda_t,s = lambda_s + beta sum_j W_sj (lambda_j - lambda_s) and the
@@ -1197,32 +1210,35 @@ k_adj_exchange(int n, int64_t stride, const double* __restrict__ pos,
                const double* __restrict__ mass, const double* __restrict__ lam,
                double* __restrict__ lam_out, double* __restrict__ gD) {
     __shared__ double table[kExpTable];
+    __shared__ SegShared<kWarpsPerBlock, double2, false, kAdjSeg> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const RealParams& P = v.of_sorted(uint32_t(s));
-    const double ls = lam[s];
+    const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
+    const bool valid = s < n && P.transfer;
     double lacc = 0.0, gacc = 0.0;
-    if (P.transfer) {
-        const double rs = r[s], drs = dr[s], ms = mass[s];
-        visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
-                              [&](uint32_t j, float, const float4&) {
-                                  if (j == uint32_t(s)) return;
-                                  double K, dK;
-                                  pair_terms<DIM>(pos, tan, stride, uint32_t(s), j, P, table, &K, &dK);
-                                  const double rsum = __dadd_rn(rs, __ldg(r + j));
-                                  const double inv = __ddiv_rn(1.0, rsum);
-                                  const double W = __dmul_rn(__dmul_rn(2.0, K), inv);
-                                  const double dW = __dmul_rn(
-                                      __dmul_rn(2.0, inv),
-                                      __fma_rn(-__dmul_rn(K, inv), __dadd_rn(drs, __ldg(dr + j)), dK));
-                                  lacc = __fma_rn(W, __dsub_rn(__ldg(lam + j), ls), lacc);
-                                  gacc = __fma_rn(dW, __dsub_rn(__ldg(mass + j), ms), gacc);
-                              });
+    seg_pairs<DIM>(
+        valid, uint32_t(s), stride, rec, pos, cell, start, P, seg,
+        [&](uint32_t so, uint32_t j, float) {
+            double K, dK;
+            pair_terms<DIM>(pos, tan, stride, so, j, v.of_sorted(so), table, &K, &dK);
+            const double inv = quot_pos(1.0, __dadd_rn(__ldg(r + so), __ldg(r + j)));
+            const double W = __dmul_rn(__dmul_rn(2.0, K), inv);
+            const double dW = __dmul_rn(
+                __dmul_rn(2.0, inv),
+                __fma_rn(-__dmul_rn(K, inv), __dadd_rn(__ldg(dr + so), __ldg(dr + j)), dK));
+            return make_double2(__dmul_rn(W, __dsub_rn(__ldg(lam + j), __ldg(lam + so))),
+                                __dmul_rn(dW, __dsub_rn(__ldg(mass + j), __ldg(mass + so))));
+        },
+        [&](double2 t) {
+            lacc = __dadd_rn(lacc, t.x);
+            gacc = __dadd_rn(gacc, t.y);
+        });
+    if (s < n) {
+        const double ls = lam[s];
+        lam_out[s] = valid ? __fma_rn(P.pp.beta, lacc, ls) : ls;
+        gD[s] = valid ? __dmul_rn(__dmul_rn(P.pp.beta, ls), gacc) : 0.0;
     }
-    lam_out[s] = __fma_rn(P.pp.beta, lacc, ls);
-    gD[s] = __dmul_rn(__dmul_rn(P.pp.beta, ls), gacc);
 }
 
 // Deterministic sum of x[0..n): fixed-size blocks reduce their slice in a fixed
@@ -1242,11 +1258,20 @@ k_block_sums(int n, const double* __restrict__ x, double* __restrict__ partial) 
     if (threadIdx.x == 0) partial[blockIdx.x] = buf[0];
 }
 
-__global__ void k_sum_into(int nparts, const double* __restrict__ partial, double* __restrict__ acc) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+// One block: thread t adds partial[t], partial[t + T], ... in order, then a
+// fixed tree over the threads; the result is added to *acc.
+__global__ void __launch_bounds__(kReduceThreads)
+k_sum_into(int nparts, const double* __restrict__ partial, double* __restrict__ acc) {
+    __shared__ double buf[kReduceThreads];
     double s = 0.0;
-    for (int k = 0; k < nparts; ++k) s = __dadd_rn(s, partial[k]);
-    *acc = __dadd_rn(*acc, s);
+    for (int k = threadIdx.x; k < nparts; k += kReduceThreads) s = __dadd_rn(s, partial[k]);
+    buf[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) buf[threadIdx.x] = __dadd_rn(buf[threadIdx.x], buf[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *acc = __dadd_rn(*acc, buf[0]);
 }
 
 // Input-order <-> cell-order moves of a per-particle binary64 array.

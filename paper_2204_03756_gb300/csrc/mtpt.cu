@@ -273,6 +273,7 @@ void derive(RealHost& R, RealParams& P) {
     P.h2 = R.h2;
     P.dsigma_dD = p.D > 0.0 ? P.sigma / (2.0 * p.D) : 0.0;
     P.inv_2D = p.D > 0.0 ? 1.0 / (2.0 * p.D) : 0.0;
+    P.inv_h2 = R.h2 > 0.0 ? 1.0 / R.h2 : 0.0;
     P.seed = p.seed;
     for (int a = 0; a < 3; ++a) {
         P.box.lo[a] = a < p.dim ? p.lo[a] : 0.0;
@@ -1117,7 +1118,7 @@ int launch_adjoint_step(mtpt_handle* h) {
     k_put_by_id<<<blocks, kBlock, 0, st>>>(n, h->id[o].p, h->lam_new.p, h->lam_in.p);
     const int nparts = (n + kReduceThreads - 1) / kReduceThreads;
     k_block_sums<<<nparts, kReduceThreads, 0, st>>>(n, h->gD.p, h->partial.p);
-    k_sum_into<<<1, 1, 0, st>>>(nparts, h->partial.p, h->acc.p);
+    k_sum_into<<<1, kReduceThreads, 0, st>>>(nparts, h->partial.p, h->acc.p);
     MTPT_CUDA_TRY(cudaGetLastError());
     h->cur = o;
     return MTPT_OK;
