@@ -35,6 +35,13 @@ from paper_2204_03756_gb300 import mtpt, workloads  # noqa: E402
 
 FORMS = {"fp64": mtpt.MTPT_FP64, "fp32w": mtpt.MTPT_FP32W}
 DTYPE = {"fp64": "f64", "fp32w": "f32+f64acc"}
+# timed single-run forms: precision form on the --workload workload, or on
+# the 3-d workload for the "_3d" forms
+FORM_WORKLOAD = {"fp32w": None, "fp64": None, "fp32w_3d": "heaviside_3d", "fp64_3d": "heaviside_3d"}
+
+
+def _base(form: str) -> str:
+    return form.split("_")[0]
 
 
 def _peaks():
@@ -51,7 +58,7 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
     """Bytes the kernel's own arithmetic must read and write once per particle
     (its inputs and outputs; cell-list traffic excluded)."""
     x = 8 * dim
-    r = 8 if form == "fp64" else 4
+    r = 8 if _base(form) == "fp64" else 4
     table = {
         "walk_key": 2 * x,                 # positions read + written
         "rowsum_f64": x + r, "rowsum_f32": x + r,          # positions in, r out
@@ -67,6 +74,7 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # particles; traffic grows in proportion to the particles a launch processes,
 # so it is scaled to the bench's launch).  Valid only for the kernel source it
 # was measured on: a different hash of kernels.cuh reports traffic as null.
+TRAFFIC_DIM = 2
 TRAFFIC_SOURCE_SHA1 = "f55d983c9b11"
 TRAFFIC_BYTES_PER_PARTICLE = {
     "walk_key": (177.794816e6 + 117.469440e6) / 8e6,
@@ -141,7 +149,7 @@ def _dist():
 
 def _params(w, form: str, rank: int) -> mtpt.Params:
     return mtpt.Params(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
-                       lo=w.lo, hi=w.hi, seed=w.seed + rank, precision=FORMS[form])
+                       lo=w.lo, hi=w.hi, seed=w.seed + rank, precision=FORMS[_base(form)])
 
 
 def workload_config(w, form: str, world: int) -> dict:
@@ -215,7 +223,7 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
     max_ms, pairs = reduce_over_ranks(ms, pairs, dist)
     sec = max_ms / 1e3
     return {
-        "form": form, "ms": max_ms, "ms_per_step": max_ms / steps,
+        "form": form, "workload": w.name, "n": w.n, "ms": max_ms, "ms_per_step": max_ms / steps,
         "particle_steps_per_s": job_throughput(w.n, steps, world, max_ms),
         "pair_interactions_per_s": pairs / sec,
         "pairs_per_particle_step": pairs / (w.n * steps * world),
@@ -356,7 +364,8 @@ def roofline(w, res, peaks):
     algo = _algo_bytes_per_particle(name, w.dim, res["form"]) * w.n
     achieved = algo / per_launch_s / 1e9
     traffic = None
-    if name in TRAFFIC_BYTES_PER_PARTICLE and _kernel_source_sha1() == TRAFFIC_SOURCE_SHA1:
+    if (name in TRAFFIC_BYTES_PER_PARTICLE and w.dim == TRAFFIC_DIM
+            and _kernel_source_sha1() == TRAFFIC_SOURCE_SHA1):
         traffic = TRAFFIC_BYTES_PER_PARTICLE[name] * w.n
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -395,27 +404,110 @@ def e2e_form(w, pos, mass, form, steps, rank):
             "d2h_bytes_per_step": int(w.n * 8), "steps": steps}
 
 
-def cpu_baseline(w, pos, mass, form):
+def _step_errors(p, pos, mass, steps, x_ref, m_ref, npairs):
+    with mtpt.Simulation(p, pos, mass) as sim:
+        sim.step(steps)
+        x, m, info = sim.positions(), sim.masses(), sim.info()
+    return {"max_rel_err_vs_oracle": float(np.abs(m - m_ref).max() / np.abs(m_ref).max()),
+            "positions_bit_exact": bool(np.array_equal(x, x_ref)),
+            "pair_count_equal": bool(info["pair_count"] == npairs)}
+
+
+def _oracle_params(O, p):
+    return O.OracleParams(dim=p.dim, D=p.D, kappa=p.kappa, dt=p.dt, beta=p.beta, lam=p.lam,
+                          lo=tuple(p.lo) + (0.0,) * (3 - p.dim),
+                          hi=tuple(p.hi) + (0.0,) * (3 - p.dim), seed=p.seed)
+
+
+def cpu_baseline(w, pos, mass, forms, batched=False, adjoint=False):
     """The CPU oracle timed on one core over one full time step of the whole
-    workload; the same step on the GPU is compared with it element by element."""
+    workload.  The same leg reports every form's error against the oracle:
+    the 2-d forms on that full step, the 3-d forms on one step of the 3-d
+    workload at 200,000 particles, the batched kernels on two steps of four
+    ensemble realisations spanning the count range (batched together, each
+    compared with its own oracle run), and the adjoint's dL/dM_0 against the
+    oracle's reverse sweep on 20,000 particles over 10 steps."""
     import oracle as O
-    p = _params(w, form, 0)
-    op = O.OracleParams(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
-                        lo=tuple(w.lo) + (0.0,) * (3 - w.dim),
-                        hi=tuple(w.hi) + (0.0,) * (3 - w.dim), seed=w.seed)
     t0 = time.perf_counter()
+    op = _oracle_params(O, _params(w, forms[0], 0))
     x_ref, m_ref, npairs = O.run(op, pos, mass, 1)
     sec = time.perf_counter() - t0
-    with mtpt.Simulation(p, pos, mass) as sim:
-        sim.step(1)
-        x_gpu, m_gpu, info = sim.positions(), sim.masses(), sim.info()
-    err = float(np.abs(m_gpu - m_ref).max() / np.abs(m_ref).max())
+    parity = {}
+    for f in forms:
+        if FORM_WORKLOAD.get(f) is None:
+            parity[f] = dict(_step_errors(_params(w, f, 0), pos, mass, 1, x_ref, m_ref, npairs),
+                             case=f"{w.name}, n={w.n}, 1 step")
+    forms3 = [f for f in forms if FORM_WORKLOAD.get(f) == "heaviside_3d"]
+    if forms3:
+        w3 = workloads.get("heaviside_3d", 200_000)
+        p3, m3 = workloads.initial_state(w3)
+        x3r, m3r, n3 = O.run(_oracle_params(O, _params(w3, forms3[0], 0)), p3, m3, 1)
+        for f in forms3:
+            parity[f] = dict(_step_errors(_params(w3, f, 0), p3, m3, 1, x3r, m3r, n3),
+                             case=f"heaviside_3d, n={w3.n}, 1 step")
+    if batched:
+        e = workloads.ensemble()
+        order = np.argsort(e.counts)
+        pick = [int(order[k]) for k in (0, len(order) // 3, 2 * len(order) // 3, len(order) - 1)]
+        members = [e.members[k] for k in pick]
+        states = [workloads.initial_state(m) for m in members]
+        params = [_params(m, "fp32w", 0) for m in members]
+        with mtpt.Batch(params, [m.n for m in members],
+                        np.concatenate([st[0] for st in states], axis=1),
+                        np.concatenate([st[1] for st in states])) as bt:
+            bt.step(2)
+            bx, bm = bt.split(bt.positions()), bt.split(bt.masses())
+        errs, exact = [], True
+        for k, (m, st) in enumerate(zip(members, states)):
+            xr, mr, _ = O.run(_oracle_params(O, params[k]), st[0], st[1], 2)
+            errs.append(float(np.abs(bm[k] - mr).max() / np.abs(mr).max()))
+            exact &= bool(np.array_equal(bx[k], xr))
+        parity["batched"] = {"max_rel_err_vs_oracle": max(errs), "positions_bit_exact": exact,
+                             "case": "2 steps of ensemble realisations with "
+                                     f"{[m.n for m in members]} particles, batched together"}
+    if adjoint:
+        parity["adjoint"] = _adjoint_parity(O)
     return {"value": w.n / sec, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"one full time step of all {w.n} particles (serial C oracle, K-D tree)",
-            "seconds": sec, "pair_interactions_per_s": npairs / sec,
-            "parity": {"form": form, "max_rel_err_vs_oracle": err,
-                       "positions_bit_exact": bool(np.array_equal(x_gpu, x_ref)),
-                       "pair_count_equal": bool(info["pair_count"] == npairs)}}
+            "seconds": sec, "pair_interactions_per_s": npairs / sec, "parity": parity}
+
+
+def _adjoint_parity(O, n=20_000, steps=10, nbins=(20, 20)):
+    """dL/dM_0 of the binned misfit: GPU adjoint vs the oracle's transfer
+    operator applied in reverse (it is symmetric) along the oracle's walk."""
+    import torch
+    w = workloads.get("uniform_mass_2d", n)
+    pos, mass = workloads.initial_state(w)
+    p = _params(w, "fp64", 0)
+    op = _oracle_params(O, p)
+    ids = np.arange(n, dtype=np.uint32)
+    xs, x, m = [], pos, mass
+    for t in range(steps):
+        x = O.random_walk(op, x, ids, t)
+        m = O.mass_transfer(op, x, m)[0]
+        xs.append(x)
+    target = workloads.target_field(nbins, w.lo, w.hi).ravel()
+    ix = np.clip(((x[0] - w.lo[0]) / (w.hi[0] - w.lo[0]) * nbins[0]).astype(int), 0, nbins[0] - 1)
+    iy = np.clip(((x[1] - w.lo[1]) / (w.hi[1] - w.lo[1]) * nbins[1]).astype(int), 0, nbins[1] - 1)
+    b = ix * nbins[1] + iy
+    area = (w.hi[0] - w.lo[0]) / nbins[0] * (w.hi[1] - w.lo[1]) / nbins[1]
+    C = np.bincount(b, weights=m, minlength=nbins[0] * nbins[1]) / area
+    g = 2.0 * (C - target)[b] / area
+    lam = g.copy()
+    for t in reversed(range(steps)):
+        lam = O.mass_transfer(op, xs[t], lam)[0]
+    h = mtpt.mtpt_create(p)
+    try:
+        mtpt.mtpt_set_particles(h, 2, pos, mass)
+        mtpt.mtpt_adjoint_forward(h, steps, 4)
+        gt = torch.from_numpy(g).cuda()
+        g0 = torch.empty_like(gt)
+        mtpt.mtpt_adjoint_backward(h, gt, g0)
+    finally:
+        mtpt.mtpt_destroy(h)
+    got = g0.cpu().numpy()
+    return {"max_rel_err_vs_oracle": float(np.abs(got - lam).max() / np.abs(lam).max()),
+            "quantity": "dL/dM_0", "case": f"uniform_mass_2d, n={n}, {steps} steps"}
 
 
 def reference_arm(args, w, pos, mass):
@@ -461,7 +553,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
-    ap.add_argument("--forms", default="fp32w,fp64,batched,adjoint",
+    ap.add_argument("--forms", default="fp32w,fp64,fp32w_3d,batched,adjoint",
                     help="comma list; the first is the headline value")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -493,8 +585,26 @@ def main():
     mtpt.load()
     pos, mass = workloads.initial_state(w)
     forms = [f for f in args.forms.split(",") if f and f not in ("batched", "adjoint")]
-    results = {f: time_form(w, pos, mass, f, args.steps, args.warmup, rank, world, dist)
-               for f in forms}
+    for f in forms:
+        if f not in FORM_WORKLOAD:
+            ap.error(f"unknown form {f!r}")
+    if forms and FORM_WORKLOAD[forms[0]] is not None:
+        ap.error("the first form (the headline) must run on --workload")
+    states = {}
+
+    def state_of(f):
+        name = FORM_WORKLOAD[f]
+        if name is None:
+            return w, pos, mass
+        if name not in states:
+            wf = workloads.get(name)
+            states[name] = (wf,) + tuple(workloads.initial_state(wf))
+        return states[name]
+
+    results = {}
+    for f in forms:
+        wf, pf, mf = state_of(f)
+        results[f] = time_form(wf, pf, mf, f, args.steps, args.warmup, rank, world, dist)
     batched = None
     if "batched" in args.forms.split(","):
         batched = time_batched(args.steps, args.warmup, rank, world, dist)
@@ -526,7 +636,7 @@ def main():
         "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": DTYPE[forms[0]], "data": "synthetic",
+        "dtype": DTYPE[_base(forms[0])], "data": "synthetic",
         "config": workload_config(w, forms[0], world),
         "pair_interactions_per_s": head["pair_interactions_per_s"],
         "pairs_per_particle_step": head["pairs_per_particle_step"],
@@ -539,13 +649,16 @@ def main():
                   for f, r in results.items()},
     }
     for f, r in results.items():
-        line["forms"][f]["roofline"] = roofline(w, r, peaks)
+        line["forms"][f]["roofline"] = roofline(state_of(f)[0], r, peaks)
     if batched is not None:
         line["forms"]["batched"] = batched
     if adjoint is not None:
         line["forms"]["adjoint"] = adjoint
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, pos, mass, forms[0])
+        line["cpu_baseline"] = cpu_baseline(w, pos, mass, forms, batched=batched is not None,
+                                            adjoint=adjoint is not None)
+        for f, err in line["cpu_baseline"]["parity"].items():
+            line["forms"][f]["err_vs_oracle"] = err
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
