@@ -567,6 +567,14 @@ __device__ __forceinline__ double kernel_d2(const double* __restrict__ pos, int6
     return d2;
 }
 
+// Hardware square root approximation (relative error far below the
+// windows' slack trim_eps, which covers it).
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Binary32 x difference of candidate o from particle me (cells cx_o - cx_me
 // apart, |cx_o - cx_me| <= 1 so the shift is exact): changes sign exactly
 // when the pair swaps.
@@ -636,7 +644,7 @@ __device__ __forceinline__ void for_each_row(uint32_t cell, const float4& me,
             const float gy = dy < 0 ? gy_below : (dy > 0 ? gy_above : 0.0f);
             const float r2 = __fsub_rn(pp.reach2, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
             if (r2 < 0.0f) continue;
-            const float rx = __fadd_rn(__fsqrt_rn(r2), eps);
+            const float rx = __fadd_rn(sqrt_approx(r2), eps);
             const uint32_t rowc = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
                                                  uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
             uint32_t lo = __ldg(start + rowc + xlo);
@@ -889,7 +897,7 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
                 const float gz = dz < 0 ? gz_below : (dz > 0 ? gz_above : 0.0f);
                 const float r2 = __fsub_rn(pp.reach2, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
                 if (r2 >= 0.0f) {
-                    rx = __fadd_rn(__fsqrt_rn(r2), eps);
+                    rx = __fadd_rn(sqrt_approx(r2), eps);
                     const uint32_t rowc = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
                                                          uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
                     uint32_t lo = __ldg(start + rowc + xlo);
