@@ -124,9 +124,11 @@ int mtpt_set_stream(mtpt_handle* h, void* stream);
  * float64).  Every coordinate must be finite and inside [lo, hi] of its axis
  * (MTPT_ERR_OUT_OF_DOMAIN otherwise) and every mass finite, in the precision
  * form at most 1e30 in magnitude (MTPT_ERR_INVALID_ARG otherwise); on either
- * error the handle keeps its old state.  The buffers are copied into a device
- * staging area (kept by the handle, (dim + 1) n float64) and checked there;
- * the call returns once the host buffers are no longer read.
+ * error the handle keeps its old state.  The buffers are copied to the device
+ * and checked there: into the free half of the handle's double-buffered state
+ * when its capacity already holds n particles, else into a staging area kept
+ * by the handle ((dim + 1) n float64).  The call returns once the host buffers
+ * are no longer read.
  * Particle ids are 0..n-1 in input order; they key the walk's generator.
  * Resets the step counter and pair counter to 0.  n = 0 is allowed. */
 int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass);

@@ -278,16 +278,18 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
     }
 }
 
-// Check of host-loaded input in its device staging copy (positions dim x n
-// with stride n, then n masses): a position outside its realisation's box
+// Check of host-loaded input in its device copy (positions dim x n with
+// stride `stride`, masses n): a position outside its realisation's box
 // [lo, hi] (NaN included) sets bit 1, a mass that is not finite or above
 // mass_limit in magnitude sets bit 2.  box holds lo[3], hi[3] per
 // realisation; first[k] is realisation k's first particle (first[nreal] = n).
+// With id_out, also writes the particle ids 0..n-1 there.
 template <int DIM>
 __global__ void __launch_bounds__(kBlock)
-k_check_input(int n, int nreal, const double* __restrict__ pos, const double* __restrict__ mass,
-              const double* __restrict__ box, const uint32_t* __restrict__ first,
-              double mass_limit, uint32_t* __restrict__ flags) {
+k_check_input(int n, int64_t stride, int nreal, const double* __restrict__ pos,
+              const double* __restrict__ mass, const double* __restrict__ box,
+              const uint32_t* __restrict__ first, double mass_limit,
+              uint32_t* __restrict__ flags, uint32_t* __restrict__ id_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bad = 0;
     if (i < n) {
@@ -303,11 +305,12 @@ k_check_input(int n, int nreal, const double* __restrict__ pos, const double* __
         const double* b = box + 6 * k;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            const double x = pos[int64_t(a) * n + i];
+            const double x = pos[int64_t(a) * stride + i];
             if (!(x >= b[a] && x <= b[3 + a])) bad |= 1u;
         }
         const double m = mass[i];
         if (not_finite(m) || !(fabs(m) <= mass_limit)) bad |= 2u;
+        if (id_out) id_out[i] = uint32_t(i);
     }
     const uint32_t any = __reduce_or_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0 && any) atomicOr(flags, any);

@@ -794,8 +794,11 @@ int unpermute_to(mtpt_handle* h, const double* src, int naxes, double* out_dev) 
 int copy_out_host(mtpt_handle* h, int naxes, double* out) {
     const size_t bytes = size_t(naxes) * size_t(h->n) * sizeof(double);
     if (bytes) MTPT_CUDA_TRY(cudaMemcpyAsync(out, h->out_tmp.p, bytes, cudaMemcpyDeviceToHost, h->stream));
+    uint32_t st = 0;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&st, h->status.p, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
     MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return read_status(h);
+    if (st & (kStatusNonFinite | kStatusOutOfDomain)) return MTPT_ERR_OUT_OF_DOMAIN;
+    return MTPT_OK;
 }
 
 int set_step_dev(mtpt_handle* h, uint64_t step) {
@@ -808,7 +811,7 @@ int set_step_dev(mtpt_handle* h, uint64_t step) {
 // Loads particles (counts[k] per realisation, concatenated) from host or
 // device buffers.
 int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, const double* mass,
-                   cudaMemcpyKind kind) {
+                   cudaMemcpyKind kind, int in_place = -1) {
     const int d = h->dim;
     int64_t n = 0;
     for (int k = 0; k < h->nreal; ++k) {
@@ -834,17 +837,23 @@ int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, con
                                       cudaMemcpyHostToDevice, h->stream));
     }
     MTPT_TRY(upload_tables(h));
-    h->cur = 0;
+    // the particles already sit in buffer in_place (positions, masses, ids)
+    // when the host load wrote them there
+    h->cur = in_place >= 0 ? in_place : 0;
+    const int b = h->cur;
     if (n > 0) {
-        MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[0].p, size_t(h->cap) * sizeof(double), pos,
-                                        size_t(n) * sizeof(double), size_t(n) * sizeof(double), d,
-                                        kind, h->stream));
-        MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[0].p, mass, size_t(n) * sizeof(double), kind, h->stream));
-        k_iota<<<grid_for(n), kBlock, 0, h->stream>>>(int(n), h->id[0].p);
-        MTPT_CUDA_TRY(cudaGetLastError());
+        if (in_place < 0) {
+            MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[b].p, size_t(h->cap) * sizeof(double), pos,
+                                            size_t(n) * sizeof(double), size_t(n) * sizeof(double),
+                                            d, kind, h->stream));
+            MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[b].p, mass, size_t(n) * sizeof(double), kind,
+                                          h->stream));
+            k_iota<<<grid_for(n), kBlock, 0, h->stream>>>(int(n), h->id[b].p);
+            MTPT_CUDA_TRY(cudaGetLastError());
+        }
         if (h->batch) {
             k_fill_rid<<<grid_for(n), kBlock, 0, h->stream>>>(int(n), h->nreal, h->id_first.p,
-                                                             h->rid[0].p);
+                                                             h->rid[b].p);
             MTPT_CUDA_TRY(cudaGetLastError());
         }
     }
@@ -857,13 +866,17 @@ int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, con
     return MTPT_OK;
 }
 
-// Host loads are copied into a device staging area and checked there
-// (k_check_input: positions inside their realisation's box, masses finite and,
-// in the precision form, at most 1e30 in magnitude) before the handle's state
-// is touched, so a rejected load leaves the old state in place.  On success
-// *pos_dev / *mass_dev point at the staged copy (positions dim x n).
+// Host loads are copied to the device and checked there (k_check_input:
+// positions inside their realisation's box, masses finite and, in the
+// precision form, at most 1e30 in magnitude) before the handle's state is
+// touched, so a rejected load leaves the old state in place.  When the
+// handle's capacity already holds n particles the copy goes straight into the
+// free half of the state double buffer (which becomes current on success,
+// *in_place set to its index, ids written by the check); otherwise into a
+// staging area, and *pos_dev / *mass_dev point at it (positions dim x n).
 int stage_host_particles(mtpt_handle* h, const int64_t* counts, const double* pos,
-                         const double* mass, const double** pos_dev, const double** mass_dev) {
+                         const double* mass, const double** pos_dev, const double** mass_dev,
+                         int* in_place) {
     int64_t n = 0;
     for (int k = 0; k < h->nreal; ++k) {
         if (counts[k] < 0) return MTPT_ERR_INVALID_ARG;
@@ -873,9 +886,9 @@ int stage_host_particles(mtpt_handle* h, const int64_t* counts, const double* po
     if (n > 0 && (!pos || !mass)) return MTPT_ERR_INVALID_ARG;
     *pos_dev = nullptr;
     *mass_dev = nullptr;
+    *in_place = -1;
     if (n == 0) return MTPT_OK;
     const int d = h->dim;
-    MTPT_TRY(h->stage.ensure(size_t(d + 1) * size_t(n)));
     MTPT_TRY(h->chk_flag.ensure(1));
     if (!h->chk_box.p) {
         std::vector<double> box(size_t(6) * size_t(h->nreal), 0.0);
@@ -897,24 +910,43 @@ int stage_host_particles(mtpt_handle* h, const int64_t* counts, const double* po
                                       cudaMemcpyHostToDevice, h->stream));
         MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));   // `first` is a local
     }
-    double* st = h->stage.p;
-    MTPT_CUDA_TRY(cudaMemcpyAsync(st, pos, size_t(d) * size_t(n) * sizeof(double),
-                                  cudaMemcpyHostToDevice, h->stream));
-    MTPT_CUDA_TRY(cudaMemcpyAsync(st + size_t(d) * size_t(n), mass, size_t(n) * sizeof(double),
-                                  cudaMemcpyHostToDevice, h->stream));
+    const int f = 1 - h->cur;
+    const bool direct = n <= h->cap && h->pos[f].p && h->mass[f].p && h->id[f].p;
+    double* sp;
+    double* sm;
+    int64_t stride;
+    if (direct) {
+        sp = h->pos[f].p;
+        sm = h->mass[f].p;
+        stride = h->cap;
+        MTPT_CUDA_TRY(cudaMemcpy2DAsync(sp, size_t(stride) * sizeof(double), pos,
+                                        size_t(n) * sizeof(double), size_t(n) * sizeof(double), d,
+                                        cudaMemcpyHostToDevice, h->stream));
+    } else {
+        MTPT_TRY(h->stage.ensure(size_t(d + 1) * size_t(n)));
+        sp = h->stage.p;
+        sm = h->stage.p + size_t(d) * size_t(n);
+        stride = n;
+        MTPT_CUDA_TRY(cudaMemcpyAsync(sp, pos, size_t(d) * size_t(n) * sizeof(double),
+                                      cudaMemcpyHostToDevice, h->stream));
+    }
+    MTPT_CUDA_TRY(cudaMemcpyAsync(sm, mass, size_t(n) * sizeof(double), cudaMemcpyHostToDevice,
+                                  h->stream));
     MTPT_CUDA_TRY(cudaMemsetAsync(h->chk_flag.p, 0, sizeof(uint32_t), h->stream));
     const double mass_limit = h->precision == MTPT_FP32W ? 1e30 : HUGE_VAL;
-    const double* sp = st;
-    const double* sm = st + size_t(d) * size_t(n);
+    uint32_t* ids = direct ? h->id[f].p : nullptr;
     switch (d) {
         case 1: k_check_input<1><<<grid_for(n), kBlock, 0, h->stream>>>(
-                    int(n), h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit, h->chk_flag.p);
+                    int(n), stride, h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit,
+                    h->chk_flag.p, ids);
                 break;
         case 2: k_check_input<2><<<grid_for(n), kBlock, 0, h->stream>>>(
-                    int(n), h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit, h->chk_flag.p);
+                    int(n), stride, h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit,
+                    h->chk_flag.p, ids);
                 break;
         default: k_check_input<3><<<grid_for(n), kBlock, 0, h->stream>>>(
-                    int(n), h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit, h->chk_flag.p);
+                    int(n), stride, h->nreal, sp, sm, h->chk_box.p, h->chk_first.p, mass_limit,
+                    h->chk_flag.p, ids);
                 break;
     }
     MTPT_CUDA_TRY(cudaGetLastError());
@@ -925,6 +957,7 @@ int stage_host_particles(mtpt_handle* h, const int64_t* counts, const double* po
     if (flag & 2u) return MTPT_ERR_INVALID_ARG;
     *pos_dev = sp;
     *mass_dev = sm;
+    if (direct) *in_place = f;
     return MTPT_OK;
 }
 
@@ -1265,16 +1298,18 @@ int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const doubl
     if (!h || h->nreal != 1) return MTPT_ERR_INVALID_ARG;
     if (n < 0) return MTPT_ERR_INVALID_ARG;
     const double *pd = nullptr, *md = nullptr;
-    MTPT_TRY(stage_host_particles(h, &n, pos, mass, &pd, &md));
-    return load_particles(h, &n, pd, md, cudaMemcpyDeviceToDevice);
+    int in_place = -1;
+    MTPT_TRY(stage_host_particles(h, &n, pos, mass, &pd, &md, &in_place));
+    return load_particles(h, &n, pd, md, cudaMemcpyDeviceToDevice, in_place);
 }
 
 int mtpt_set_particles_batch(mtpt_handle* h, const int64_t* counts, const double* pos,
                              const double* mass) {
     if (!h || !counts) return MTPT_ERR_INVALID_ARG;
     const double *pd = nullptr, *md = nullptr;
-    MTPT_TRY(stage_host_particles(h, counts, pos, mass, &pd, &md));
-    return load_particles(h, counts, pd, md, cudaMemcpyDeviceToDevice);
+    int in_place = -1;
+    MTPT_TRY(stage_host_particles(h, counts, pos, mass, &pd, &md, &in_place));
+    return load_particles(h, counts, pd, md, cudaMemcpyDeviceToDevice, in_place);
 }
 
 int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
