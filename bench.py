@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -469,7 +470,44 @@ def cpu_baseline(w, pos, mass, forms, batched=False, adjoint=False):
         parity["adjoint"] = _adjoint_parity(O)
     return {"value": w.n / sec, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"one full time step of all {w.n} particles (serial C oracle, K-D tree)",
-            "seconds": sec, "pair_interactions_per_s": npairs / sec, "parity": parity}
+            "seconds": sec, "pair_interactions_per_s": npairs / sec, "parity": parity,
+            "erf_check": _erf_check(O), "host": _host_info()}
+
+
+def _host_info():
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_count": os.cpu_count(), "cpu": model, "machine": platform.machine()}
+
+
+def _erf_check(O):
+    """The small 2-d Heaviside case (1e4 particles, 100 steps, binary64): GPU
+    and oracle runs against the closed-form erfc profile of pure diffusion
+    (RMSE of the mean particle mass in 50 slabs of x), and against each
+    other."""
+    from oracle import analytic as A
+    w = workloads.get("heaviside_2d")
+    pos, mass = workloads.initial_state(w)
+    p = _params(w, "fp64", 0)
+    with mtpt.Simulation(p, pos, mass) as sim:
+        sim.step(w.steps)
+        xg, mg = sim.positions(), sim.masses()
+    xr, mr, _ = O.run(_oracle_params(O, p), pos, mass, w.steps)
+    t = w.steps * w.dt
+    out = {"workload": w.name, "n": w.n, "steps": w.steps}
+    for name, (x, m) in (("gpu", (xg, mg)), ("oracle", (xr, mr))):
+        c, mean, _ = A.binned_profile(x[0], m, w.lo[0], w.hi[0], 50)
+        out[f"rmse_{name}_vs_erf"] = A.rmse(mean, A.erf_profile(c, t, w.D, w.mass_param, "left"))
+    out["max_rel_err_gpu_vs_oracle"] = float(np.abs(mg - mr).max() / np.abs(mr).max())
+    out["positions_bit_exact"] = bool(np.array_equal(xg, xr))
+    return out
 
 
 def _adjoint_parity(O, n=20_000, steps=10, nbins=(20, 20)):

@@ -107,6 +107,15 @@ typedef struct mtpt_info {
 
 typedef struct mtpt_handle mtpt_handle;
 
+/* Bounds-check word of the checked build (the library compiled with
+ * MTPT_CHECKED, which verifies index invariants of every kernel at run time
+ * and skips any access that violates one): *out receives the OR of the
+ * violated checks since the last reset on the current device (0: none), after
+ * a device synchronisation; reset != 0 clears it.  The normal build compiles
+ * the checks out and returns MTPT_ERR_STATE with *out = 0.  No counterpart in
+ * the paper: it stands in for a memory checker in the tests. */
+int mtpt_check_word(uint32_t* out, int32_t reset);
+
 /* Create a handle on the current CUDA device.  *out receives the handle.
  * Validates the parameters (MTPT_ERR_INVALID_ARG).  Allocates nothing on the
  * device until particles are set. */

@@ -3,7 +3,10 @@
 One translation unit (``csrc/mtpt.cu``) compiled by nvcc with
 ``-gencode arch=compute_103a,code=sm_103a``; the shared object lands in
 ``paper_2204_03756_gb300/_lib/`` next to the package, so the process that
-imports the package loads it from the source tree.
+imports the package loads it from the source tree.  A second object,
+``libmtpt_checked.so``, is the same source with ``-DMTPT_CHECKED`` (run-time
+bounds checks of the kernels' index invariants, for the tests); both compile
+in parallel.
 """
 from __future__ import annotations
 
@@ -16,6 +19,8 @@ SRC_DIR = os.path.join(PKG_DIR, "csrc")
 INCLUDE_DIR = os.path.join(os.path.dirname(PKG_DIR), "include")
 LIB_DIR = os.path.join(PKG_DIR, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libmtpt.so")
+LIB_CHECKED_PATH = os.path.join(LIB_DIR, "libmtpt_checked.so")
+VARIANTS = ((LIB_PATH, ()), (LIB_CHECKED_PATH, ("-DMTPT_CHECKED",)))
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -44,33 +49,38 @@ def build_command(out_path: str = LIB_PATH, extra=()) -> list:
             "-o", out_path, os.path.join(SRC_DIR, "mtpt.cu")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB_PATH):
+def needs_build(path: str = LIB_PATH) -> bool:
+    if not os.path.exists(path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(path)
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
 def start_build(force: bool = False):
-    """Launch nvcc in the background; returns the Popen (or None if the
-    library is up to date)."""
-    if not force and not needs_build():
-        return None
+    """Launch nvcc for every out-of-date variant in the background; returns
+    the list of (Popen, temporary path, final path)."""
     os.makedirs(LIB_DIR, exist_ok=True)
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
-    proc = subprocess.Popen(build_command(tmp), stdout=subprocess.PIPE,
-                            stderr=subprocess.STDOUT, text=True)
-    proc._mtpt_tmp = tmp  # type: ignore[attr-defined]
-    return proc
+    jobs = []
+    for path, extra in VARIANTS:
+        if not force and not needs_build(path):
+            continue
+        tmp = path + f".tmp{os.getpid()}"
+        proc = subprocess.Popen(build_command(tmp, extra), stdout=subprocess.PIPE,
+                                stderr=subprocess.STDOUT, text=True)
+        jobs.append((proc, tmp, path))
+    return jobs
 
 
-def finish_build(proc) -> str:
-    if proc is None:
-        return LIB_PATH
-    out, _ = proc.communicate()
-    if proc.returncode != 0:
-        raise RuntimeError(f"nvcc failed ({proc.returncode}):\n{out}")
-    os.replace(proc._mtpt_tmp, LIB_PATH)
+def finish_build(jobs) -> str:
+    errors = []
+    for proc, tmp, path in jobs or ():
+        out, _ = proc.communicate()
+        if proc.returncode != 0:
+            errors.append(f"nvcc failed for {os.path.basename(path)} ({proc.returncode}):\n{out}")
+            continue
+        os.replace(tmp, path)
+    if errors:
+        raise RuntimeError("\n".join(errors))
     return LIB_PATH
 
 

@@ -30,6 +30,28 @@ namespace mtpt {
 
 enum : uint32_t { kStatusNonFinite = 1u, kStatusOutOfDomain = 2u };
 
+// Bounds-checked build (compiled with -DMTPT_CHECKED; the tests load it as a
+// second library): index invariants that hold by construction are verified at
+// run time; a violation sets its bit in a device word and the access is
+// skipped.  The normal build compiles every check to `true`.
+enum : uint32_t {
+    kChkCell = 1u,       // walk: cell index inside the realisation's cells
+    kChkSlot = 2u,       // scatter: counting-sort slot inside [0, n)
+    kChkGather = 4u,     // gather: source and in-cell rank inside the cell's range
+    kChkRow = 8u,        // pair search: neighbour row inside the realisation's cells
+    kChkSegment = 16u,   // segment engine: entries within the segments' capacity
+    kChkOutput = 32u,    // outputs: particle id inside [0, n)
+};
+#ifdef MTPT_CHECKED
+__device__ uint32_t g_check_word;
+__device__ __forceinline__ bool check(bool ok, uint32_t bit) {
+    if (!ok) atomicOr(&g_check_word, bit);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool check(bool, uint32_t) { return true; }
+#endif
+
 constexpr int kBlock = 256;
 constexpr int kScanThreads = 1024;
 constexpr int kScanTile = 4 * kScanThreads;   // cells per scan block
@@ -273,6 +295,9 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
         bool bad = false;
         const uint32_t c = P.cell_base + cell_of<DIM>(x, P.g, &bad);
         if (bad) atomicOr(status, kStatusNonFinite);
+        if (!check(c - P.cell_base < uint32_t(P.g.n[0]) * uint32_t(P.g.n[1]) * uint32_t(P.g.n[2]),
+                   kChkCell))
+            return;
         key[i] = c;
         atomicAdd(&count[c], 1u);
     }
@@ -459,7 +484,9 @@ k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ 
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t c = key[i];
-    const uint32_t slot = start[c] + atomicSub(&count[c], 1u) - 1u;
+    const uint32_t left = atomicSub(&count[c], 1u);
+    const uint32_t slot = start[c] + left - 1u;
+    if (!check(left >= 1u && slot < uint32_t(n), kChkSlot)) return;
     perm[slot] = uint32_t(i);
 }
 
@@ -484,6 +511,7 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t src = perm[s];
+    if (!check(src < uint32_t(n), kChkGather)) return;
     const uint32_t c = key[src];
     const uint32_t b = start[c], e = start[c + 1];
     const uint32_t my_id = id_in[src];
@@ -491,10 +519,12 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
     uint32_t rank = 0;
     for (uint32_t k = b; k < e; ++k) {
         const uint32_t o = perm[k];
+        if (!check(o < uint32_t(n), kChkGather)) continue;
         const long long xo = order_key(pos_in[o]);
         rank += (xo < my_x || (xo == my_x && id_in[o] < my_id)) ? 1u : 0u;
     }
     const uint32_t dst = b + rank;
+    if (!check(dst < e, kChkGather)) return;
     id_out[dst] = my_id;
     cell_out[dst] = c;
     if constexpr (View::kBatch) rid_out[dst] = __ldg(v.rid_input + src);
@@ -650,6 +680,9 @@ __device__ __forceinline__ void for_each_row(uint32_t cell, const float4& me,
             const float rx = __fadd_rn(sqrt_approx(r2), eps);
             const uint32_t rowc = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
                                                  uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
+            if (!check(rowc + uint32_t(xhi) + 1u - P.cell_base <=
+                           uint32_t(g.n[0]) * uint32_t(g.n[1]) * uint32_t(g.n[2]), kChkRow))
+                continue;
             uint32_t lo = __ldg(start + rowc + xlo);
             uint32_t hi = __ldg(start + rowc + xhi + 1);
             const uint32_t j3 = hi;
@@ -835,6 +868,7 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
     auto flush = [&]() {
         uint32_t total;
         const uint32_t off = warp_exclusive_scan(cnt, &total);
+        check(cnt <= uint32_t(SEG) && total <= uint32_t(SEG) * 32u, kChkSegment);
         S.off[warp][lane] = off;
         S.base[warp][lane] = done;
         for (uint32_t k = 0; k < cnt; ++k) S.owner[warp][off + k] = uint8_t(lane);
@@ -903,8 +937,11 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
                     rx = __fadd_rn(sqrt_approx(r2), eps);
                     const uint32_t rowc = P.cell_base + (uint32_t(c[2] + dz) * uint32_t(g.n[1]) +
                                                          uint32_t(c[1] + dy)) * uint32_t(g.n[0]);
-                    uint32_t lo = __ldg(start + rowc + xlo);
-                    uint32_t hi = __ldg(start + rowc + xhi + 1);
+                    const bool row_ok = check(
+                        rowc + uint32_t(xhi) + 1u - P.cell_base <=
+                            uint32_t(g.n[0]) * uint32_t(g.n[1]) * uint32_t(g.n[2]), kChkRow);
+                    uint32_t lo = row_ok ? __ldg(start + rowc + xlo) : 0u;
+                    uint32_t hi = row_ok ? __ldg(start + rowc + xhi + 1) : 0u;
                     j3 = hi;
                     while (lo < hi) {
                         const uint32_t mid = (lo + hi) >> 1;
@@ -1322,6 +1359,7 @@ __global__ void k_unpermute(int n, int64_t stride, int naxes, const uint32_t* __
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t k = id[s];
+    if (!check(k < uint32_t(n), kChkOutput)) return;
     for (int a = 0; a < naxes; ++a) {
         const double x = widen(src[(a * stride + s) * src_step]);
         out[int64_t(a) * n + k] = scale == 1.0 ? x : __dmul_rn(x, scale);

@@ -1248,6 +1248,23 @@ int mtpt_adjoint_backward(mtpt_handle* h, const double* gmass_dev, double* gmass
     return read_status(h);
 }
 
+int mtpt_check_word(uint32_t* out, int32_t reset) {
+    if (!out) return MTPT_ERR_INVALID_ARG;
+    *out = 0;
+#ifdef MTPT_CHECKED
+    MTPT_CUDA_TRY(cudaDeviceSynchronize());
+    MTPT_CUDA_TRY(cudaMemcpyFromSymbol(out, g_check_word, sizeof(uint32_t)));
+    if (reset) {
+        const uint32_t zero = 0;
+        MTPT_CUDA_TRY(cudaMemcpyToSymbol(g_check_word, &zero, sizeof(uint32_t)));
+    }
+    return MTPT_OK;
+#else
+    (void)reset;
+    return MTPT_ERR_STATE;
+#endif
+}
+
 int mtpt_create(const mtpt_params* params, mtpt_handle** out) {
     return create_common(params, 1, false, out);
 }

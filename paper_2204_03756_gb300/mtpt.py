@@ -40,7 +40,7 @@ EXPORTED = [
     "mtpt_timing_enable", "mtpt_timing_read", "mtpt_timing_reset", "mtpt_step_noalloc",
     "mtpt_create_batch", "mtpt_set_particles_batch", "mtpt_get_realisation_info",
     "mtpt_set_tuning", "mtpt_get_tuning", "mtpt_autotune", "mtpt_adjoint_forward",
-    "mtpt_adjoint_backward", "mtpt_status_string",
+    "mtpt_adjoint_backward", "mtpt_status_string", "mtpt_check_word",
 ]
 
 
@@ -107,6 +107,10 @@ _lib = None
 
 
 def lib_path() -> str:
+    """The library this process loads: the normal build, or the bounds-checked
+    build when the environment sets MTPT_LIBRARY=checked."""
+    if os.environ.get("MTPT_LIBRARY", "") == "checked":
+        return _build.LIB_CHECKED_PATH
     return _build.LIB_PATH
 
 
@@ -135,6 +139,7 @@ def load():
     lib.mtpt_get_pairs.argtypes = [vp, ctypes.c_int64, P(ctypes.c_int64), vp, vp]
     lib.mtpt_get_info.argtypes = [vp, P(_Info)]
     lib.mtpt_set_step.argtypes = [vp, ctypes.c_uint64]
+    lib.mtpt_check_word.argtypes = [P(ctypes.c_uint32), ctypes.c_int32]
     lib.mtpt_sync.argtypes = [vp]
     lib.mtpt_timing_enable.argtypes = [vp, ctypes.c_int32]
     lib.mtpt_timing_read.argtypes = [vp, ctypes.c_int32, P(_KernelStat), P(ctypes.c_int32)]
@@ -243,6 +248,14 @@ def mtpt_autotune(h, trial_steps: int = 4) -> dict:
     t = _Tuning()
     _check(load().mtpt_autotune(h, trial_steps, ctypes.byref(t)), "mtpt_autotune")
     return {"cell_scale": t.cell_scale, "pair_block": t.pair_block}
+
+
+def mtpt_check_word(reset: bool = False) -> int:
+    """Bounds-check word of the checked build (see include/mtpt.h); raises
+    MtptError(MTPT_ERR_STATE) in the normal build."""
+    out = ctypes.c_uint32()
+    _check(load().mtpt_check_word(ctypes.byref(out), 1 if reset else 0), "mtpt_check_word")
+    return int(out.value)
 
 
 def mtpt_adjoint_forward(h, nsteps: int, checkpoint_every: int) -> None:

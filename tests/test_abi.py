@@ -72,3 +72,17 @@ def test_status_strings(lib):
     for code in range(7):
         assert mtpt.mtpt_status_string(code)
     assert mtpt.mtpt_status_string(99) == "unknown status"
+
+
+def test_checked_library_exports_every_declared_symbol():
+    from paper_2204_03756_gb300 import build
+    build.build()
+    lib = ctypes.CDLL(build.LIB_CHECKED_PATH)
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_normal_build_has_no_check_word(lib):
+    out = ctypes.c_uint32(7)
+    assert lib.mtpt_check_word(ctypes.byref(out), 0) == mtpt.MTPT_ERR_STATE
+    assert out.value == 0
