@@ -76,12 +76,12 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # so it is scaled to the bench's launch).  Valid only for the kernel source it
 # was measured on: a different hash of kernels.cuh reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "f55d983c9b11"
+TRAFFIC_SOURCE_SHA1 = "d4bb827008e3"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (177.794816e6 + 117.469440e6) / 8e6,
-    "gather": (305.862912e6 + 395.149312e6) / 8e6,
-    "rowsum_f32": (177.818112e6 + 24.458752e6) / 8e6,
-    "exchange_f32": (337.840896e6 + 56.212480e6) / 8e6,
+    "walk_key": (177.799168e6 + 117.391360e6) / 8e6,
+    "gather": (305.955840e6 + 395.250944e6) / 8e6,
+    "rowsum_f32": (177.817600e6 + 24.145152e6) / 8e6,
+    "exchange_f32": (337.833984e6 + 56.066560e6) / 8e6,
 }
 
 
@@ -474,13 +474,23 @@ def cpu_baseline(w, pos, mass, forms, batched=False, adjoint=False):
             "erf_check": _erf_check(O), "host": _host_info()}
 
 
+# Arm CPU part numbers (MIDR) of the server cores this may run on
+ARM_PARTS = {"0xd0c": "Neoverse-N1", "0xd40": "Neoverse-V1", "0xd49": "Neoverse-N2",
+             "0xd4f": "Neoverse-V2", "0xd84": "Neoverse-V3"}
+
+
 def _host_info():
     model = platform.processor() or platform.machine()
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu part")):
-                    model = line.split(":", 1)[1].strip()
+                key, _, val = line.partition(":")
+                key, val = key.strip().lower(), val.strip()
+                if key == "model name":
+                    model = val
+                    break
+                if key == "cpu part":
+                    model = f"{ARM_PARTS.get(val, 'Arm')} (CPU part {val})"
                     break
     except OSError:
         pass
