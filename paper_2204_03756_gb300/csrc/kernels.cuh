@@ -1112,7 +1112,7 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
 // hardware ex2, compensated binary32 row sum, rounded to binary32 into rec.w.
 template <int DIM, class View, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)
+__global__ void __launch_bounds__(BLOCK, (DIM == 3 ? 1536 : 2048) / BLOCK)
 k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
              const __grid_constant__ View v, float* __restrict__ r_out,
@@ -1147,7 +1147,7 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
 // bit), mass difference from the binary32 head/tail split (exactly
 // antisymmetric), flux accumulated with compensation, update in binary64.
 template <int DIM, class View, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1536 / BLOCK)
+__global__ void __launch_bounds__(BLOCK, (DIM == 3 ? 1536 : 2048) / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
                const __grid_constant__ View v, const float* __restrict__ r,
