@@ -86,3 +86,25 @@ def test_normal_build_has_no_check_word(lib):
     out = ctypes.c_uint32(7)
     assert lib.mtpt_check_word(ctypes.byref(out), 0) == mtpt.MTPT_ERR_STATE
     assert out.value == 0
+
+
+@pytest.mark.parametrize("variant", ["normal", "checked"])
+def test_c_client_compiles_links_and_runs_without_a_gpu(tmp_path, variant):
+    """The header is valid C99 and a C program links every entry point from
+    the shipped library and gets the documented answers from the calls that
+    need no GPU."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    cuda_build.build()
+    lib = cuda_build.LIB_PATH if variant == "normal" else cuda_build.LIB_CHECKED_PATH
+    here = os.path.dirname(os.path.abspath(__file__))
+    exe = str(tmp_path / "abi_check")
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-o", exe,
+           os.path.join(here, "c", "abi_check.c"), "-I", cuda_build.INCLUDE_DIR, lib,
+           "-Wl,-rpath," + os.path.dirname(lib)]
+    out = subprocess.run(cmd, capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0 and run.stdout.strip() == "ok", run.stdout + run.stderr
