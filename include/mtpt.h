@@ -25,10 +25,15 @@
  *     last mtpt_set_particles* call keeps index i in every output.
  *   - Stream: all device work of a handle is ordered on the handle's stream
  *     (the legacy default stream unless mtpt_set_stream was called).  Calls
- *     with host buffers synchronise that stream before returning; *_device
- *     calls only enqueue work.
+ *     that read host buffers return once the buffers are no longer read (the
+ *     rest of their work may still be queued); calls that write host buffers
+ *     synchronise the stream before returning; *_device calls only enqueue
+ *     work.
  *   - Device errors found inside kernels (non-finite positions) are latched
  *     in a device status word and reported by the next synchronising call.
+ *   - Threads: a handle is not safe for concurrent calls; use one thread per
+ *     handle at a time.  Distinct handles are independent (mtpt_step_noalloc
+ *     shares one scratch array per device; see there).
  */
 #ifndef MTPT_H
 #define MTPT_H
