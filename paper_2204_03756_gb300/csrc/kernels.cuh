@@ -860,18 +860,20 @@ struct SegShared {
     uint32_t base[NW][32];             // entries each lane had before this flush
 };
 
-// Binary64 neighbour lists: pass 1 stores each accepted neighbour j != s and
-// its kernel value K_sj (binary64) in slot k of s (entry at k * stride + s),
-// up to `cap` slots; count[s] is the full number.  Pass 2 of a warp whose
-// lanes all fit their lists reads them instead of searching and re-evaluating
-// exp; otherwise the warp searches.  Both paths visit the same pairs in the
-// same order with the same values.
-struct NbList64 {
+// Neighbour lists: pass 1 stores each accepted neighbour j != s and its pair
+// value (the binary64 K_sj, or (K_sj, dK_sj/dD) in the adjoint) in slot k of
+// s (entry at k * stride + s), up to `cap` slots; count[s] is the full
+// number.  Pass 2 of a warp whose lanes all fit their lists reads them
+// instead of searching and re-evaluating exp; otherwise the warp searches.
+// Both paths visit the same pairs in the same order with the same values.
+template <class V>
+struct NbList {
     uint32_t* j;
-    double* k;
+    V* k;
     uint32_t* count;
     int cap;           // 0: no list
 };
+using NbList64 = NbList<double>;
 
 // Phases A-C for the calling warp (every lane of the warp must call it; lanes
 // with valid = false walk nothing).  eval(owner_s, j, d2f) returns the pair
@@ -885,7 +887,7 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
                                               const uint32_t* __restrict__ start,
                                               const RealParams& P, SegShared<NW, V, D2, SEG>& S,
                                               Eval&& eval, Add&& add,
-                                              NbList64 store = NbList64{}) {
+                                              NbList<V> store = NbList<V>{}) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t warp_s0 = s - uint32_t(lane);
     uint32_t cnt = 0, done = 0;
@@ -903,14 +905,12 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
             const uint32_t j = S.j[warp][k][o];
             const V val = eval(warp_s0 + o, j, D2 ? S.d2[warp][D2 ? k : 0][o] : 0.0f);
             S.v[warp][e] = val;
-            if constexpr (std::is_same<V, double>::value) {
-                if (store.cap > 0) {
-                    const uint32_t slot = S.base[warp][o] + k;
-                    if (slot < uint32_t(store.cap)) {
-                        const int64_t at = int64_t(slot) * stride + (warp_s0 + o);
-                        store.j[at] = j;
-                        store.k[at] = val;
-                    }
+            if (store.cap > 0) {
+                const uint32_t slot = S.base[warp][o] + k;
+                if (slot < uint32_t(store.cap)) {
+                    const int64_t at = int64_t(slot) * stride + (warp_s0 + o);
+                    store.j[at] = j;
+                    store.k[at] = val;
                 }
             }
         }
@@ -1002,12 +1002,12 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
     return done;
 }
 
-// Phases B-C over stored binary64 lists (the warp's lanes all fit their
-// lists): eval(owner_s, j, K) returns the pair term, add(term) as above.
-template <int NW, int SEG, class Eval, class Add>
+// Phases B-C over stored lists (the warp's lanes all fit their lists):
+// eval(owner_s, j, stored value) returns the pair term, add(term) as above.
+template <int NW, class V, int SEG, class VL, class Eval, class Add>
 __device__ __forceinline__ void dense_listed(bool valid, uint32_t s, int64_t stride,
-                                             uint32_t cnt, const NbList64& nb,
-                                             SegShared<NW, double, false, SEG>& S, Eval&& eval,
+                                             uint32_t cnt, const NbList<VL>& nb,
+                                             SegShared<NW, V, false, SEG>& S, Eval&& eval,
                                              Add&& add) {
     constexpr uint32_t kChunk = SEG * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1243,7 +1243,7 @@ k_adj_rowsum(int n, int64_t stride, const double* __restrict__ pos, const double
              const float4* __restrict__ rec, const uint32_t* __restrict__ cell,
              const uint32_t* __restrict__ start, const double* __restrict__ exp_table,
              const __grid_constant__ View v, double* __restrict__ r_out,
-             double* __restrict__ dr_out) {
+             double* __restrict__ dr_out, NbList<double2> nb) {
     __shared__ double table[kExpTable];
     __shared__ SegShared<kWarpsPerBlock, double2, false, kAdjSeg> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
@@ -1252,7 +1252,7 @@ k_adj_rowsum(int n, int64_t stride, const double* __restrict__ pos, const double
     const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
     const bool valid = s < n && P.transfer;
     double r = 1.0, dr = 0.0;
-    seg_pairs<DIM>(
+    const uint32_t cnt = seg_pairs<DIM>(
         valid, uint32_t(s), stride, rec, pos, cell, start, P, seg,
         [&](uint32_t so, uint32_t j, float) {
             double K, dK;
@@ -1262,10 +1262,11 @@ k_adj_rowsum(int n, int64_t stride, const double* __restrict__ pos, const double
         [&](double2 t) {
             r = __dadd_rn(r, t.x);
             dr = __dadd_rn(dr, t.y);
-        });
+        }, nb);
     if (s < n) {
         r_out[s] = r;
         dr_out[s] = dr;
+        if (nb.cap > 0) nb.count[s] = valid ? cnt : 0u;
     }
 }
 
@@ -1280,7 +1281,7 @@ k_adj_exchange(int n, int64_t stride, const double* __restrict__ pos,
                const double* __restrict__ exp_table, const __grid_constant__ View v,
                const double* __restrict__ r, const double* __restrict__ dr,
                const double* __restrict__ mass, const double* __restrict__ lam,
-               double* __restrict__ lam_out, double* __restrict__ gD) {
+               double* __restrict__ lam_out, double* __restrict__ gD, NbList<double2> nb) {
     __shared__ double table[kExpTable];
     __shared__ SegShared<kWarpsPerBlock, double2, false, kAdjSeg> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
@@ -1289,23 +1290,35 @@ k_adj_exchange(int n, int64_t stride, const double* __restrict__ pos,
     const RealParams& P = v.of_sorted(uint32_t(s < n ? s : 0));
     const bool valid = s < n && P.transfer;
     double lacc = 0.0, gacc = 0.0;
-    seg_pairs<DIM>(
-        valid, uint32_t(s), stride, rec, pos, cell, start, P, seg,
-        [&](uint32_t so, uint32_t j, float) {
-            double K, dK;
-            pair_terms<DIM>(pos, tan, stride, so, j, v.of_sorted(so), table, &K, &dK);
-            const double inv = quot_pos(1.0, __dadd_rn(__ldg(r + so), __ldg(r + j)));
-            const double W = __dmul_rn(__dmul_rn(2.0, K), inv);
-            const double dW = __dmul_rn(
-                __dmul_rn(2.0, inv),
-                __fma_rn(-__dmul_rn(K, inv), __dadd_rn(__ldg(dr + so), __ldg(dr + j)), dK));
-            return make_double2(__dmul_rn(W, __dsub_rn(__ldg(lam + j), __ldg(lam + so))),
-                                __dmul_rn(dW, __dsub_rn(__ldg(mass + j), __ldg(mass + so))));
-        },
-        [&](double2 t) {
-            lacc = __dadd_rn(lacc, t.x);
-            gacc = __dadd_rn(gacc, t.y);
-        });
+    auto terms = [&](uint32_t so, uint32_t j, double K, double dK) {
+        const double inv = quot_pos(1.0, __dadd_rn(__ldg(r + so), __ldg(r + j)));
+        const double W = __dmul_rn(__dmul_rn(2.0, K), inv);
+        const double dW = __dmul_rn(
+            __dmul_rn(2.0, inv),
+            __fma_rn(-__dmul_rn(K, inv), __dadd_rn(__ldg(dr + so), __ldg(dr + j)), dK));
+        return make_double2(__dmul_rn(W, __dsub_rn(__ldg(lam + j), __ldg(lam + so))),
+                            __dmul_rn(dW, __dsub_rn(__ldg(mass + j), __ldg(mass + so))));
+    };
+    auto add = [&](double2 t) {
+        lacc = __dadd_rn(lacc, t.x);
+        gacc = __dadd_rn(gacc, t.y);
+    };
+    const uint32_t listed = (nb.cap > 0 && valid) ? nb.count[s] : 0u;
+    const bool fits = nb.cap > 0 && __all_sync(0xffffffffu, listed <= uint32_t(nb.cap));
+    if (fits) {
+        dense_listed(valid, uint32_t(s), stride, listed, nb, seg,
+                     [&](uint32_t so, uint32_t j, double2 kd) { return terms(so, j, kd.x, kd.y); },
+                     add);
+    } else {
+        seg_pairs<DIM>(
+            valid, uint32_t(s), stride, rec, pos, cell, start, P, seg,
+            [&](uint32_t so, uint32_t j, float) {
+                double K, dK;
+                pair_terms<DIM>(pos, tan, stride, so, j, v.of_sorted(so), table, &K, &dK);
+                return terms(so, j, K, dK);
+            },
+            add);
+    }
     if (s < n) {
         const double ls = lam[s];
         lam_out[s] = valid ? __fma_rn(P.pp.beta, lacc, ls) : ls;

@@ -137,6 +137,9 @@ struct mtpt_handle {
     DevBuf<uint32_t> nb_j, nb_count;      // binary64 form neighbour lists
     DevBuf<double> nb_k;
     int nb_cap = 0;
+    DevBuf<uint32_t> adj_nb_j, adj_nb_count;     // adjoint (K, dK) lists
+    DevBuf<double2> adj_nb_k;
+    int adj_cap = 0;
     DevBuf<double> out_tmp;
     // staging copy of host-loaded input and its check tables
     DevBuf<double> stage, chk_box;
@@ -430,9 +433,10 @@ int setup_grids(mtpt_handle* h) {
         expect = std::max(expect, double(h->reals[k].n) / vol * ball *
                                       std::pow(h->reals[k].psi, double(p.dim)));
     }
-    h->nb_cap = h->precision == MTPT_FP64
-                    ? int(std::min(64.0, std::max(8.0, std::ceil(expect + 4.0 * std::sqrt(expect) + 4.0))))
-                    : 0;
+    const int list_cap =
+        int(std::min(64.0, std::max(8.0, std::ceil(expect + 4.0 * std::sqrt(expect) + 4.0))));
+    h->nb_cap = h->precision == MTPT_FP64 ? list_cap : 0;
+    h->adj_cap = list_cap;
     h->n_cells = cell_base;
     h->n_corners = corner_base;
     h->n_cells_pad = ((h->n_cells + 1 + kScanTile - 1) / kScanTile) * kScanTile;
@@ -1142,12 +1146,14 @@ int launch_adjoint_step(mtpt_handle* h) {
     MTPT_CUDA_TRY(cudaGetLastError());
     MTPT_TRY((launch_gather<DIM, SingleView>(h, c, o, v)));
     k_take_by_id<<<blocks, kBlock, 0, st>>>(n, h->id[o].p, h->lam_in.p, h->lam_s.p);
+    const NbList<double2> adj_nb{h->adj_nb_j.p, h->adj_nb_k.p, h->adj_nb_count.p,
+                                 h->adj_nb_k.p ? h->adj_cap : 0};
     k_adj_rowsum<DIM, SingleView><<<blocks, kBlock, 0, st>>>(
         n, stride, h->pos[o].p, h->tan[o].p, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, v,
-        h->r64.p, h->dr64.p);
+        h->r64.p, h->dr64.p, adj_nb);
     k_adj_exchange<DIM, SingleView><<<blocks, kBlock, 0, st>>>(
         n, stride, h->pos[o].p, h->tan[o].p, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, v,
-        h->r64.p, h->dr64.p, h->mass[o].p, h->lam_s.p, h->lam_new.p, h->gD.p);
+        h->r64.p, h->dr64.p, h->mass[o].p, h->lam_s.p, h->lam_new.p, h->gD.p, adj_nb);
     k_put_by_id<<<blocks, kBlock, 0, st>>>(n, h->id[o].p, h->lam_new.p, h->lam_in.p);
     const int nparts = (n + kReduceThreads - 1) / kReduceThreads;
     k_block_sums<<<nparts, kReduceThreads, 0, st>>>(n, h->gD.p, h->partial.p);
@@ -1184,6 +1190,11 @@ int mtpt_adjoint_forward(mtpt_handle* h, int64_t nsteps, int64_t checkpoint_ever
     for (auto* b : {&h->dr64, &h->lam_in, &h->lam_s, &h->lam_new, &h->gD})
         MTPT_TRY(b->ensure(cap));
     MTPT_TRY(h->r64.ensure(cap));
+    if (h->adj_cap > 0) {
+        MTPT_TRY(h->adj_nb_j.ensure(size_t(h->adj_cap) * cap));
+        MTPT_TRY(h->adj_nb_k.ensure(size_t(h->adj_cap) * cap));
+        MTPT_TRY(h->adj_nb_count.ensure(cap));
+    }
     MTPT_TRY(h->partial.ensure(size_t((n + kReduceThreads - 1) / kReduceThreads + 1)));
     MTPT_TRY(h->acc.ensure(1));
     h->tangent_on = true;
@@ -1296,6 +1307,7 @@ int mtpt_destroy(mtpt_handle* h) {
     h->lam_in.release(); h->lam_s.release(); h->lam_new.release(); h->gD.release();
     h->partial.release(); h->acc.release();
     h->nb_j.release(); h->nb_k.release(); h->nb_count.release();
+    h->adj_nb_j.release(); h->adj_nb_k.release(); h->adj_nb_count.release();
     for (auto& pe : h->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
