@@ -85,6 +85,19 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 }
 
 
+# What bounds each kernel in that same capture (ncu counters; see
+# profiles/step_kernels_gaussian_2d_8M_full.md), reported beside the roofline
+# while the kernel source hash matches.
+BINDING = {
+    "exchange_f32": "instruction issue: 76 % of issue slots at 19 of 32 active lanes; DRAM 12 %",
+    "rowsum_f32": "instruction issue: 81 % of issue slots at 20 of 32 active lanes; DRAM 8 %",
+    "rowsum_f64": "binary64 pipe 86 % busy",
+    "exchange_f64": "binary64 pipe 86 % busy",
+    "gather": "DRAM 53 % (random reads of the source particles)",
+    "walk_key": "binary64 pipe 82 % busy (x + sigma xi)",
+}
+
+
 def _kernel_source_sha1() -> str:
     import hashlib
     path = os.path.join(ROOT, "paper_2204_03756_gb300", "csrc", "kernels.cuh")
@@ -352,6 +365,8 @@ def roofline(w, res, peaks):
     name, (launches, total_ms) = max(kst.items(), key=lambda kv: kv[1][1])
     per_launch_s = total_ms / launches / 1e3
     share = total_ms / sum(v[1] for v in kst.values())
+    current = w.dim == TRAFFIC_DIM and _kernel_source_sha1() == TRAFFIC_SOURCE_SHA1
+    binding = BINDING.get(name) if current else None
     if name in ("rowsum_f64", "exchange_f64"):
         pairs = res["pairs_per_particle_step"] * w.n
         ops = _f64_ops_per_pair(name, w.dim) * pairs
@@ -360,18 +375,17 @@ def roofline(w, res, peaks):
                 "peak": F64_PEAK_OPS / 1e9, "unit": "G binary64 op/s",
                 "frac": achieved / (F64_PEAK_OPS / 1e9), "traffic": None,
                 "algorithmic_ops_per_launch": ops, "launch_ms": per_launch_s * 1e3,
-                "share_of_step": share,
+                "share_of_step": share, "binding_ncu": binding,
                 "peak_source": "derived: 2 binary64 ops/clk/SM x 152 SMs x 2.07 GHz"}
     algo = _algo_bytes_per_particle(name, w.dim, res["form"]) * w.n
     achieved = algo / per_launch_s / 1e9
     traffic = None
-    if (name in TRAFFIC_BYTES_PER_PARTICLE and w.dim == TRAFFIC_DIM
-            and _kernel_source_sha1() == TRAFFIC_SOURCE_SHA1):
+    if name in TRAFFIC_BYTES_PER_PARTICLE and current:
         traffic = TRAFFIC_BYTES_PER_PARTICLE[name] * w.n
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "algorithmic_bytes_per_launch": algo, "launch_ms": per_launch_s * 1e3,
-            "share_of_step": share, "peak_source": peaks["source"]}
+            "share_of_step": share, "binding_ncu": binding, "peak_source": peaks["source"]}
 
 
 def e2e_form(w, pos, mass, form, steps, rank):
