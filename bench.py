@@ -76,12 +76,12 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # so it is scaled to the bench's launch).  Valid only for the kernel source it
 # was measured on: a different hash of kernels.cuh reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "d4bb827008e3"
+TRAFFIC_SOURCE_SHA1 = "174cedcba85a"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (177.799168e6 + 117.391360e6) / 8e6,
-    "gather": (305.955840e6 + 395.250944e6) / 8e6,
-    "rowsum_f32": (177.817600e6 + 24.145152e6) / 8e6,
-    "exchange_f32": (337.833984e6 + 56.066560e6) / 8e6,
+    "walk_key": (177.797376e6 + 117.537792e6) / 8e6,
+    "gather": (305.868288e6 + 395.096064e6) / 8e6,
+    "rowsum_f32": (177.830912e6 + 24.683264e6) / 8e6,
+    "exchange_f32": (337.835264e6 + 56.158720e6) / 8e6,
 }
 
 
@@ -89,8 +89,8 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 # profiles/step_kernels_gaussian_2d_8M_full.md), reported beside the roofline
 # while the kernel source hash matches.
 BINDING = {
-    "exchange_f32": "instruction issue: 76 % of issue slots at 19 of 32 active lanes; DRAM 12 %",
-    "rowsum_f32": "instruction issue: 81 % of issue slots at 20 of 32 active lanes; DRAM 8 %",
+    "exchange_f32": "instruction issue: 83 % of issue slots at 19 of 32 active lanes; DRAM 13 %",
+    "rowsum_f32": "instruction issue: 88 % of issue slots at 20 of 32 active lanes; DRAM 9 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
     "gather": "DRAM 53 % (random reads of the source particles)",
