@@ -186,6 +186,7 @@ typedef struct {
     double D, kappa, dt, beta, lambda;
     double lo[3], hi[3];
     uint64_t seed;
+    double v[3];      /* uniform velocity of the model equation (Sec. 2); 0 in the paper's runs */
 } orc_params;
 
 typedef struct {
@@ -222,7 +223,10 @@ double orc_reflect(double x, double lo, double hi) {
     return x;
 }
 
-/* pos is structure-of-arrays: pos[a * n + i] is axis a of particle i. */
+/* pos is structure-of-arrays: pos[a * n + i] is axis a of particle i.
+ * Each axis moves by sigma xi; with a velocity v (the advection term of the
+ * model equation, Sec. 2, where the paper itself takes v = 0) the move is
+ * v dt + sigma xi, the advective part applied as a plain translation. */
 void orc_random_walk(const orc_params* p, int64_t n, double* pos, const uint32_t* id,
                      uint64_t step) {
     orc_derived dv;
@@ -233,6 +237,7 @@ void orc_random_walk(const orc_params* p, int64_t n, double* pos, const uint32_t
         for (int a = 0; a < p->dim; ++a) {
             double x = pos[a * n + i];
             double disp = dv.sigma * (double)xi[a];
+            if (p->v[a] != 0.0) disp = p->v[a] * p->dt + disp;
             x = x + disp;
             pos[a * n + i] = orc_reflect(x, p->lo[a], p->hi[a]);
         }

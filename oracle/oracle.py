@@ -47,14 +47,16 @@ class _CParams(ctypes.Structure):
                 ("dt", ctypes.c_double), ("beta", ctypes.c_double),
                 ("lam", ctypes.c_double),
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("v", ctypes.c_double * 3)]
 
 
 @dataclass
 class OracleParams:
     """Parameters of Sec. 2-3: dimension, D, kappa = D_RW / D, dt, beta,
     lambda (psi = lambda sqrt(4 D_MT dt / beta)), box [lo, hi] with
-    reflecting walls, and the random-walk seed."""
+    reflecting walls, the random-walk seed, and a uniform velocity v (the
+    advection term of the model equation of Sec. 2; the paper's runs take
+    v = 0)."""
     dim: int = 2
     D: float = 1.0
     kappa: float = 0.5
@@ -64,13 +66,15 @@ class OracleParams:
     lo: tuple = (0.0, 0.0, 0.0)
     hi: tuple = (100.0, 100.0, 100.0)
     seed: int = 0
+    v: tuple = (0.0, 0.0, 0.0)
 
     def c(self) -> _CParams:
         lo = list(self.lo) + [0.0] * (3 - len(self.lo))
         hi = list(self.hi) + [0.0] * (3 - len(self.hi))
+        v = list(self.v) + [0.0] * (3 - len(self.v))
         return _CParams(self.dim, self.D, self.kappa, self.dt, self.beta, self.lam,
                         (ctypes.c_double * 3)(*lo[:3]), (ctypes.c_double * 3)(*hi[:3]),
-                        self.seed)
+                        self.seed, (ctypes.c_double * 3)(*v[:3]))
 
 
 def load():

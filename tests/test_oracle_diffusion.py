@@ -62,3 +62,29 @@ def test_concentration_from_masses():
     # C = N M / L^d; at unit density the concentration is the particle mass
     assert np.allclose(A.concentration([0.5, 1.0], 10_000, 100.0, 2), [0.5, 1.0])
     assert np.allclose(A.concentration([1.0], 1000, 10.0, 3), [1.0])
+
+
+def test_advected_heaviside_front_moves_by_v_t():
+    """Advection-diffusion (model equation of Sec. 2 with a uniform v): the
+    Heaviside front is the erfc profile translated by v t.  Fitting both the
+    shift and D recovers v t and the D that was put in (walls far enough from
+    the front that the depleted and crowded strips near them do not reach
+    it)."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(6)
+    n, Lx, Ly = 20000, 200.0, 10.0                      # density 10
+    pos = np.stack([rng.uniform(0, Lx, n), rng.uniform(0, Ly, n)])
+    m = (pos[0] < 100.0).astype(np.float64)
+    v, steps, dt = 2.0, 100, 0.1                        # t = 10: front 100 -> 120
+    p = O.OracleParams(dim=2, D=1.0, kappa=0.5, dt=dt, lo=(0, 0, 0), hi=(Lx, Ly, 0),
+                       seed=12, v=(v, 0.0, 0.0))
+    pos2, m2, _ = O.run(p, pos, m, steps)
+    t = steps * dt
+    c, mean, counts = A.binned_profile(pos2[0], m2, 0.0, Lx, 100)
+    sel = (c > 100.0) & (c < 140.0)
+    f = lambda q: A.rmse(mean[sel], A.erf_profile(c[sel], t, q[1], 100.0 + q[0], "left"))
+    r = minimize(f, x0=[15.0, 0.8], bounds=[(0.0, 40.0), (0.1, 5.0)], method="L-BFGS-B")
+    shift, D_fit = r.x
+    assert abs(shift - v * t) < 0.6, shift
+    assert 0.85 <= D_fit <= 1.1, D_fit
+    assert f(r.x) < 0.03

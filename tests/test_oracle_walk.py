@@ -66,3 +66,62 @@ def test_walls_are_never_crossed_and_reflection_gives_a_half_normal():
     assert abs(out[0].mean() - sigma * np.sqrt(2.0 / np.pi)) < 5 * sigma / np.sqrt(n)
     z = O.normals(p.seed, np.arange(n), 0)
     assert np.array_equal(out[0], np.abs(sigma * z[:, 0].astype(np.float64)))
+
+
+# --- advection: the velocity term of the model equation (Sec. 2) ---------------
+
+def test_advection_without_random_walk_is_an_exact_translation():
+    """kappa = 0 (no random walk): every step moves every particle by exactly
+    the rounded v dt per axis, so T steps equal T binary64 additions of it."""
+    rng = np.random.default_rng(31)
+    n = 500
+    pos = rng.uniform(300.0, 700.0, size=(2, n))
+    v = (0.75, -1.3)
+    p = O.OracleParams(dim=2, D=1.0, kappa=0.0, dt=0.1, lo=(0, 0, 0), hi=(1000, 1000, 0),
+                       seed=4, v=v + (0.0,))
+    ids = np.arange(n, dtype=np.uint32)
+    x = pos.copy()
+    want = pos.copy()
+    for t in range(25):
+        x = O.random_walk(p, x, ids, t)
+        for a in range(2):
+            want[a] = want[a] + v[a] * 0.1
+    assert np.array_equal(x, want)
+
+
+def test_advection_adds_v_t_to_the_mean_displacement():
+    """With the random walk on, the mean displacement is v t and its variance
+    per axis 2 D_RW t (far from the walls)."""
+    rng = np.random.default_rng(32)
+    n, steps, dt = 20000, 40, 0.1
+    pos = rng.uniform(4000.0, 6000.0, size=(2, n))
+    v = (0.5, -0.25)
+    p = O.OracleParams(dim=2, D=1.0, kappa=1.0, dt=dt, lo=(0, 0, 0), hi=(10000, 10000, 0),
+                       seed=8, v=v + (0.0,))
+    ids = np.arange(n, dtype=np.uint32)
+    x = pos.copy()
+    for t in range(steps):
+        x = O.random_walk(p, x, ids, t)
+    T = steps * dt
+    for a in range(2):
+        d = x[a] - pos[a]
+        assert abs(d.mean() - v[a] * T) < 4 * np.sqrt(2 * T / n), (a, d.mean())
+        assert abs(d.var() - 2 * T) < 0.05 * 2 * T, (a, d.var())
+
+
+def test_advection_into_a_wall_is_mirrored():
+    """A particle carried past a wall by v dt lands on its mirror image, and no
+    particle ever leaves the box."""
+    p = O.OracleParams(dim=1, D=1.0, kappa=0.0, dt=0.5, lo=(0, 0, 0), hi=(10, 0, 0),
+                       seed=1, v=(3.0, 0.0, 0.0))
+    x = np.array([[9.0, 0.5, 5.0]])
+    ids = np.arange(3, dtype=np.uint32)
+    x1 = O.random_walk(p, x, ids, 0)
+    assert np.array_equal(x1[0], [2 * 10.0 - (9.0 + 1.5), 0.5 + 1.5, 5.0 + 1.5])
+    rng = np.random.default_rng(33)
+    y = rng.uniform(0, 10, size=(1, 400))
+    q = O.OracleParams(dim=1, D=2.0, kappa=1.0, dt=0.5, lo=(0, 0, 0), hi=(10, 0, 0),
+                       seed=2, v=(7.0, 0.0, 0.0))
+    for t in range(30):
+        y = O.random_walk(q, y, np.arange(400, dtype=np.uint32), t)
+        assert (y >= 0).all() and (y <= 10).all()
