@@ -38,7 +38,8 @@ FORMS = {"fp64": mtpt.MTPT_FP64, "fp32w": mtpt.MTPT_FP32W}
 DTYPE = {"fp64": "f64", "fp32w": "f32+f64acc"}
 # timed single-run forms: precision form on the --workload workload, or on
 # the 3-d workload for the "_3d" forms
-FORM_WORKLOAD = {"fp32w": None, "fp64": None, "fp32w_3d": "heaviside_3d", "fp64_3d": "heaviside_3d"}
+FORM_WORKLOAD = {"fp32w": None, "fp64": None, "fp32w_3d": "heaviside_3d", "fp64_3d": "heaviside_3d",
+                 "fp32w_adv": "advection_2d", "fp64_adv": "advection_2d"}
 
 
 def _base(form: str) -> str:
@@ -163,7 +164,8 @@ def _dist():
 
 def _params(w, form: str, rank: int) -> mtpt.Params:
     return mtpt.Params(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
-                       lo=w.lo, hi=w.hi, seed=w.seed + rank, precision=FORMS[_base(form)])
+                       lo=w.lo, hi=w.hi, seed=w.seed + rank, precision=FORMS[_base(form)],
+                       v=w.v)
 
 
 def workload_config(w, form: str, world: int) -> dict:
@@ -431,14 +433,15 @@ def _step_errors(p, pos, mass, steps, x_ref, m_ref, npairs):
 def _oracle_params(O, p):
     return O.OracleParams(dim=p.dim, D=p.D, kappa=p.kappa, dt=p.dt, beta=p.beta, lam=p.lam,
                           lo=tuple(p.lo) + (0.0,) * (3 - p.dim),
-                          hi=tuple(p.hi) + (0.0,) * (3 - p.dim), seed=p.seed)
+                          hi=tuple(p.hi) + (0.0,) * (3 - p.dim), seed=p.seed,
+                          v=tuple(p.v)[:3] + (0.0,) * (3 - len(tuple(p.v)[:3])))
 
 
 def cpu_baseline(w, pos, mass, forms, batched=False, adjoint=False):
     """The CPU oracle timed on one core over one full time step of the whole
     workload.  The same leg reports every form's error against the oracle:
-    the 2-d forms on that full step, the 3-d forms on one step of the 3-d
-    workload at 200,000 particles, the batched kernels on two steps of four
+    the forms on that workload on that full step, the forms on other
+    workloads (3-d, advection) on one step of theirs at 200,000 particles, the batched kernels on two steps of four
     ensemble realisations spanning the count range (batched together, each
     compared with its own oracle run), and the adjoint's dL/dM_0 against the
     oracle's reverse sweep on 20,000 particles over 10 steps."""
@@ -452,14 +455,15 @@ def cpu_baseline(w, pos, mass, forms, batched=False, adjoint=False):
         if FORM_WORKLOAD.get(f) is None:
             parity[f] = dict(_step_errors(_params(w, f, 0), pos, mass, 1, x_ref, m_ref, npairs),
                              case=f"{w.name}, n={w.n}, 1 step")
-    forms3 = [f for f in forms if FORM_WORKLOAD.get(f) == "heaviside_3d"]
-    if forms3:
-        w3 = workloads.get("heaviside_3d", 200_000)
-        p3, m3 = workloads.initial_state(w3)
-        x3r, m3r, n3 = O.run(_oracle_params(O, _params(w3, forms3[0], 0)), p3, m3, 1)
-        for f in forms3:
-            parity[f] = dict(_step_errors(_params(w3, f, 0), p3, m3, 1, x3r, m3r, n3),
-                             case=f"heaviside_3d, n={w3.n}, 1 step")
+    others = sorted({FORM_WORKLOAD[f] for f in forms if FORM_WORKLOAD.get(f) is not None})
+    for name in others:
+        fs = [f for f in forms if FORM_WORKLOAD.get(f) == name]
+        wk = workloads.get(name, 200_000)
+        pk, mk = workloads.initial_state(wk)
+        xr, mr, nr = O.run(_oracle_params(O, _params(wk, fs[0], 0)), pk, mk, 1)
+        for f in fs:
+            parity[f] = dict(_step_errors(_params(wk, f, 0), pk, mk, 1, xr, mr, nr),
+                             case=f"{name}, n={wk.n}, 1 step")
     if batched:
         e = workloads.ensemble()
         order = np.argsort(e.counts)
@@ -615,7 +619,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
-    ap.add_argument("--forms", default="fp32w,fp64,fp32w_3d,batched,adjoint",
+    ap.add_argument("--forms", default="fp32w,fp64,fp32w_3d,fp32w_adv,batched,adjoint",
                     help="comma list; the first is the headline value")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")

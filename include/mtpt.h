@@ -94,6 +94,10 @@ typedef struct mtpt_params {
     double lo[3];
     double hi[3];
     uint64_t seed;
+    double v[3];            /* uniform velocity (the advection term of the model
+                             * equation, Sec. 2; the paper's runs take 0): each
+                             * axis moves by v[a] dt + sigma xi before the
+                             * reflection.  Finite, |v[a] dt| <= 1e15. */
 } mtpt_params;
 
 /* Derived quantities and counters of a handle. */

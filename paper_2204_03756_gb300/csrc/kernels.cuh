@@ -98,7 +98,9 @@ struct RealParams {
     uint32_t id_offset;  // first global particle index of the realisation
     uint32_t cell_base;  // first global cell of the realisation
     int32_t transfer;    // 1 when D_MT > 0 (pair passes run)
-    int32_t walk;        // 1 when sigma > 0
+    int32_t walk;        // 1 when sigma > 0 or a velocity component is nonzero
+    double vdt[3];       // v dt per axis (advection)
+    uint32_t advect;     // bit a set when v[a] != 0
     double dsigma_dD;    // d sigma / dD = sigma / (2 D) (adjoint)
     double h2;           // 2 D_MT dt / beta (adjoint)
     double inv_2D;       // 1 / (2 D) (adjoint)
@@ -251,8 +253,11 @@ __device__ __forceinline__ uint32_t cell_of(const double* x, const Grid& g, bool
 
 // With TANGENT, also carries the pathwise derivative of the positions with
 // respect to D (tan, same layout as pos): the walk adds dsigma/dD xi and a
-// mirror flips the sign, exactly as it maps the coordinate.
-template <int DIM, class View, bool TANGENT = false>
+// mirror flips the sign, exactly as it maps the coordinate.  ADVECT compiles
+// the velocity term in (launched when some realisation has v != 0), so the
+// binary64 pipe of a walk without one carries only its two operations per
+// axis.
+template <int DIM, class View, bool TANGENT = false, bool ADVECT = false>
 __global__ void __launch_bounds__(kBlock)
 k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __restrict__ id,
            const unsigned long long* __restrict__ step_dev, int do_walk, int do_key,
@@ -272,7 +277,12 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             const double za = f32_to_f64(z[a]);
-            double xv = __dadd_rn(x[a], __dmul_rn(P.sigma, za));
+            // move sigma xi, or v dt + sigma xi with a velocity on this axis
+            double disp = __dmul_rn(P.sigma, za);
+            if constexpr (ADVECT) {
+                if (P.advect & (1u << a)) disp = __dadd_rn(P.vdt[a], disp);
+            }
+            double xv = __dadd_rn(x[a], disp);
             const long long k = order_key(xv);
             // strictly inside in the integer order => inside in binary64, no
             // mirror needed; anything else (walls, outside, NaN) takes the

@@ -110,7 +110,7 @@ struct mtpt_handle {
     std::vector<RealParams> params_heap;
     RealHost* reals = &real_inline;
     RealParams* params = &params_inline;
-    bool any_transfer = false, any_walk = false;
+    bool any_transfer = false, any_walk = false, any_advect = false;
     double cell_scale = 1.0;          // tuning: cell width = cell_scale x psi (>= 1)
     int pair_block = 256;             // tuning: block size of the binary32 pair passes
     cudaStream_t stream = nullptr;
@@ -249,6 +249,8 @@ int validate_params(const mtpt_params* p) {
         if (!std::isfinite(p->lo[a]) || !std::isfinite(p->hi[a]) || !(p->lo[a] < p->hi[a]))
             return MTPT_ERR_INVALID_ARG;
         if (std::fabs(p->lo[a]) > 1e15 || std::fabs(p->hi[a]) > 1e15) return MTPT_ERR_INVALID_ARG;
+        if (!std::isfinite(p->v[a]) || !(std::fabs(p->v[a] * p->dt) <= 1e15))
+            return MTPT_ERR_INVALID_ARG;
     }
     return MTPT_OK;
 }
@@ -272,7 +274,12 @@ void derive(RealHost& R, RealParams& P) {
     R.psi2 = R.psi * R.psi;
     P.kernel_norm = R.h2 > 0.0 ? std::pow(2.0 * M_PI * R.h2, -0.5 * p.dim) : 0.0;
     P.transfer = R.h2 > 0.0 ? 1 : 0;
-    P.walk = P.sigma > 0.0 ? 1 : 0;
+    P.advect = 0;
+    for (int a = 0; a < 3; ++a) {
+        P.vdt[a] = a < p.dim ? p.v[a] * p.dt : 0.0;
+        if (a < p.dim && p.v[a] != 0.0) P.advect |= 1u << a;
+    }
+    P.walk = (P.sigma > 0.0 || P.advect) ? 1 : 0;
     P.h2 = R.h2;
     P.dsigma_dD = p.D > 0.0 ? P.sigma / (2.0 * p.D) : 0.0;
     P.inv_2D = p.D > 0.0 ? 1.0 / (2.0 * p.D) : 0.0;
@@ -296,7 +303,8 @@ void derive(RealHost& R, RealParams& P) {
 // is small: with u = 2^-24, the binary32 evaluation of (x - lo) / w is within
 // dc = 3 u (B + L) / psi cells of the exact one (B = max(|lo|, |hi|)), so
 // cells of width w >= psi / (1 - 2 dc) keep every pair within psi in adjacent
-// cells.  Boxes where dc > 1e-3 (very many cells per axis) use binary64.
+// cells (at most 2 % wider).  Boxes where dc > 1e-2 (very many cells per
+// axis) use binary64.
 int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, double scale) {
     const mtpt_params& p = R.prm;
     Grid& g = P.g;
@@ -306,7 +314,7 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
         const double B = std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a]));
         dc = std::max(dc, 3.0 * u * (B + (p.hi[a] - p.lo[a])) / R.psi);
     }
-    g.cell_f32 = (P.transfer && dc <= 1e-3) ? 1 : 0;
+    g.cell_f32 = (P.transfer && dc <= 1e-2) ? 1 : 0;
     const double widen = g.cell_f32 ? 1.0 / (1.0 - 2.0 * dc) : 1.0;
     const double psi_eff = R.psi * widen * scale * (1.0 + 1e-9);
     double ncell[3] = {1, 1, 1};
@@ -413,12 +421,14 @@ int setup_grids(mtpt_handle* h) {
     int corner_base = 0;
     h->any_transfer = false;
     h->any_walk = false;
+    h->any_advect = false;
     for (int k = 0; k < h->nreal; ++k) {
         MTPT_TRY(setup_grid(h->reals[k], h->params[k], cell_base, corner_base, h->cell_scale));
         cell_base += h->reals[k].n_cells;
         corner_base += h->reals[k].n_corners;
         h->any_transfer |= h->params[k].transfer != 0;
         h->any_walk |= h->params[k].walk != 0;
+        h->any_advect |= h->params[k].advect != 0;
     }
     if (cell_base > int64_t(0xffffffffLL) - kScanTile) return MTPT_ERR_INVALID_ARG;
     // binary64 neighbour-list slots: the expected neighbour count of the
@@ -637,14 +647,24 @@ int launch_step(mtpt_handle* h, int flags) {
     const View vin = make_view<View>(h, c, c);
     if (walk || transfer) {
         MTPT_TIMED(h, "walk_key");
-        if (h->tangent_on)
-            k_walk_key<DIM, View, true><<<blocks, kBlock, 0, st>>>(
+        if (h->tangent_on) {
+            if (h->any_advect)
+                k_walk_key<DIM, View, true, true><<<blocks, kBlock, 0, st>>>(
+                    n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0,
+                    transfer ? 1 : 0, vin, h->key.p, h->count.p, h->status.p, h->tan[c].p);
+            else
+                k_walk_key<DIM, View, true><<<blocks, kBlock, 0, st>>>(
+                    n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0,
+                    transfer ? 1 : 0, vin, h->key.p, h->count.p, h->status.p, h->tan[c].p);
+        } else if (h->any_advect) {
+            k_walk_key<DIM, View, false, true><<<blocks, kBlock, 0, st>>>(
                 n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0,
-                transfer ? 1 : 0, vin, h->key.p, h->count.p, h->status.p, h->tan[c].p);
-        else
+                transfer ? 1 : 0, vin, h->key.p, h->count.p, h->status.p);
+        } else {
             k_walk_key<DIM, View><<<blocks, kBlock, 0, st>>>(
                 n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, walk ? 1 : 0,
                 transfer ? 1 : 0, vin, h->key.p, h->count.p, h->status.p);
+        }
         MTPT_CUDA_TRY(cudaGetLastError());
     }
     const bool advance = (flags & MTPT_DO_WALK) != 0;
@@ -1133,9 +1153,14 @@ int launch_adjoint_step(mtpt_handle* h) {
     cudaStream_t st = h->stream;
     const int c = h->cur, o = 1 - h->cur;
     const SingleView v = make_view<SingleView>(h, c, c);
-    k_walk_key<DIM, SingleView, true><<<blocks, kBlock, 0, st>>>(
-        n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, h->any_walk ? 1 : 0, 1, v, h->key.p,
-        h->count.p, h->status.p, h->tan[c].p);
+    if (h->any_advect)
+        k_walk_key<DIM, SingleView, true, true><<<blocks, kBlock, 0, st>>>(
+            n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, h->any_walk ? 1 : 0, 1, v,
+            h->key.p, h->count.p, h->status.p, h->tan[c].p);
+    else
+        k_walk_key<DIM, SingleView, true><<<blocks, kBlock, 0, st>>>(
+            n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, h->any_walk ? 1 : 0, 1, v,
+            h->key.p, h->count.p, h->status.p, h->tan[c].p);
     const int ntiles = int(h->n_cells_pad / kScanTile);
     const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
     k_scan_tile_sums<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p);

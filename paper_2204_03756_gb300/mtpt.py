@@ -56,7 +56,7 @@ class _Params(ctypes.Structure):
                 ("dt", ctypes.c_double), ("beta", ctypes.c_double),
                 ("lam", ctypes.c_double),
                 ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("v", ctypes.c_double * 3)]
 
 
 class _KernelStat(ctypes.Structure):
@@ -83,7 +83,8 @@ class _Info(ctypes.Structure):
 class Params:
     """Sec. 2-3 parameters: dimension, D, kappa = D_RW / D, dt, beta, lambda
     (psi = lambda sqrt(4 D_MT dt / beta)), box [lo, hi] with reflecting walls,
-    walk seed and precision form (MTPT_FP64 or MTPT_FP32W)."""
+    walk seed, precision form (MTPT_FP64 or MTPT_FP32W) and a uniform velocity
+    v (advection; 0 in the paper's runs)."""
     dim: int = 2
     D: float = 1.0
     kappa: float = 0.5
@@ -94,13 +95,15 @@ class Params:
     hi: tuple = (1.0, 1.0, 1.0)
     seed: int = 0
     precision: int = MTPT_FP64
+    v: tuple = (0.0, 0.0, 0.0)
 
     def c(self) -> _Params:
         lo = list(self.lo)[:3] + [0.0] * (3 - min(3, len(self.lo)))
         hi = list(self.hi)[:3] + [0.0] * (3 - min(3, len(self.hi)))
+        v = list(self.v)[:3] + [0.0] * (3 - min(3, len(self.v)))
         return _Params(self.dim, self.precision, self.D, self.kappa, self.dt, self.beta,
                        self.lam, (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi),
-                       self.seed)
+                       self.seed, (ctypes.c_double * 3)(*v))
 
 
 _lib = None

@@ -17,6 +17,12 @@ Workloads (sizes and parameters of the paper's test problem family, Sec. 2):
   x < 63 else 0, D = 1, dt = 0.05, 500 steps.
 * ``uniform_mass_2d`` N = 250,000 in [0,500]^2, mass U(0,1), D = 0.5,
   dt = 0.1, 200 steps.
+* ``advection_2d``   N = 4,000,000 in [0,2000]^2 (density 1), mass 1 where
+  x < 500 else 0, D = 1, kappa = 0.5, dt = 0.1, uniform velocity
+  v = (0.1, 0.05) (the advection term of the model equation, Sec. 2), 1,000
+  steps.  The velocity is small so that over the run the particles carried
+  into the downstream walls (where zero-flux reflection piles them up in a
+  thin dense layer) stay a small fraction of the whole.
 
 Every workload takes kappa = 0.5, beta = 1 and lambda = 3 (cutoff
 psi = 3 sqrt(4 D_MT dt)), and may be scaled down (``n`` with the box scaled
@@ -52,6 +58,7 @@ class Workload:
     lam: float = 3.0
     seed: int = SEED_BASE
     mass_param: float = 0.0  # Heaviside split x, or Gaussian sigma
+    v: tuple = (0.0, 0.0, 0.0)  # uniform velocity (advection)
 
     def scaled(self, n: int) -> "Workload":
         """Same density and parameters with ``n`` particles: every box edge
@@ -75,6 +82,9 @@ WORKLOADS = {
                              seed=SEED_BASE + 3, mass_param=63.0),
     "uniform_mass_2d": Workload("uniform_mass_2d", 2, 250_000, (0.0, 0.0), (500.0, 500.0),
                                 0.5, 0.5, 0.1, 200, "uniform01", seed=SEED_BASE + 5),
+    "advection_2d": Workload("advection_2d", 2, 4_000_000, (0.0, 0.0), (2000.0, 2000.0),
+                             1.0, 0.5, 0.1, 1000, "heaviside_left", seed=SEED_BASE + 7,
+                             mass_param=500.0, v=(0.1, 0.05, 0.0)),
 }
 
 

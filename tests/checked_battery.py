@@ -35,6 +35,14 @@ def run() -> dict:
                 out[f"{name}_{fk}_r"] = sim.row_sums()
                 gi, gj = sim.pairs()
                 out[f"{name}_{fk}_pairs"] = np.stack([gi, gj])
+    # advection (uniform velocity), both forms
+    w = workloads.get("advection_2d", 30_000)
+    pos, mass = workloads.initial_state(w)
+    for fk, form in forms.items():
+        with mtpt.Simulation(_params(w, form, v=w.v), pos, mass) as sim:
+            sim.step(4)
+            out[f"advection_{fk}_m"] = sim.masses()
+            out[f"advection_{fk}_x"] = sim.positions()
     # a batch of uneven realisations, both forms
     e = workloads.ensemble(nreal=16)
     members = sorted(e.members, key=lambda m: m.n)[:5]

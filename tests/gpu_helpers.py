@@ -11,7 +11,7 @@ TOL = {mtpt.MTPT_FP64: 1e-12, mtpt.MTPT_FP32W: 1e-5}
 
 def params_of(w, precision=mtpt.MTPT_FP64, **over):
     kw = dict(dim=w.dim, D=w.D, kappa=w.kappa, dt=w.dt, beta=w.beta, lam=w.lam,
-              lo=w.lo, hi=w.hi, seed=w.seed, precision=precision)
+              lo=w.lo, hi=w.hi, seed=w.seed, precision=precision, v=w.v)
     kw.update(over)
     return mtpt.Params(**kw)
 
@@ -19,8 +19,9 @@ def params_of(w, precision=mtpt.MTPT_FP64, **over):
 def oracle_params(p: mtpt.Params) -> O.OracleParams:
     lo = tuple(p.lo) + (0.0,) * (3 - len(p.lo))
     hi = tuple(p.hi) + (0.0,) * (3 - len(p.hi))
+    v = tuple(p.v) + (0.0,) * (3 - len(p.v))
     return O.OracleParams(dim=p.dim, D=p.D, kappa=p.kappa, dt=p.dt, beta=p.beta, lam=p.lam,
-                          lo=lo, hi=hi, seed=p.seed)
+                          lo=lo, hi=hi, seed=p.seed, v=v[:3])
 
 
 def rel_err(got, ref) -> float:

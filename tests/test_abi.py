@@ -45,7 +45,8 @@ def test_parameter_validation_without_gpu(lib):
     bad = [dict(dim=0), dict(dim=4), dict(kappa=1.5), dict(dt=0.0), dict(D=-1.0),
            dict(lo=(5, 0), hi=(1, 10)), dict(beta=0.0), dict(lam=0.0), dict(precision=7),
            dict(D=float("nan")), dict(lam=20.5), dict(lo=(-2e15, 0)),
-           dict(D=1e-33, dt=1e-3)]          # h^2 = 1e-36: below the kernel range
+           dict(D=1e-33, dt=1e-3),          # h^2 = 1e-36: below the kernel range
+           dict(v=(float("nan"), 0.0)), dict(v=(0.0, float("inf"))), dict(v=(1e17, 0.0))]
     for b in bad:
         kw = dict(good)
         kw.update(b)

@@ -127,3 +127,20 @@ def test_tuned_grids_keep_parity_and_autotune_restores_state(form):
         xr5, mr5, _ = O.run(oracle_params(p), pos, mass, 5)
         assert np.array_equal(s.positions(), xr5)
         assert rel_err(s.masses(), mr5) <= TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_with_per_realisation_velocities_equals_single_runs(form):
+    e = workloads.ensemble(nreal=3, n_min=500, n_max=4000, steps=5)
+    vs = [(0.0, 0.0), (1.0, -0.5), (-2.0, 3.0)]
+    params = [params_of(w, precision=form, v=v) for w, v in zip(e.members, vs)]
+    pos, mass = workloads.ensemble_state(e)
+    with mtpt.Batch(params, e.counts, pos, mass) as b:
+        b.step(5)
+        bx, bm = b.split(b.positions()), b.split(b.masses())
+    for k, w in enumerate(e.members):
+        p0, m0 = workloads.initial_state(w)
+        with mtpt.Simulation(params[k], p0, m0) as sim:
+            sim.step(5)
+            assert np.array_equal(sim.positions(), bx[k])
+            assert np.array_equal(sim.masses(), bm[k])

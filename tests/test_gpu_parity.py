@@ -296,8 +296,8 @@ def test_device_buffers_through_torch():
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("case", ["far_f32_cells", "far_f64_cells", "sparse_wide_cells",
-                                  "one_cell_high", "on_cell_corners"])
+@pytest.mark.parametrize("case", ["far_f32_cells", "farther_f32_cells", "far_f64_cells",
+                                  "sparse_wide_cells", "one_cell_high", "on_cell_corners"])
 def test_pair_windows_on_adversarial_boxes(form, case):
     """The per-row candidate windows rest on a slack derived from the
     binary32 cell-index and offset error bounds: boxes far from the origin
@@ -306,11 +306,13 @@ def test_pair_windows_on_adversarial_boxes(form, case):
     corners must all keep the exact pair set -- in the emitted pairs and in
     the pair counts of both pair passes."""
     cases = ["far_f32_cells", "far_f64_cells", "sparse_wide_cells", "one_cell_high",
-             "on_cell_corners"]
+             "on_cell_corners", "farther_f32_cells"]
     rng = np.random.default_rng(11 + cases.index(case))
     n = 2500
     if case == "far_f32_cells":
         lo = np.array([4800.0, -5000.0]); L = np.array([45.0, 38.0])
+    elif case == "farther_f32_cells":             # binary32 cell error ~5e-3 cells
+        lo = np.array([48000.0, -50000.0]); L = np.array([45.0, 38.0])
     elif case == "far_f64_cells":
         lo = np.array([2.0e6, -3.5e6]); L = np.array([45.0, 38.0])
     elif case == "sparse_wide_cells":              # cells ~14 psi wide (count capped)
@@ -341,3 +343,45 @@ def test_pair_windows_on_adversarial_boxes(form, case):
     with mtpt.Simulation(p, pos, rng.uniform(0, 1, n)) as sim:
         sim.step(1)                                    # kappa = 0: transfer only
         assert sim.info()["pair_count"] == len(bi)
+
+
+# --- advection (the velocity term of the model equation, Sec. 2) ------------------
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_advected_walk_is_bit_exact_with_reflections(dim):
+    """v dt + sigma xi per axis before the reflection, as in the oracle; a
+    small box and a large velocity force repeated mirrors at the walls, and an
+    axis with v = 0 keeps the plain walk."""
+    rng = np.random.default_rng(40 + dim)
+    n = 3001
+    L = 6.0
+    pos = rng.uniform(0, L, size=(dim, n))
+    v = (2.5, 0.0, -4.0)[:dim]
+    for form in FORMS:
+        p = mtpt.Params(dim=dim, D=1.0, kappa=0.5, dt=0.2, lo=(0.0,) * dim, hi=(L,) * dim,
+                        seed=23, precision=form, v=v)
+        g, r = run_both(p, pos, rng.uniform(0, 1, n), 6)
+        assert np.array_equal(g["pos"], r["pos"])
+        assert g["info"]["pair_count"] == r["pairs"]
+        assert rel_err(g["mass"], r["mass"]) <= TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_advection_workload_scaled_matches_the_oracle(form):
+    w = workloads.get("advection_2d", 40_000)
+    pos, mass = workloads.initial_state(w)
+    g, r = run_both(params_of(w, precision=form), pos, mass, 10)
+    assert np.array_equal(g["pos"], r["pos"])
+    assert g["info"]["pair_count"] == r["pairs"]
+    assert rel_err(g["mass"], r["mass"]) <= TOL[form]
+
+
+def test_walk_without_random_walk_still_advects():
+    """kappa = 0 switches the random walk off but not the advection."""
+    rng = np.random.default_rng(44)
+    pos = rng.uniform(100, 200, size=(2, 2000))
+    p = mtpt.Params(dim=2, D=1.0, kappa=0.0, dt=0.1, lo=(0, 0), hi=(300, 300), seed=3,
+                    v=(1.5, -0.5))
+    g, r = run_both(p, pos, rng.uniform(0, 1, 2000), 4)
+    assert np.array_equal(g["pos"], r["pos"])
+    assert not np.array_equal(g["pos"], pos)
