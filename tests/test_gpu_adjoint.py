@@ -25,10 +25,10 @@ def _built():
 NB = (8, 8)
 
 
-def _case(n=2000, steps=20, precision=mtpt.MTPT_FP64):
+def _case(n=2000, steps=20, precision=mtpt.MTPT_FP64, v=(0.0, 0.0)):
     w = workloads.get("uniform_mass_2d", n)
     pos, mass = workloads.initial_state(w)
-    p = params_of(w, precision=precision)
+    p = params_of(w, precision=precision, v=v)
     target = workloads.target_field(NB, w.lo, w.hi)
     return w, p, pos, mass, target, steps
 
@@ -58,9 +58,12 @@ def _oracle_forward(op, pos, mass, steps):
     return xs, x, m, pairs
 
 
-def test_mass_gradient_matches_the_oracle_reverse_sweep_and_D_gradient_matches_fd():
+@pytest.mark.parametrize("v", [(0.0, 0.0), (0.8, -0.3)])
+def test_mass_gradient_matches_the_oracle_reverse_sweep_and_D_gradient_matches_fd(v):
+    """Also with a velocity: advection moves the path (and so the operator
+    A_t) but not the tangents dX/dD."""
     import torch
-    w, p, pos, mass, target, steps = _case()
+    w, p, pos, mass, target, steps = _case(v=v)
     op = oracle_params(p)
     xs, xT, mT, _ = _oracle_forward(op, pos, mass, steps)
     L, g, _ = _loss_and_grad(w, xT, mT, target)
