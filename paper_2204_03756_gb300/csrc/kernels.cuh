@@ -338,13 +338,22 @@ k_check_input(int n, int64_t stride, int nreal, const double* __restrict__ pos,
             k = lo;
         }
         const double* b = box + 6 * k;
+        // integer tests only (the binary64 unit is slow): x inside [lo, hi]
+        // through the order keys (a NaN fails the finiteness test), |m| <=
+        // mass_limit through the magnitude bits (ordered like the values)
+        // (-0 and +0 compare equal, so both map to key 0)
+        auto key0 = [](double v) {
+            return (__double_as_longlong(v) & 0x7fffffffffffffffLL) == 0 ? 0LL : order_key(v);
+        };
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             const double x = pos[int64_t(a) * stride + i];
-            if (!(x >= b[a] && x <= b[3 + a])) bad |= 1u;
+            const long long kx = key0(x);
+            if (not_finite(x) || kx < key0(b[a]) || kx > key0(b[3 + a])) bad |= 1u;
         }
         const double m = mass[i];
-        if (not_finite(m) || !(fabs(m) <= mass_limit)) bad |= 2u;
+        const long long mag = __double_as_longlong(m) & 0x7fffffffffffffffLL;
+        if (not_finite(m) || mag > __double_as_longlong(mass_limit)) bad |= 2u;
         if (id_out) id_out[i] = uint32_t(i);
     }
     const uint32_t any = __reduce_or_sync(0xffffffffu, bad);

@@ -41,8 +41,8 @@ def test_rejected_host_loads_keep_the_old_state(form):
             assert np.array_equal(sim.positions(), x0)
             assert np.array_equal(sim.masses(), m0)
             assert sim.info()["step"] == info0["step"]
-        # the walls themselves are inside
-        p = pos.copy(); p[0, 0] = w.lo[0]; p[1, 1] = w.hi[1]
+        # the walls themselves are inside, -0 as well as +0 at a wall at 0
+        p = pos.copy(); p[0, 0] = w.lo[0]; p[1, 1] = w.hi[1]; p[0, 2] = -0.0; p[1, 3] = 0.0
         mtpt.mtpt_set_particles(sim.h, 2, p, mass)
         assert sim.info()["step"] == 0
         assert np.array_equal(sim.positions(), p)
