@@ -390,9 +390,14 @@ def roofline(w, res, peaks):
             "share_of_step": share, "binding_ncu": binding, "peak_source": peaks["source"]}
 
 
-def e2e_form(w, pos, mass, form, steps, rank):
-    """Through the C ABI with HOST buffers: each step uploads the state from
-    pinned host memory, advances one time step and reads the masses back."""
+def e2e_form(w, pos, mass, form, steps, rank, world=1, dist=None):
+    """Through the C ABI with HOST buffers: every step uploads the state from
+    pinned host memory, advances one time step and reads the masses back into
+    pinned host memory.  `value` uses the pipelined calls
+    (mtpt_set_particles_async / mtpt_get_masses_async: the copies of one step
+    overlap the device work of another; one mtpt_sync after the last step);
+    `sync_calls` the synchronous mtpt_set_particles / mtpt_get_masses, which
+    wait for each copy."""
     import torch
     p = _params(w, form, rank)
     pin_pos = torch.from_numpy(np.ascontiguousarray(pos)).pin_memory()
@@ -400,25 +405,49 @@ def e2e_form(w, pos, mass, form, steps, rank):
     out = torch.empty(w.n, dtype=torch.float64).pin_memory()
     h = mtpt.mtpt_create(p)
     lib = mtpt.load()
-    try:
-        def one():
+
+    def pipelined(k):
+        for _ in range(k):
+            rc = lib.mtpt_set_particles_async(h, w.n, pin_pos.data_ptr(), pin_mass.data_ptr())
+            rc = rc or lib.mtpt_step(h, 1)
+            rc = rc or lib.mtpt_get_masses_async(h, out.data_ptr())
+            if rc:
+                raise mtpt.MtptError(rc, "e2e pipelined step")
+        rc = lib.mtpt_sync(h)
+        if rc:
+            raise mtpt.MtptError(rc, "e2e sync")
+
+    def synchronous(k):
+        for _ in range(k):
             rc = lib.mtpt_set_particles(h, w.n, pin_pos.data_ptr(), pin_mass.data_ptr())
             rc = rc or lib.mtpt_step(h, 1)
             rc = rc or lib.mtpt_get_masses(h, out.data_ptr())
             if rc:
                 raise mtpt.MtptError(rc, "e2e step")
-        one()
+
+    def timed(fn):
+        fn(3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(steps):
-            one()
+        fn(steps)
         torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
+        return time.perf_counter() - t0
+
+    try:
+        synchronous(1)
+        sec_sync = timed(synchronous)
+        sec = timed(pipelined)
     finally:
         mtpt.mtpt_destroy(h)
-    return {"value": w.n * steps / sec, "unit": "particle-steps/s",
-            "h2d_bytes_per_step": int(pos.nbytes + mass.nbytes),
-            "d2h_bytes_per_step": int(w.n * 8), "steps": steps}
+    # whole job: every rank's particles over the slowest rank's time
+    ms, _ = reduce_over_ranks(sec * 1e3, 0.0, dist)
+    ms_sync, _ = reduce_over_ranks(sec_sync * 1e3, 0.0, dist)
+    return {"value": job_throughput(w.n, steps, world, ms), "unit": "particle-steps/s",
+            "h2d_bytes_per_step": int(pos.nbytes + mass.nbytes) * world,
+            "d2h_bytes_per_step": int(w.n * 8) * world, "steps": steps,
+            "ms_per_step": ms / steps, "api": "pipelined",
+            "sync_calls": {"value": job_throughput(w.n, steps, world, ms_sync),
+                           "ms_per_step": ms_sync / steps}}
 
 
 def _step_errors(p, pos, mass, steps, x_ref, m_ref, npairs):
@@ -621,7 +650,7 @@ def main():
     ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--forms", default="fp32w,fp64,fp32w_3d,fp32w_adv,batched,adjoint",
                     help="comma list; the first is the headline value")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--n", type=int, default=None,
@@ -696,7 +725,7 @@ def main():
             dist.destroy_process_group()
         return 0
     head = results[forms[0]]
-    e2e = e2e_form(w, pos, mass, forms[0], args.e2e_steps, rank)
+    e2e = e2e_form(w, pos, mass, forms[0], args.e2e_steps, rank, world, dist)
     line = {
         "metric": "particle-steps/s", "value": head["particle_steps_per_s"],
         "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,

@@ -28,7 +28,8 @@
  *     that read host buffers return once the buffers are no longer read (the
  *     rest of their work may still be queued); calls that write host buffers
  *     synchronise the stream before returning; *_device calls only enqueue
- *     work.
+ *     work.  The two *_async calls are the exception: they only enqueue
+ *     copies, and their host buffers belong to the copy until mtpt_sync.
  *   - Device errors found inside kernels (non-finite positions) are latched
  *     in a device status word and reported by the next synchronising call.
  *   - Threads: a handle is not safe for concurrent calls; use one thread per
@@ -228,8 +229,40 @@ int mtpt_get_info(mtpt_handle* h, mtpt_info* out);
  * uninterrupted run bit for bit). */
 int mtpt_set_step(mtpt_handle* h, uint64_t step);
 
-/* Wait for the handle's stream and report any latched device error. */
+/* Wait for the handle's stream (and the copy streams of the *_async calls)
+ * and report any latched device error. */
 int mtpt_sync(mtpt_handle* h);
+
+/* Pipelined host I/O.  A loop that feeds every step from host memory and
+ * reads every result back,
+ *     repeat: mtpt_set_particles_async; mtpt_step(h, 1); mtpt_get_masses_async
+ *     then:   mtpt_sync,
+ * overlaps the host-to-device copy of one step's input and the device-to-host
+ * copy of another step's masses with the device work of a third.  The copies
+ * run on two streams the handle creates for them, ordered against the
+ * handle's stream by events, through two device staging slots each way
+ * ((dim + 1) n and n float64 per slot, kept by the handle).  Both calls
+ * return once the work is enqueued: the host buffers must stay allocated and
+ * unchanged (pos, mass) or unread (out) until mtpt_sync returns.  Overlap
+ * needs page-locked host memory; pageable memory gives the same results with
+ * the copies serialised by the driver. */
+
+/* Enqueue a load of n particles from HOST buffers laid out as for
+ * mtpt_set_particles.  n must equal the handle's current particle count
+ * (MTPT_ERR_INVALID_ARG otherwise, also for a handle of more than one
+ * realisation; MTPT_ERR_STATE before the first load).  The device checks the
+ * copy as mtpt_set_particles does and, if it passes, makes it the state that
+ * the next step queued on the handle's stream advances (ids 0..n-1, step
+ * counter 0).  A rejected load leaves the previous state and step counter in
+ * place and is reported once, by the next synchronising call (mtpt_sync or
+ * any other call that syncs): MTPT_ERR_OUT_OF_DOMAIN for a position,
+ * MTPT_ERR_INVALID_ARG for a mass. */
+int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const double* mass);
+
+/* Enqueue a copy of the masses, in input order, into a HOST buffer of n
+ * doubles: the masses as they stand after the work queued on the handle so
+ * far.  The values are in `out` once mtpt_sync returns. */
+int mtpt_get_masses_async(mtpt_handle* h, double* out);
 
 /* Per-kernel timing (tracing).  While enabled, every kernel the handle
  * launches is bracketed by two CUDA events on the handle's stream; the

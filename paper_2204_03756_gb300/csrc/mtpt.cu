@@ -8,7 +8,8 @@
 // realisation its own block of cells in one global cell list, so every phase
 // is one launch over all particles of all realisations.  Multi-step calls
 // replay a captured CUDA graph of two steps.  No step goes through the host:
-// the only host<->device traffic is in mtpt_set_particles* / mtpt_get_*.
+// the only host<->device traffic is in mtpt_set_particles* / mtpt_get_*
+// (the *_async pair copies on two streams of its own, ordered by events).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +23,7 @@
 
 #include "../../include/mtpt.h"
 #include "kernels.cuh"
+#include "hostio.cuh"
 
 using namespace mtpt;
 
@@ -29,6 +31,7 @@ namespace {
 
 constexpr int kMaxDim = 3;
 constexpr int64_t kGraphMinSteps = 4;   // multi-step calls from this size replay a graph
+constexpr int kSettleBlocks = 152;      // grid-stride blocks of k_load_settle (one per SM)
 
 #define MTPT_CUDA_TRY(expr)                                   \
     do {                                                      \
@@ -145,6 +148,14 @@ struct mtpt_handle {
     DevBuf<double> stage, chk_box;
     DevBuf<uint32_t> chk_first, chk_flag;
     DevBuf<double> exp_table;
+    // pipelined host I/O: two staging slots each way, per-slot check flags,
+    // copy streams and the events that order them against `stream`
+    DevBuf<double> in_slot[2], out_slot[2];
+    DevBuf<uint32_t> in_flag;
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
+    cudaEvent_t out_ready[2] = {nullptr, nullptr}, out_free[2] = {nullptr, nullptr};
+    int in_next = 0, out_next = 0;
     DevBuf<uint32_t> status;
     DevBuf<unsigned long long> pair_counter, step_dev;
     DevBuf<unsigned long long> emit_counter;
@@ -160,9 +171,12 @@ struct mtpt_handle {
     uint64_t adj_step0 = 0;
     bool adj_ready = false;
     DevBuf<double> dr64, lam_in, lam_s, lam_new, gD, partial, acc;
-    // captured two-step graph (valid for `graph_cur`, `graph_flags`)
+    // captured two-step graph (valid for `graph_cur`, `graph_flags` and the
+    // mass buffer pair as it was: every step swaps the pair, so between loads
+    // its order follows `cur`, but a pipelined load moves `cur` alone)
     cudaGraphExec_t graph = nullptr;
     int graph_cur = -1, graph_flags = -1;
+    const double* graph_mass0 = nullptr;
     cudaStream_t capture_stream = nullptr;
     // per-kernel timing
     bool timing = false;
@@ -229,6 +243,7 @@ void drop_graph(mtpt_handle* h) {
     h->graph = nullptr;
     h->graph_cur = -1;
     h->graph_flags = -1;
+    h->graph_mass0 = nullptr;
 }
 
 int validate_params(const mtpt_params* p) {
@@ -551,12 +566,30 @@ int upload_tables(mtpt_handle* h) {
     return MTPT_OK;
 }
 
+// Status code of a status word read after the stream drained.  A rejected
+// pipelined load is reported once: its bits are cleared here.  It kept the old
+// step counter on the device, so the host mirror (reset when the load was
+// enqueued) is read back.
+int status_code(mtpt_handle* h, uint32_t st) {
+    const uint32_t load_bits = st & (kStatusLoadPosition | kStatusLoadMass);
+    if (load_bits) {
+        const uint32_t rest = st & ~load_bits;
+        MTPT_CUDA_TRY(cudaMemcpy(h->status.p, &rest, sizeof(rest), cudaMemcpyHostToDevice));
+        unsigned long long step = 0;
+        MTPT_CUDA_TRY(cudaMemcpy(&step, h->step_dev.p, sizeof(step), cudaMemcpyDeviceToHost));
+        h->step = uint64_t(step);
+    }
+    if (st & (kStatusNonFinite | kStatusOutOfDomain | kStatusLoadPosition))
+        return MTPT_ERR_OUT_OF_DOMAIN;
+    if (st & kStatusLoadMass) return MTPT_ERR_INVALID_ARG;
+    return MTPT_OK;
+}
+
 int read_status(mtpt_handle* h) {
     uint32_t st = 0;
     MTPT_CUDA_TRY(cudaMemcpyAsync(&st, h->status.p, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
     MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (st & (kStatusNonFinite | kStatusOutOfDomain)) return MTPT_ERR_OUT_OF_DOMAIN;
-    return MTPT_OK;
+    return status_code(h, st);
 }
 
 template <class View>
@@ -781,6 +814,7 @@ int capture_two_steps(mtpt_handle* h, int flags) {
     h->graph = exec;
     h->graph_cur = cur0;
     h->graph_flags = flags;
+    h->graph_mass0 = h->mass[0].p;
     return MTPT_OK;
 }
 
@@ -788,7 +822,8 @@ int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {
     const bool use_graph = nsteps >= kGraphMinSteps && !h->timing && !h->tangent_on && h->n > 0;
     int64_t done = 0;
     if (use_graph) {
-        if (!h->graph || h->graph_cur != h->cur || h->graph_flags != flags)
+        if (!h->graph || h->graph_cur != h->cur || h->graph_flags != flags ||
+            h->graph_mass0 != h->mass[0].p)
             MTPT_TRY(capture_two_steps(h, flags));
         for (; done + 2 <= nsteps; done += 2) MTPT_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
         // an even number of steps leaves the buffers where they started; a
@@ -821,8 +856,7 @@ int copy_out_host(mtpt_handle* h, int naxes, double* out) {
     uint32_t st = 0;
     MTPT_CUDA_TRY(cudaMemcpyAsync(&st, h->status.p, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
     MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (st & (kStatusNonFinite | kStatusOutOfDomain)) return MTPT_ERR_OUT_OF_DOMAIN;
-    return MTPT_OK;
+    return status_code(h, st);
 }
 
 int set_step_dev(mtpt_handle* h, uint64_t step) {
@@ -982,6 +1016,92 @@ int stage_host_particles(mtpt_handle* h, const int64_t* counts, const double* po
     *pos_dev = sp;
     *mass_dev = sm;
     if (direct) *in_place = f;
+    return MTPT_OK;
+}
+
+// Streams, events and staging slots of the pipelined host I/O, made on first
+// use and grown with n.  Growing a slot waits for every copy in flight first
+// (a copy may still read or write the old allocation).
+int ensure_async(mtpt_handle* h) {
+    if (!h->h2d) MTPT_CUDA_TRY(cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
+    if (!h->d2h) MTPT_CUDA_TRY(cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
+    for (int s = 0; s < 2; ++s) {
+        cudaEvent_t* evs[4] = {&h->in_ready[s], &h->in_free[s], &h->out_ready[s], &h->out_free[s]};
+        for (cudaEvent_t* e : evs)
+            if (!*e) MTPT_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    const size_t n = size_t(std::max<int64_t>(h->n, 1));
+    const size_t in_need = size_t(h->dim + 1) * n;
+    if (h->in_slot[0].count < in_need || h->in_slot[1].count < in_need ||
+        h->out_slot[0].count < n || h->out_slot[1].count < n) {
+        MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        MTPT_CUDA_TRY(cudaStreamSynchronize(h->h2d));
+        MTPT_CUDA_TRY(cudaStreamSynchronize(h->d2h));
+        for (int s = 0; s < 2; ++s) {
+            MTPT_TRY(h->in_slot[s].ensure(in_need));
+            MTPT_TRY(h->out_slot[s].ensure(n));
+        }
+    }
+    MTPT_TRY(h->in_flag.ensure(2));
+    if (!h->chk_box.p) {
+        double box[6] = {0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < h->dim; ++a) {
+            box[a] = h->reals[0].prm.lo[a];
+            box[3 + a] = h->reals[0].prm.hi[a];
+        }
+        MTPT_TRY(h->chk_box.ensure(6));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(h->chk_box.p, box, sizeof(box), cudaMemcpyHostToDevice,
+                                      h->stream));
+        MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));   // `box` is a local
+    }
+    return MTPT_OK;
+}
+
+void release_async(mtpt_handle* h) {
+    if (h->h2d) cudaStreamSynchronize(h->h2d);
+    if (h->d2h) cudaStreamSynchronize(h->d2h);
+    for (int s = 0; s < 2; ++s) {
+        cudaEvent_t* evs[4] = {&h->in_ready[s], &h->in_free[s], &h->out_ready[s], &h->out_free[s]};
+        for (cudaEvent_t* e : evs) {
+            if (*e) cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+        h->in_slot[s].release();
+        h->out_slot[s].release();
+    }
+    h->in_flag.release();
+    if (h->h2d) cudaStreamDestroy(h->h2d);
+    if (h->d2h) cudaStreamDestroy(h->d2h);
+    h->h2d = h->d2h = nullptr;
+}
+
+template <int DIM>
+int launch_load_async(mtpt_handle* h, int slot, int f) {
+    const int n = int(h->n);
+    const int c = h->cur;
+    const double mass_limit = h->precision == MTPT_FP32W ? 1e30 : HUGE_VAL;
+    uint32_t* flag = h->in_flag.p + slot;
+    MTPT_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(uint32_t), h->stream));
+    {
+        MTPT_TIMED(h, "load_input");
+        k_load_input<DIM><<<grid_for(n), kBlock, 0, h->stream>>>(
+            n, h->in_slot[slot].p, h->chk_box.p, mass_limit, flag, h->cap, h->pos[f].p,
+            h->mass[f].p, h->id[f].p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        MTPT_TIMED(h, "load_settle");
+        k_load_settle<DIM><<<std::min(grid_for(n), kSettleBlocks), kBlock, 0, h->stream>>>(
+            n, h->cap, flag, h->pos[c].p, h->mass[c].p, h->id[c].p, h->pos[f].p, h->mass[f].p,
+            h->id[f].p, h->status.p, h->step_dev.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    if (h->batch) {
+        // one realisation: every rid is 0, whichever state the settle kept
+        k_fill_rid<<<grid_for(n), kBlock, 0, h->stream>>>(n, h->nreal, h->id_first.p,
+                                                         h->rid[f].p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
     return MTPT_OK;
 }
 
@@ -1312,6 +1432,7 @@ int mtpt_create_batch(const mtpt_params* params, int32_t count, mtpt_handle** ou
 int mtpt_destroy(mtpt_handle* h) {
     if (!h) return MTPT_OK;
     cudaStreamSynchronize(h->stream);
+    release_async(h);
     drop_graph(h);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (int b = 0; b < 2; ++b) {
@@ -1413,6 +1534,57 @@ int mtpt_get_masses(mtpt_handle* h, double* out) {
     return copy_out_host(h, 1, out);
 }
 
+int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const double* mass) {
+    if (!h || h->nreal != 1) return MTPT_ERR_INVALID_ARG;
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    if (n != h->n || (n > 0 && (!pos || !mass))) return MTPT_ERR_INVALID_ARG;
+    if (n == 0) return MTPT_OK;
+    MTPT_TRY(ensure_async(h));
+    const int slot = h->in_next;
+    const int d = h->dim;
+    double* dst = h->in_slot[slot].p;
+    // the slot is free once the load that used it last has been checked
+    MTPT_CUDA_TRY(cudaStreamWaitEvent(h->h2d, h->in_free[slot], 0));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(dst, pos, size_t(d) * size_t(n) * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->h2d));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(dst + size_t(d) * size_t(n), mass, size_t(n) * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->h2d));
+    MTPT_CUDA_TRY(cudaEventRecord(h->in_ready[slot], h->h2d));
+    MTPT_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->in_ready[slot], 0));
+    const int f = 1 - h->cur;
+    switch (d) {
+        case 1: MTPT_TRY(launch_load_async<1>(h, slot, f)); break;
+        case 2: MTPT_TRY(launch_load_async<2>(h, slot, f)); break;
+        default: MTPT_TRY(launch_load_async<3>(h, slot, f)); break;
+    }
+    MTPT_CUDA_TRY(cudaEventRecord(h->in_free[slot], h->stream));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->pair_counter.p, 0, sizeof(unsigned long long), h->stream));
+    h->in_next = 1 - slot;
+    h->cur = f;
+    h->step = 0;
+    h->have_row_sums = false;
+    h->adj_ready = false;
+    return MTPT_OK;
+}
+
+int mtpt_get_masses_async(mtpt_handle* h, double* out) {
+    if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    if (h->n == 0) return MTPT_OK;
+    MTPT_TRY(ensure_async(h));
+    const int slot = h->out_next;
+    // the slot is free once the copy that read it last has finished
+    MTPT_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->out_free[slot], 0));
+    MTPT_TRY(unpermute_to(h, h->mass[h->cur].p, 1, h->out_slot[slot].p));
+    MTPT_CUDA_TRY(cudaEventRecord(h->out_ready[slot], h->stream));
+    MTPT_CUDA_TRY(cudaStreamWaitEvent(h->d2h, h->out_ready[slot], 0));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(out, h->out_slot[slot].p, size_t(h->n) * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->d2h));
+    MTPT_CUDA_TRY(cudaEventRecord(h->out_free[slot], h->d2h));
+    h->out_next = 1 - slot;
+    return MTPT_OK;
+}
+
 int mtpt_get_positions_device(mtpt_handle* h, double* out_dev) {
     if (!h || (!out_dev && h->n > 0)) return MTPT_ERR_INVALID_ARG;
     if (!h->have_particles) return MTPT_ERR_STATE;
@@ -1506,6 +1678,8 @@ int mtpt_set_step(mtpt_handle* h, uint64_t step) {
 int mtpt_sync(mtpt_handle* h) {
     if (!h) return MTPT_ERR_INVALID_ARG;
     MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->h2d) MTPT_CUDA_TRY(cudaStreamSynchronize(h->h2d));
+    if (h->d2h) MTPT_CUDA_TRY(cudaStreamSynchronize(h->d2h));
     return h->status.p ? read_status(h) : MTPT_OK;
 }
 

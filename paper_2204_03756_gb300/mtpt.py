@@ -41,6 +41,7 @@ EXPORTED = [
     "mtpt_create_batch", "mtpt_set_particles_batch", "mtpt_get_realisation_info",
     "mtpt_set_tuning", "mtpt_get_tuning", "mtpt_autotune", "mtpt_adjoint_forward",
     "mtpt_adjoint_backward", "mtpt_status_string", "mtpt_check_word",
+    "mtpt_set_particles_async", "mtpt_get_masses_async",
 ]
 
 
@@ -134,6 +135,8 @@ def load():
     lib.mtpt_set_stream.argtypes = [vp, vp]
     lib.mtpt_set_particles.argtypes = [vp, ctypes.c_int64, vp, vp]
     lib.mtpt_set_particles_device.argtypes = [vp, ctypes.c_int64, vp, vp]
+    lib.mtpt_set_particles_async.argtypes = [vp, ctypes.c_int64, vp, vp]
+    lib.mtpt_get_masses_async.argtypes = [vp, vp]
     lib.mtpt_step.argtypes = [vp, ctypes.c_int64]
     lib.mtpt_step_ex.argtypes = [vp, ctypes.c_int64, ctypes.c_int32]
     for name in ("mtpt_get_masses", "mtpt_get_masses_device", "mtpt_get_positions",
@@ -277,7 +280,10 @@ def mtpt_adjoint_backward(h, gmass, gmass0) -> float:
 
 
 def mtpt_destroy(h) -> None:
-    _check(load().mtpt_destroy(h), "mtpt_destroy")
+    try:
+        _check(load().mtpt_destroy(h), "mtpt_destroy")
+    finally:
+        _ASYNC_HOLD.pop(_handle_key(h), None)
 
 
 def mtpt_set_stream(h, stream: int | None) -> None:
@@ -361,7 +367,57 @@ def mtpt_set_step(h, step: int) -> None:
 
 
 def mtpt_sync(h) -> None:
-    _check(load().mtpt_sync(h), "mtpt_sync")
+    try:
+        _check(load().mtpt_sync(h), "mtpt_sync")
+    finally:
+        _ASYNC_HOLD.pop(_handle_key(h), None)
+
+
+# Host arrays handed to the *_async calls stay referenced here until the
+# handle's next mtpt_sync (or mtpt_destroy), so the copies never read or
+# write freed memory.
+_ASYNC_HOLD: dict = {}
+
+
+def _handle_key(h) -> int:
+    return int(ctypes.cast(h, ctypes.c_void_p).value or 0)
+
+
+def _host_in_place(a, numel: int, what: str) -> int:
+    """Address of a float64, C-contiguous host array of `numel` elements (numpy
+    or CPU torch tensor), used in place: a converted copy would be a
+    temporary that the pending copy outlives."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != numel:
+                raise ValueError(f"{what}: expected a contiguous float64 CPU tensor of {numel}")
+            return a.data_ptr()
+    except ImportError:
+        pass
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+            and a.size == numel):
+        raise ValueError(f"{what}: expected a C-contiguous float64 array of {numel}")
+    return a.ctypes.data
+
+
+def mtpt_set_particles_async(h, dim: int, pos, mass) -> None:
+    """Enqueue a host load (include/mtpt.h); pos (dim x n) and mass (n) are
+    read in place until mtpt_sync: pinned torch tensors give the overlap."""
+    n = mass.numel() if hasattr(mass, "numel") else np.asarray(mass).size
+    pp = _host_in_place(pos, dim * n, "pos")
+    pm = _host_in_place(mass, n, "mass")
+    _check(load().mtpt_set_particles_async(h, n, pp, pm), "mtpt_set_particles_async")
+    _ASYNC_HOLD.setdefault(_handle_key(h), []).extend((pos, mass))
+
+
+def mtpt_get_masses_async(h, out) -> None:
+    """Enqueue the read of the masses into `out` (n float64, host), filled
+    once mtpt_sync returns."""
+    n = out.numel() if hasattr(out, "numel") else np.asarray(out).size
+    po = _host_in_place(out, n, "out")
+    _check(load().mtpt_get_masses_async(h, po), "mtpt_get_masses_async")
+    _ASYNC_HOLD.setdefault(_handle_key(h), []).append(out)
 
 
 def mtpt_timing_enable(h, on: bool) -> None:
@@ -419,6 +475,17 @@ class Simulation:
 
     def masses(self) -> np.ndarray:
         return mtpt_get_masses(self.h, self.n)
+
+    def set_particles_async(self, pos, mass):
+        """Pipelined load (same n); pos, mass are read in place until sync()."""
+        mtpt_set_particles_async(self.h, self.params.dim, pos, mass)
+
+    def masses_async(self, out):
+        """Pipelined read into `out` (n float64, host), valid after sync()."""
+        mtpt_get_masses_async(self.h, out)
+
+    def sync(self):
+        mtpt_sync(self.h)
 
     def positions(self) -> np.ndarray:
         return mtpt_get_positions(self.h, self.params.dim, self.n)

@@ -32,7 +32,8 @@ int main(void) {
         ENTRY(mtpt_timing_enable), ENTRY(mtpt_timing_read), ENTRY(mtpt_timing_reset),
         ENTRY(mtpt_step_noalloc), ENTRY(mtpt_adjoint_forward), ENTRY(mtpt_adjoint_backward),
         ENTRY(mtpt_set_tuning), ENTRY(mtpt_get_tuning), ENTRY(mtpt_autotune),
-        ENTRY(mtpt_status_string)};
+        ENTRY(mtpt_status_string), ENTRY(mtpt_set_particles_async),
+        ENTRY(mtpt_get_masses_async)};
     for (size_t k = 0; k < sizeof(entries) / sizeof(entries[0]); ++k) EXPECT(entries[k] != NULL);
 
     mtpt_params p;
@@ -54,6 +55,9 @@ int main(void) {
     EXPECT(mtpt_step(h, -1) == MTPT_ERR_INVALID_ARG);
     double m = 0.0;
     EXPECT(mtpt_get_masses(h, &m) == MTPT_ERR_STATE);
+    EXPECT(mtpt_get_masses_async(h, &m) == MTPT_ERR_STATE);
+    EXPECT(mtpt_set_particles_async(h, 1, &m, &m) == MTPT_ERR_STATE);
+    EXPECT(mtpt_set_particles_async(NULL, 1, &m, &m) == MTPT_ERR_INVALID_ARG);
     EXPECT(mtpt_destroy(h) == MTPT_OK);
     EXPECT(mtpt_destroy(NULL) == MTPT_OK);
 

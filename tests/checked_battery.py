@@ -43,6 +43,25 @@ def run() -> dict:
             sim.step(4)
             out[f"advection_{fk}_m"] = sim.masses()
             out[f"advection_{fk}_x"] = sim.positions()
+    # pipelined host loads and reads, one of them rejected on the device
+    w = workloads.get("heaviside_2d", 20_000)
+    pos, mass = workloads.initial_state(w)
+    bad = pos.copy()
+    bad[0, 7] = w.hi[0] + 1.0
+    outs = [np.empty(w.n) for _ in range(3)]
+    with mtpt.Simulation(_params(w, mtpt.MTPT_FP32W), pos, mass) as sim:
+        for inp, o in zip(((pos, mass), (bad, mass), (pos, mass)), outs):
+            sim.set_particles_async(*inp)
+            sim.step(2)
+            sim.masses_async(o)
+        try:
+            sim.sync()
+        except mtpt.MtptError as e:
+            assert e.code == mtpt.MTPT_ERR_OUT_OF_DOMAIN
+        else:
+            raise AssertionError("the rejected load was not reported")
+    for k, o in enumerate(outs):
+        out[f"async_{k}_m"] = o
     # a batch of uneven realisations, both forms
     e = workloads.ensemble(nreal=16)
     members = sorted(e.members, key=lambda m: m.n)[:5]

@@ -65,6 +65,10 @@ def test_calls_before_particles_are_rejected(lib):
             mtpt.mtpt_step(h, 1)
         assert e.value.code == mtpt.MTPT_ERR_STATE
         assert lib.mtpt_step(h, -1) == mtpt.MTPT_ERR_INVALID_ARG
+        buf = (ctypes.c_double * 2)()
+        assert lib.mtpt_set_particles_async(h, 1, buf, buf) == mtpt.MTPT_ERR_STATE
+        assert lib.mtpt_get_masses_async(h, buf) == mtpt.MTPT_ERR_STATE
+        assert lib.mtpt_set_particles_async(None, 1, buf, buf) == mtpt.MTPT_ERR_INVALID_ARG
     finally:
         mtpt.mtpt_destroy(h)
 
