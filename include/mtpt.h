@@ -295,7 +295,7 @@ int mtpt_timing_reset(mtpt_handle* h);
  * pool, and time-critical loops that cannot pay for cudaMalloc/cudaFree
  * (cudaFree synchronises the device).  It creates no handle and calls no
  * cudaMalloc, cudaFree or other allocating routine: its working memory is a
- * fixed file-scope device array of MTPT_NOALLOC_SCRATCH_BYTES (9 MiB) that
+ * fixed file-scope device array of MTPT_NOALLOC_SCRATCH_BYTES (12 MiB) that
  * every GPU which loads this library holds until the process exits.
  *
  * pos_dev (dim x n SoA float64) and mass_dev (n float64) hold the state in
@@ -320,7 +320,7 @@ int mtpt_timing_reset(mtpt_handle* h);
  * (cudaGetSymbolAddress) with that device current and caches it; make that
  * first call on a device before any stream capture begins. */
 #define MTPT_NOALLOC_MAX_PARTICLES 65536
-#define MTPT_NOALLOC_SCRATCH_BYTES (9u << 20)
+#define MTPT_NOALLOC_SCRATCH_BYTES (12u << 20)
 int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step, double* pos_dev,
                       double* mass_dev, void* stream);
 

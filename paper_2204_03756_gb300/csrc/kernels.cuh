@@ -494,53 +494,72 @@ k_scan_apply(const uint4* __restrict__ count4, const uint32_t* __restrict__ tile
 }
 
 // ---------------------------------------------------------------------------
-// Step 2b: counting-sort scatter.  Each particle takes a slot of its cell;
-// decrementing the count returns every count to zero for the next step.
+// Step 2b: counting-sort scatter.  Each particle takes a slot of its cell
+// (decrementing the count returns every count to zero for the next step) and
+// stores there its index and a 16-byte sort key: x, and id | cell << 32, all
+// that the in-cell ranking of the gather reads.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock)
 k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ start,
-          uint32_t* __restrict__ count, uint32_t* __restrict__ perm) {
+          uint32_t* __restrict__ count, const double* __restrict__ x,
+          const uint32_t* __restrict__ id, uint32_t* __restrict__ perm,
+          double2* __restrict__ sortkey) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t c = key[i];
+    const double xi = x[i];
+    const uint32_t idi = id[i];
     const uint32_t left = atomicSub(&count[c], 1u);
     const uint32_t slot = start[c] + left - 1u;
     if (!check(left >= 1u && slot < uint32_t(n), kChkSlot)) return;
     perm[slot] = uint32_t(i);
+    sortkey[slot] = make_double2(xi, __longlong_as_double((long long)(uint64_t(idi) |
+                                                                      (uint64_t(c) << 32))));
 }
 
 // Step 2c: gather into cell order.  The slot order the atomics gave inside a
 // cell is replaced by the rank of (x, id) -- binary64 x in its integer order,
 // the id breaking ties -- so the layout (and every sum over it) is identical
 // run to run, and each neighbour row (cells cx-1..cx+1 of one y (, z)) is
-// sorted by x up to the cells' rounding slack, which the pair search uses.  Also writes the particle's cell, its
-// binary32 offset from the cell corner (from the binary32 head/tail split of
-// the coordinate and of the corner: error below 2^-23 w, no binary64
-// instruction) and, in the precision form, the mass's head/tail split.
+// sorted by x up to the cells' rounding slack, which the pair search uses.
+// The rank reads the sort keys of the cell's slots, next to the particle's
+// own; the rest of the payload comes from the source index.  Also writes the
+// particle's cell, its binary32 offset from the cell corner (from the
+// binary32 head/tail split of the coordinate and of the corner: error below
+// 2^-23 w, no binary64 instruction) and, in the precision form, the mass's
+// head/tail split.
 template <int DIM, bool SPLIT_MASS, class View, bool TANGENT = false>
 __global__ void __launch_bounds__(kBlock)
-k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ key,
-         const uint32_t* __restrict__ start, const uint32_t* __restrict__ id_in,
+k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
+         const double2* __restrict__ sortkey, const uint32_t* __restrict__ start,
          const double* __restrict__ pos_in, const double* __restrict__ mass_in,
-         uint32_t* __restrict__ id_out, double* __restrict__ pos_out, double* __restrict__ mass_out,
-         uint32_t* __restrict__ cell_out, float4* __restrict__ rec_out,
-         float2* __restrict__ msplit_out, const float2* __restrict__ corners,
-         uint32_t* __restrict__ rid_out, const __grid_constant__ View v,
-         const double* __restrict__ tan_in = nullptr, double* __restrict__ tan_out = nullptr) {
+         uint32_t* __restrict__ id_out, double* __restrict__ pos_out,
+         double* __restrict__ mass_out, uint32_t* __restrict__ cell_out,
+         float4* __restrict__ rec_out, float2* __restrict__ msplit_out,
+         const float2* __restrict__ corners, uint32_t* __restrict__ rid_out,
+         const __grid_constant__ View v, const double* __restrict__ tan_in = nullptr,
+         double* __restrict__ tan_out = nullptr) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t src = perm[s];
+    const double2 me = sortkey[s];
     if (!check(src < uint32_t(n), kChkGather)) return;
-    const uint32_t c = key[src];
+    // payload loads first: independent of the ranking below
+    double xa[3] = {me.x, 0.0, 0.0};
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) xa[a] = pos_in[a * stride + src];
+    const double m = mass_in[src];
+    const unsigned long long idc = (unsigned long long)__double_as_longlong(me.y);
+    const uint32_t my_id = uint32_t(idc), c = uint32_t(idc >> 32);
     const uint32_t b = start[c], e = start[c + 1];
-    const uint32_t my_id = id_in[src];
-    const long long my_x = order_key(pos_in[src]);
+    if (!check(b <= uint32_t(s) && uint32_t(s) < e && e <= uint32_t(n), kChkGather)) return;
+    const long long my_x = order_key(me.x);
     uint32_t rank = 0;
     for (uint32_t k = b; k < e; ++k) {
-        const uint32_t o = perm[k];
-        if (!check(o < uint32_t(n), kChkGather)) continue;
-        const long long xo = order_key(pos_in[o]);
-        rank += (xo < my_x || (xo == my_x && id_in[o] < my_id)) ? 1u : 0u;
+        const double2 q = sortkey[k];
+        const long long xo = order_key(q.x);
+        const uint32_t ido = uint32_t(__double_as_longlong(q.y));
+        rank += (xo < my_x || (xo == my_x && ido < my_id)) ? 1u : 0u;
     }
     const uint32_t dst = b + rank;
     if (!check(dst < e, kChkGather)) return;
@@ -548,7 +567,6 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
     cell_out[dst] = c;
     if constexpr (View::kBatch) rid_out[dst] = __ldg(v.rid_input + src);
     const RealParams& P = v.of_input(src);
-    const double m = mass_in[src];
     mass_out[dst] = m;
     if (SPLIT_MASS) {
         float hi, lo;
@@ -561,7 +579,7 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm, const uint32_
     for (int a = 0; a < DIM; ++a) {
         const uint32_t ca = rest % uint32_t(P.g.n[a]);
         rest /= uint32_t(P.g.n[a]);
-        const double x = pos_in[a * stride + src];
+        const double x = xa[a];
         pos_out[a * stride + dst] = x;
         if constexpr (TANGENT) tan_out[a * stride + dst] = tan_in[a * stride + src];
         if (P.transfer) {
@@ -1129,7 +1147,7 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
 }
 
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
-// hardware ex2, compensated binary32 row sum, rounded to binary32 into rec.w.
+// hardware ex2, compensated binary32 row sum, rounded to binary32 into r_out.
 template <int DIM, class View, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (DIM == 3 ? 1536 : 2048) / BLOCK)
 k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,

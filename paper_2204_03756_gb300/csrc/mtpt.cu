@@ -129,6 +129,7 @@ struct mtpt_handle {
     int cur = 0;
     // per-step scratch
     DevBuf<uint32_t> key, perm, cell, count, start, tile_sums;
+    DevBuf<double2> sortkey;          // (x, id | cell << 32) per slot (k_scatter)
     DevBuf<float4> rec;
     DevBuf<float2> corners;
     DevBuf<int> corner_first;
@@ -501,6 +502,7 @@ int ensure_capacity(mtpt_handle* h, int64_t n) {
         }
         MTPT_TRY(h->key.ensure(cap));
         MTPT_TRY(h->perm.ensure(cap));
+        MTPT_TRY(h->sortkey.ensure(cap));
         MTPT_TRY(h->cell.ensure(cap));
         MTPT_TRY(h->rec.ensure(cap));
         if (h->precision == MTPT_FP64) {
@@ -611,40 +613,42 @@ BatchView make_view<BatchView>(const mtpt_handle* h, int input_buf, int sorted_b
     return v;
 }
 
-// Gather from buffer c into buffer o in cell order (tangents too when on).
-template <int DIM, class View>
-int launch_gather(mtpt_handle* h, int c, int o, const View& vin) {
+// Counting-sort scatter of buffer c's particles into slots (index and sort
+// key), then the gather into buffer o in cell order (tangents too when on).
+template <int DIM, class View, bool TANGENT>
+int launch_sort_t(mtpt_handle* h, int c, int o, const View& vin) {
     const int n = int(h->n);
     const int blocks = grid_for(n);
     const int64_t stride = h->cap;
     uint32_t* rid_out = View::kBatch ? h->rid[o].p : nullptr;
-    float2* msplit = h->precision == MTPT_FP32W ? h->msplit.p : nullptr;
-    MTPT_TIMED(h, "gather");
-    if (h->precision == MTPT_FP32W) {
-        if (h->tangent_on)
-            k_gather<DIM, true, View, true><<<blocks, kBlock, 0, h->stream>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
-                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
-                msplit, h->corners.p, rid_out, vin, h->tan[c].p, h->tan[o].p);
-        else
-            k_gather<DIM, true, View><<<blocks, kBlock, 0, h->stream>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
-                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
-                msplit, h->corners.p, rid_out, vin);
-    } else {
-        if (h->tangent_on)
-            k_gather<DIM, false, View, true><<<blocks, kBlock, 0, h->stream>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
-                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
-                nullptr, h->corners.p, rid_out, vin, h->tan[c].p, h->tan[o].p);
-        else
-            k_gather<DIM, false, View><<<blocks, kBlock, 0, h->stream>>>(
-                n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p,
-                h->mass[c].p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p,
-                nullptr, h->corners.p, rid_out, vin);
+    const double* tan_in = TANGENT ? h->tan[c].p : nullptr;
+    double* tan_out = TANGENT ? h->tan[o].p : nullptr;
+    {
+        MTPT_TIMED(h, "scatter");
+        k_scatter<<<blocks, kBlock, 0, h->stream>>>(n, h->key.p, h->start.p, h->count.p,
+                                                    h->pos[c].p, h->id[c].p, h->perm.p,
+                                                    h->sortkey.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
     }
+    MTPT_TIMED(h, "gather");
+    if (h->precision == MTPT_FP32W)
+        k_gather<DIM, true, View, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->perm.p, h->sortkey.p, h->start.p, h->pos[c].p, h->mass[c].p,
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
+            h->corners.p, rid_out, vin, tan_in, tan_out);
+    else
+        k_gather<DIM, false, View, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->perm.p, h->sortkey.p, h->start.p, h->pos[c].p, h->mass[c].p,
+            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr, h->corners.p,
+            rid_out, vin, tan_in, tan_out);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
+}
+
+template <int DIM, class View>
+int launch_sort(mtpt_handle* h, int c, int o, const View& vin) {
+    if (h->tangent_on) return launch_sort_t<DIM, View, true>(h, c, o, vin);
+    return launch_sort_t<DIM, View, false>(h, c, o, vin);
 }
 
 template <int DIM, class View, int BLOCK>
@@ -725,13 +729,8 @@ int launch_step(mtpt_handle* h, int flags) {
         k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p,
                                                       reinterpret_cast<uint4*>(h->start.p));
     }
-    {
-        MTPT_TIMED(h, "scatter");
-        k_scatter<<<blocks, kBlock, 0, st>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
-    }
     const bool split = h->precision == MTPT_FP32W;
-    uint32_t* rid_out = View::kBatch ? h->rid[o].p : nullptr;
-    MTPT_TRY((launch_gather<DIM, View>(h, c, o, vin)));
+    MTPT_TRY((launch_sort<DIM, View>(h, c, o, vin)));
     // state now lives in buffer o (cell order); masses are updated into c
     const View vs = make_view<View>(h, o, o);
     const double* pos_s = h->pos[o].p;
@@ -1171,18 +1170,7 @@ int launch_emit(mtpt_handle* h, int64_t cap) {
     k_scan_tile_offsets<<<1, kScanThreads, 0, h->stream>>>(h->tile_sums.p, ntiles, h->step_dev.p, 0);
     k_scan_apply<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p,
                                                          reinterpret_cast<uint4*>(h->start.p));
-    k_scatter<<<blocks, kBlock, 0, h->stream>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
-    uint32_t* rid_out = View::kBatch ? h->rid[o].p : nullptr;
-    if (h->precision == MTPT_FP32W)
-        k_gather<DIM, true, View><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
-            h->corners.p, rid_out, vin);
-    else
-        k_gather<DIM, false, View><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->perm.p, h->key.p, h->start.p, h->id[c].p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr, h->corners.p,
-            rid_out, vin);
+    MTPT_TRY((launch_sort_t<DIM, View, false>(h, c, o, vin)));
     const View vs = make_view<View>(h, o, o);
     k_emit_pairs<DIM, View><<<blocks, kBlock, 0, h->stream>>>(
         n, stride, h->pos[o].p, h->rec.p, h->cell.p, h->start.p, h->id[o].p, vs,
@@ -1287,9 +1275,8 @@ int launch_adjoint_step(mtpt_handle* h) {
     k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(h->tile_sums.p, ntiles, h->step_dev.p, 1);
     k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p,
                                                   reinterpret_cast<uint4*>(h->start.p));
-    k_scatter<<<blocks, kBlock, 0, st>>>(n, h->key.p, h->start.p, h->count.p, h->perm.p);
     MTPT_CUDA_TRY(cudaGetLastError());
-    MTPT_TRY((launch_gather<DIM, SingleView>(h, c, o, v)));
+    MTPT_TRY((launch_sort<DIM, SingleView>(h, c, o, v)));
     k_take_by_id<<<blocks, kBlock, 0, st>>>(n, h->id[o].p, h->lam_in.p, h->lam_s.p);
     const NbList<double2> adj_nb{h->adj_nb_j.p, h->adj_nb_k.p, h->adj_nb_count.p,
                                  h->adj_nb_k.p ? h->adj_cap : 0};
@@ -1441,7 +1428,7 @@ int mtpt_destroy(mtpt_handle* h) {
         h->id[b].release();
         h->rid[b].release();
     }
-    h->key.release(); h->perm.release(); h->cell.release(); h->count.release();
+    h->key.release(); h->perm.release(); h->sortkey.release(); h->cell.release(); h->count.release();
     h->start.release(); h->tile_sums.release(); h->rec.release(); h->corners.release();
     h->corner_first.release(); h->id_first.release(); h->params_dev.release();
     h->r64.release(); h->r32.release(); h->msplit.release(); h->out_tmp.release();
@@ -1928,6 +1915,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     uint32_t* id_sorted = cv.take<uint32_t>(size_t(n));
     h.key.p = cv.take<uint32_t>(size_t(n));
     h.perm.p = cv.take<uint32_t>(size_t(n));
+    h.sortkey.p = cv.take<double2>(size_t(n));
     h.cell.p = cv.take<uint32_t>(size_t(n));
     h.rec.p = cv.take<float4>(size_t(n));
     if (h.precision == MTPT_FP64) {

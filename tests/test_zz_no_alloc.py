@@ -68,3 +68,31 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert "scratch" in mtpt.status_string(rc)
     assert lib.mtpt_step_noalloc(ctypes.byref(cp), -1, 0, None, None, None) == \
         mtpt.MTPT_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("form", [mtpt.MTPT_FP64, mtpt.MTPT_FP32W])
+def test_noalloc_runs_at_its_documented_limit(form):
+    """MTPT_NOALLOC_MAX_PARTICLES particles in 3-d fit the scratch even when
+    the box is so sparse that the cell count reaches its cap (the largest
+    layout the call can need), and match the handle path."""
+    import torch
+    lib = _lib()
+    n = mtpt.NOALLOC_MAX_PARTICLES
+    rng = np.random.default_rng(31)
+    L = 1000.0
+    pos = rng.uniform(0.0, L, size=(3, n))
+    mass = rng.uniform(0.0, 1.0, n)
+    p = mtpt.Params(dim=3, D=1.0, kappa=0.5, dt=0.1, lo=(0, 0, 0), hi=(L, L, L), seed=4,
+                    precision=form)
+    cp = p.c()
+    pos_t = torch.from_numpy(pos.copy()).cuda()
+    mass_t = torch.from_numpy(mass.copy()).cuda()
+    rc = lib.mtpt_step_noalloc(ctypes.byref(cp), n, 0, pos_t.data_ptr(), mass_t.data_ptr(), None)
+    assert rc == mtpt.MTPT_OK, mtpt.status_string(rc)
+    torch.cuda.synchronize()
+    with mtpt.Simulation(p, pos, mass) as ref:
+        ref.step(1)
+        assert np.array_equal(pos_t.cpu().numpy(), ref.positions())
+        want = ref.masses()
+    err = np.abs(mass_t.cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= TOL[form]
