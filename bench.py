@@ -77,12 +77,13 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # so it is scaled to the bench's launch).  Valid only for the kernel source it
 # was measured on: a different hash of kernels.cuh reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "9f4be57b6c4a"
+TRAFFIC_SOURCE_SHA1 = "b8e7bce4d2a8"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (177.798400e6 + 117.567232e6) / 8e6,
-    "gather": (305.869056e6 + 394.997760e6) / 8e6,
-    "rowsum_f32": (177.826816e6 + 24.156416e6) / 8e6,
-    "exchange_f32": (337.839360e6 + 55.972096e6) / 8e6,
+    "walk_key": (177.796352e6 + 117.956096e6) / 8e6,
+    "scatter": (163.769856e6 + 124.358400e6) / 8e6,
+    "gather": (306.039808e6 + 394.758400e6) / 8e6,
+    "rowsum_f32": (177.829888e6 + 25.130496e6) / 8e6,
+    "exchange_f32": (338.113536e6 + 53.869824e6) / 8e6,
 }
 
 
@@ -94,7 +95,8 @@ BINDING = {
     "rowsum_f32": "instruction issue: 88 % of issue slots at 20 of 32 active lanes; DRAM 9 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
-    "gather": "DRAM 53 % (random reads of the source particles)",
+    "gather": "DRAM 71 % (payload reads through the permutation, cell-ordered writes)",
+    "scatter": "DRAM 54 % (slot writes of the permutation and sort keys)",
     "walk_key": "binary64 pipe 82 % busy (x + sigma xi)",
 }
 
