@@ -233,8 +233,9 @@ int mtpt_set_step(mtpt_handle* h, uint64_t step);
  * and report any latched device error. */
 int mtpt_sync(mtpt_handle* h);
 
-/* Pipelined host I/O.  A loop that feeds every step from host memory and
- * reads every result back,
+/* Pipelined host I/O (no counterpart in the paper: host traffic around the
+ * Sec. 3 step).  A loop that feeds every step from host memory and reads
+ * every result back,
  *     repeat: mtpt_set_particles_async; mtpt_step(h, 1); mtpt_get_masses_async
  *     then:   mtpt_sync,
  * overlaps the host-to-device copy of one step's input and the device-to-host
@@ -261,7 +262,8 @@ int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const
 
 /* Enqueue a copy of the masses, in input order, into a HOST buffer of n
  * doubles: the masses as they stand after the work queued on the handle so
- * far.  The values are in `out` once mtpt_sync returns. */
+ * far.  The values are in `out` once mtpt_sync returns.  MTPT_ERR_STATE
+ * before the first load; MTPT_ERR_INVALID_ARG for a null `out` with n > 0. */
 int mtpt_get_masses_async(mtpt_handle* h, double* out);
 
 /* Per-kernel timing (tracing).  While enabled, every kernel the handle
