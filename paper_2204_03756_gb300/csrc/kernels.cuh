@@ -78,7 +78,7 @@ struct PairParams {
     float band_lo;     // binary32 d2 below this: certainly a neighbour
     float band_hi;     // binary32 d2 above this: certainly not a neighbour
     float reach2;      // band_hi (1 + 2^-16): bounds dx^2 + dy^2 (+ dz^2) of a neighbour
-    float trim_eps;    // slack of the per-row candidate windows (see row_window)
+    float trim_eps;    // slack of the per-row candidate windows (see for_each_row)
     double a;          // 1 / (2 h^2)
     float a_log2e;     // a * log2(e) in binary32 (precision form)
     double beta;
@@ -582,6 +582,117 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
         const double x = xa[a];
         pos_out[a * stride + dst] = x;
         if constexpr (TANGENT) tan_out[a * stride + dst] = tan_in[a * stride + src];
+        if (P.transfer) {
+            float xh, xlo;
+            split_double(x, &xh, &xlo);
+            const float2 cr = __ldg(corners + P.g.corner_off[a] + ca);
+            off[a] = __fadd_rn(__fsub_rn(xh, cr.x), __fsub_rn(xlo, cr.y));
+        }
+    }
+    rec_out[dst] = make_float4(off[0], off[1], off[2], float((c - P.cell_base) % uint32_t(P.g.n[0])));
+}
+
+// Sort of a freshly loaded single run, whose particles arrive in input order
+// rather than cell order: the same counting sort and the same cell order, but
+// the scatter stores each particle's whole payload as one record of 16-byte
+// chunks at its slot, so the gather reads only records in slot order.  A
+// record fills whole 32-byte sectors, which the scattered stores of an
+// unsorted input then write without a read (the sort keys plus a separate
+// payload read through the permutation cost more there; in steady state,
+// where the slots barely move, the opposite holds).  Eight-byte lanes:
+//   0: x   1: id | cell << 32   2..DIM: the other axes   DIM + 1: mass
+//   then DIM position tangents (TANGENT)
+template <int DIM, bool TANGENT>
+struct SortRec {
+    static constexpr int kLanes = 2 + DIM + (TANGENT ? DIM : 0);
+    static constexpr int kChunks = (kLanes + 1) / 2;
+    static constexpr int kTan = DIM + 2;
+};
+
+template <int DIM, bool TANGENT>
+__global__ void __launch_bounds__(kBlock)
+k_scatter_rec(int n, int64_t stride, const uint32_t* __restrict__ key,
+              const uint32_t* __restrict__ start, uint32_t* __restrict__ count,
+              const double* __restrict__ pos, const double* __restrict__ mass,
+              const uint32_t* __restrict__ id, const double* __restrict__ tan,
+              double2* __restrict__ recs) {
+    using R = SortRec<DIM, TANGENT>;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t c = key[i];
+    double lane[2 * R::kChunks];
+    lane[0] = pos[i];
+    lane[1] = __longlong_as_double((long long)(uint64_t(id[i]) | (uint64_t(c) << 32)));
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) lane[1 + a] = pos[a * stride + i];
+    lane[DIM + 1] = mass[i];
+    if constexpr (TANGENT) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) lane[R::kTan + a] = tan[a * stride + i];
+    }
+    if constexpr (R::kLanes % 2 == 1) lane[R::kLanes] = 0.0;
+    const uint32_t left = atomicSub(&count[c], 1u);
+    const uint32_t slot = start[c] + left - 1u;
+    if (!check(left >= 1u && slot < uint32_t(n), kChkSlot)) return;
+    double2* r = recs + size_t(slot) * R::kChunks;
+#pragma unroll
+    for (int k = 0; k < R::kChunks; ++k) r[k] = make_double2(lane[2 * k], lane[2 * k + 1]);
+}
+
+// Gather from the records: the rank inside the cell by (x order key, id)
+// reads chunk 0 of the cell's records; outputs as k_gather's.
+template <int DIM, bool SPLIT_MASS, bool TANGENT>
+__global__ void __launch_bounds__(kBlock)
+k_gather_rec(int n, int64_t stride, const double2* __restrict__ recs,
+             const uint32_t* __restrict__ start, uint32_t* __restrict__ id_out,
+             double* __restrict__ pos_out, double* __restrict__ mass_out,
+             uint32_t* __restrict__ cell_out, float4* __restrict__ rec_out,
+             float2* __restrict__ msplit_out, const float2* __restrict__ corners,
+             const __grid_constant__ SingleView v, double* __restrict__ tan_out) {
+    using R = SortRec<DIM, TANGENT>;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double lane[2 * R::kChunks];
+    const double2* me = recs + size_t(s) * R::kChunks;
+#pragma unroll
+    for (int k = 0; k < R::kChunks; ++k) {
+        const double2 q = me[k];
+        lane[2 * k] = q.x;
+        lane[2 * k + 1] = q.y;
+    }
+    const unsigned long long idc = (unsigned long long)__double_as_longlong(lane[1]);
+    const uint32_t my_id = uint32_t(idc), c = uint32_t(idc >> 32);
+    const uint32_t b = start[c], e = start[c + 1];
+    if (!check(b <= uint32_t(s) && uint32_t(s) < e && e <= uint32_t(n), kChkGather)) return;
+    const long long my_x = order_key(lane[0]);
+    uint32_t rank = 0;
+    for (uint32_t k = b; k < e; ++k) {
+        const double2 q = recs[size_t(k) * R::kChunks];
+        const long long xo = order_key(q.x);
+        const uint32_t ido = uint32_t(__double_as_longlong(q.y));
+        rank += (xo < my_x || (xo == my_x && ido < my_id)) ? 1u : 0u;
+    }
+    const uint32_t dst = b + rank;
+    if (!check(dst < e, kChkGather)) return;
+    id_out[dst] = my_id;
+    cell_out[dst] = c;
+    const RealParams& P = v.p;
+    const double m = lane[DIM + 1];
+    mass_out[dst] = m;
+    if (SPLIT_MASS) {
+        float hi, lo;
+        split_double(m, &hi, &lo);
+        msplit_out[dst] = make_float2(hi, lo);
+    }
+    float off[3] = {0.0f, 0.0f, 0.0f};
+    uint32_t rest = c - P.cell_base;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const uint32_t ca = rest % uint32_t(P.g.n[a]);
+        rest /= uint32_t(P.g.n[a]);
+        const double x = lane[a == 0 ? 0 : 1 + a];
+        pos_out[a * stride + dst] = x;
+        if constexpr (TANGENT) tan_out[a * stride + dst] = lane[R::kTan + a];
         if (P.transfer) {
             float xh, xlo;
             split_double(x, &xh, &xlo);

@@ -130,6 +130,8 @@ struct mtpt_handle {
     // per-step scratch
     DevBuf<uint32_t> key, perm, cell, count, start, tile_sums;
     DevBuf<double2> sortkey;          // (x, id | cell << 32) per slot (k_scatter)
+    DevBuf<double2> sortrec;          // payload records per slot (k_scatter_rec)
+    bool fresh = false;               // state loaded in input order, not yet sorted
     DevBuf<float4> rec;
     DevBuf<float2> corners;
     DevBuf<int> corner_first;
@@ -645,8 +647,48 @@ int launch_sort_t(mtpt_handle* h, int c, int o, const View& vin) {
     return MTPT_OK;
 }
 
+// The sort of a freshly loaded single run: payload records (see
+// k_scatter_rec), then the gather from them.
+template <int DIM, bool TANGENT>
+int launch_sort_rec(mtpt_handle* h, int c, int o, const SingleView& vin) {
+    const int n = int(h->n);
+    const int blocks = grid_for(n);
+    const int64_t stride = h->cap;
+    MTPT_TRY(h->sortrec.ensure(size_t(SortRec<DIM, TANGENT>::kChunks) * size_t(h->cap)));
+    {
+        MTPT_TIMED(h, "scatter");
+        k_scatter_rec<DIM, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->key.p, h->start.p, h->count.p, h->pos[c].p, h->mass[c].p, h->id[c].p,
+            TANGENT ? h->tan[c].p : nullptr, h->sortrec.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    MTPT_TIMED(h, "gather");
+    double* tan_out = TANGENT ? h->tan[o].p : nullptr;
+    if (h->precision == MTPT_FP32W)
+        k_gather_rec<DIM, true, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->sortrec.p, h->start.p, h->id[o].p, h->pos[o].p, h->mass[o].p,
+            h->cell.p, h->rec.p, h->msplit.p, h->corners.p, vin, tan_out);
+    else
+        k_gather_rec<DIM, false, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
+            n, stride, h->sortrec.p, h->start.p, h->id[o].p, h->pos[o].p, h->mass[o].p,
+            h->cell.p, h->rec.p, nullptr, h->corners.p, vin, tan_out);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
+}
+
+// Sort of buffer c into buffer o: the record sort right after a host load of
+// a single run (input order), the sort-key sort otherwise.  Both give the
+// same cell order bit for bit.
 template <int DIM, class View>
 int launch_sort(mtpt_handle* h, int c, int o, const View& vin) {
+    const bool fresh = h->fresh;
+    h->fresh = false;
+    if constexpr (!View::kBatch) {
+        if (fresh) {
+            if (h->tangent_on) return launch_sort_rec<DIM, true>(h, c, o, vin);
+            return launch_sort_rec<DIM, false>(h, c, o, vin);
+        }
+    }
     if (h->tangent_on) return launch_sort_t<DIM, View, true>(h, c, o, vin);
     return launch_sort_t<DIM, View, false>(h, c, o, vin);
 }
@@ -784,7 +826,7 @@ int capture_two_steps(mtpt_handle* h, int flags) {
         MTPT_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     const cudaStream_t user = h->stream;
     const int cur0 = h->cur;
-    const bool rows0 = h->have_row_sums;
+    const bool rows0 = h->have_row_sums, fresh0 = h->fresh;
     DevBuf<double> mass0 = h->mass[0], mass1 = h->mass[1];
     h->stream = h->capture_stream;
     MTPT_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -796,6 +838,7 @@ int capture_two_steps(mtpt_handle* h, int flags) {
     h->stream = user;
     h->cur = cur0;
     h->have_row_sums = rows0;
+    h->fresh = fresh0;
     h->mass[0] = mass0;
     h->mass[1] = mass1;
     if (ec != cudaSuccess || rc != MTPT_OK || !graph) {
@@ -820,6 +863,10 @@ int capture_two_steps(mtpt_handle* h, int flags) {
 int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {
     const bool use_graph = nsteps >= kGraphMinSteps && !h->timing && !h->tangent_on && h->n > 0;
     int64_t done = 0;
+    if (use_graph && h->fresh) {          // the record sort stays out of the graph
+        MTPT_TRY(dispatch_step(h, flags));
+        done = 1;
+    }
     if (use_graph) {
         if (!h->graph || h->graph_cur != h->cur || h->graph_flags != flags ||
             h->graph_mass0 != h->mass[0].p)
@@ -920,6 +967,7 @@ int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, con
     h->have_row_sums = false;
     h->have_particles = true;
     h->adj_ready = false;
+    h->fresh = true;
     return MTPT_OK;
 }
 
@@ -1170,7 +1218,7 @@ int launch_emit(mtpt_handle* h, int64_t cap) {
     k_scan_tile_offsets<<<1, kScanThreads, 0, h->stream>>>(h->tile_sums.p, ntiles, h->step_dev.p, 0);
     k_scan_apply<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p,
                                                          reinterpret_cast<uint4*>(h->start.p));
-    MTPT_TRY((launch_sort_t<DIM, View, false>(h, c, o, vin)));
+    MTPT_TRY((launch_sort<DIM, View>(h, c, o, vin)));
     const View vs = make_view<View>(h, o, o);
     k_emit_pairs<DIM, View><<<blocks, kBlock, 0, h->stream>>>(
         n, stride, h->pos[o].p, h->rec.p, h->cell.p, h->start.p, h->id[o].p, vs,
@@ -1428,7 +1476,7 @@ int mtpt_destroy(mtpt_handle* h) {
         h->id[b].release();
         h->rid[b].release();
     }
-    h->key.release(); h->perm.release(); h->sortkey.release(); h->cell.release(); h->count.release();
+    h->key.release(); h->perm.release(); h->sortkey.release(); h->sortrec.release(); h->cell.release(); h->count.release();
     h->start.release(); h->tile_sums.release(); h->rec.release(); h->corners.release();
     h->corner_first.release(); h->id_first.release(); h->params_dev.release();
     h->r64.release(); h->r32.release(); h->msplit.release(); h->out_tmp.release();
@@ -1551,6 +1599,7 @@ int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const
     h->step = 0;
     h->have_row_sums = false;
     h->adj_ready = false;
+    h->fresh = true;
     return MTPT_OK;
 }
 
@@ -1736,6 +1785,7 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
     MTPT_TRY(sid.ensure(size_t(std::max<int64_t>(n, 1))));
     if (h->batch) MTPT_TRY(srid.ensure(size_t(std::max<int64_t>(n, 1))));
     const int c0 = h->cur;
+    const bool fresh0 = h->fresh;         // every trial starts from the same state
     auto copy_state = [&](bool save) -> int {
         const size_t pitch = size_t(h->cap) * sizeof(double), row = size_t(n) * sizeof(double);
         if (n == 0) return MTPT_OK;
@@ -1748,6 +1798,7 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
                 MTPT_CUDA_TRY(cudaMemcpyAsync(srid.p, h->rid[c0].p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
         } else {
             h->cur = c0;
+            h->fresh = fresh0;
             MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[c0].p, pitch, spos.p, row, row, d,
                                             cudaMemcpyDeviceToDevice, h->stream));
             MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[c0].p, smass.p, row, cudaMemcpyDeviceToDevice, h->stream));

@@ -51,8 +51,9 @@ def test_noalloc_step_matches_the_handle_path_on_two_calls(form, name, n):
             got_x = pos_t.cpu().numpy()
             want_m, want_x = ref.masses(), ref.positions()
             assert np.array_equal(got_x, want_x)
-            err = np.abs(got_m - want_m).max() / np.abs(want_m).max()
-            assert err <= TOL[form], (call, err)
+            # the handle sorts its freshly loaded state with payload records,
+            # this call with sort keys: the same cell order, the same masses
+            assert np.array_equal(got_m, want_m), call
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
