@@ -145,3 +145,42 @@ def test_argument_errors():
         with pytest.raises(mtpt.MtptError) as e:
             mtpt.mtpt_set_particles_async(b.h, 2, bpos, bmass)
         assert e.value.code == mtpt.MTPT_ERR_INVALID_ARG
+
+
+def test_pipeline_on_a_user_stream_with_timing_and_a_one_member_batch():
+    """The pipelined calls on a caller's stream with per-kernel timing on, and
+    on a batch handle of one realisation, give the single handle's masses."""
+    import torch
+    w = workloads.get("heaviside_2d", 6000)
+    p = params_of(w, precision=mtpt.MTPT_FP32W)
+    inputs = _inputs(w, 2, 9)
+    ref = []
+    with mtpt.Simulation(p, *inputs[0]) as sim:
+        for k in (1, 0, 1):
+            sim.set_particles(*inputs[k])
+            sim.step(2)
+            ref.append(sim.masses())
+    pinned = [(_pinned(x), _pinned(m)) for x, m in inputs]
+    stream = torch.cuda.Stream()
+    outs = [torch.empty(w.n, dtype=torch.float64).pin_memory() for _ in ref]
+    with mtpt.Simulation(p, *inputs[0]) as sim:
+        mtpt.mtpt_set_stream(sim.h, stream.cuda_stream)
+        mtpt.mtpt_timing_enable(sim.h, True)
+        for k, out in zip((1, 0, 1), outs):
+            sim.set_particles_async(*pinned[k])
+            sim.step(2)
+            sim.masses_async(out)
+        sim.sync()
+        stats = mtpt.mtpt_timing_read(sim.h)
+        assert stats["load_input"][0] == 3 and stats["exchange_f32"][0] == 6
+    for r, o in zip(ref, outs):
+        assert np.array_equal(o.numpy(), r)
+    outs_b = [np.empty(w.n) for _ in ref]
+    with mtpt.Batch([p], [w.n], *inputs[0]) as b:
+        for k, out in zip((1, 0, 1), outs_b):
+            mtpt.mtpt_set_particles_async(b.h, 2, *inputs[k])
+            b.step(2)
+            mtpt.mtpt_get_masses_async(b.h, out)
+        b.sync()
+    for r, o in zip(ref, outs_b):
+        assert np.array_equal(o, r)
