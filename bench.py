@@ -87,6 +87,20 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 }
 
 
+# Warp instructions per particle of the binary32-form kernels in the same
+# capture (smsp__inst_executed.sum / 8e6): with the live launch time they
+# give the issue rate, against the issue peak of 4 warp instructions per
+# clock per SM (one per scheduler).
+INSTR_PER_PARTICLE = {
+    "walk_key": 82277063 / 8e6,
+    "scatter": 8250000 / 8e6,
+    "gather": 84628991 / 8e6,
+    "rowsum_f32": 301831677 / 8e6,
+    "exchange_f32": 390664107 / 8e6,
+}
+SMS, SCHEDULERS_PER_SM = 152, 4
+
+
 # What bounds each kernel in that same capture (ncu counters; see
 # profiles/step_kernels_gaussian_2d_8M_full.md), reported beside the roofline
 # while the kernel source hash matches.
@@ -371,6 +385,21 @@ def _f64_ops_per_pair(kernel: str, dim: int) -> float:
 F64_PEAK_OPS = 2 * 152 * 2.07e9
 
 
+def issue_rate(name, w, per_launch_s, clocks):
+    """Warp instructions issued per second by one launch of `name` (from the
+    captured count per particle) against the issue peak at the SM clock the
+    timed region ran at; None when the capture does not apply."""
+    if name not in INSTR_PER_PARTICLE or w.dim != TRAFFIC_DIM or \
+            _kernel_source_sha1() != TRAFFIC_SOURCE_SHA1:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    achieved = INSTR_PER_PARTICLE[name] * w.n / per_launch_s
+    peak = SMS * SCHEDULERS_PER_SM * mhz * 1e6
+    return {"achieved": achieved, "peak": peak, "unit": "warp instr/s", "frac": achieved / peak,
+            "instr_per_launch": INSTR_PER_PARTICLE[name] * w.n,
+            "peak_source": f"{SMS} SMs x {SCHEDULERS_PER_SM} schedulers x {mhz:.0f} MHz"}
+
+
 def roofline(w, res, peaks):
     kst = res["kernels"]
     name, (launches, total_ms) = max(kst.items(), key=lambda kv: kv[1][1])
@@ -396,7 +425,8 @@ def roofline(w, res, peaks):
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"],
             "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "algorithmic_bytes_per_launch": algo, "launch_ms": per_launch_s * 1e3,
-            "share_of_step": share, "binding_ncu": binding, "peak_source": peaks["source"]}
+            "share_of_step": share, "binding_ncu": binding, "peak_source": peaks["source"],
+            "issue": issue_rate(name, w, per_launch_s, res.get("clocks"))}
 
 
 def e2e_form(w, pos, mass, form, steps, rank, world=1, dist=None):
