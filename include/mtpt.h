@@ -127,20 +127,30 @@ typedef struct mtpt_handle mtpt_handle;
 int mtpt_check_word(uint32_t* out, int32_t reset);
 
 /* Create a handle on the current CUDA device.  *out receives the handle.
+ * Defining passage: the parameters of Sec. 3 -- the split D_RW = kappa D,
+ * D_MT = (1 - kappa) D of the diffusion coefficient, the search radius psi of
+ * Eq. "cutoff", the kernel bandwidth h^2 = 2 D_MT dt / beta that follows
+ * Eq. "kernel", and the domain with zero-flux (reflecting) walls; v is the
+ * velocity of the model equation of Sec. 2.
  * Validates the parameters (MTPT_ERR_INVALID_ARG).  Allocates nothing on the
  * device until particles are set. */
 int mtpt_create(const mtpt_params* params, mtpt_handle** out);
 
 /* Release every device allocation and the handle.  Synchronises the stream.
- * Passing NULL is a no-op returning MTPT_OK. */
+ * Passing NULL is a no-op returning MTPT_OK.  Resource management: no
+ * counterpart in the paper. */
 int mtpt_destroy(mtpt_handle* h);
 
 /* Order all later device work of the handle on `stream` (a cudaStream_t;
- * NULL selects the legacy default stream). */
+ * NULL selects the legacy default stream).  Execution control: no
+ * counterpart in the paper. */
 int mtpt_set_stream(mtpt_handle* h, void* stream);
 
 /* Load n particles from HOST buffers: pos (dim x n, SoA float64) and mass (n
- * float64).  Every coordinate must be finite and inside [lo, hi] of its axis
+ * float64).  Defining passage: the particle state of Sec. 2.1 and Sec. 3 --
+ * positions X_i inside the domain and masses M_i at the current time (the
+ * paper's test problem scatters the particles uniformly and gives them a
+ * Heaviside mass, Sec. 2.1).  Every coordinate must be finite and inside [lo, hi] of its axis
  * (MTPT_ERR_OUT_OF_DOMAIN otherwise) and every mass finite, in the precision
  * form at most 1e30 in magnitude (MTPT_ERR_INVALID_ARG otherwise); on either
  * error the handle keeps its old state.  The buffers are copied to the device
@@ -159,6 +169,9 @@ int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
                               const double* mass_dev);
 
 /* Batch of independent realisations stepped together (the ensemble form).
+ * Defining passage: each realisation is one run of the Sec. 3 step; the
+ * paper averages its timings over an ensemble of five independent runs
+ * (Sec. 2.3), which a batch steps in one launch per kernel.
  * params[k] holds realisation k's parameters (D, kappa, dt, beta, lambda,
  * box, seed may all differ); dim and precision must be equal across the
  * batch (MTPT_ERR_INVALID_ARG otherwise), 1 <= count <= 2^20.  Every time
@@ -167,7 +180,8 @@ int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
  * same particles would. */
 int mtpt_create_batch(const mtpt_params* params, int32_t count, mtpt_handle** out);
 
-/* Load the particles of every realisation of a batch from HOST buffers:
+/* Load the particles of every realisation of a batch from HOST buffers
+ * (the particle state of Sec. 2.1 and Sec. 3, per realisation):
  * counts[k] particles for realisation k (count entries), concatenated in
  * realisation order.  pos is dim x total (SoA over the concatenation: axis a
  * of particle i of realisation k at pos[a * total + offset_k + i], offset_k
@@ -178,12 +192,17 @@ int mtpt_create_batch(const mtpt_params* params, int32_t count, mtpt_handle** ou
 int mtpt_set_particles_batch(mtpt_handle* h, const int64_t* counts, const double* pos,
                              const double* mass);
 
-/* Derived quantities of realisation k of a batch (n is that realisation's
+/* Derived quantities (Sec. 3) of realisation k of a batch (n is that realisation's
  * particle count; pair_count is not filled). */
 int mtpt_get_realisation_info(mtpt_handle* h, int32_t k, mtpt_info* out);
 
 /* Advance nsteps full time steps (walk, then mass transfer on the moved
- * positions).  Enqueued on the stream; returns the launch status.  Calls of
+ * positions).  Defining passage: the time step of Sec. 3 -- the random walk
+ * X_i(t + dt) = X_i(t) + xi_i sqrt(2 D_RW dt) with elastic reflection at the
+ * walls, every pair within psi of Eq. "cutoff", the simplified kernel that
+ * follows Eq. "kernel", the normalisation W_ij = K_ij / (1/2 (column sum +
+ * row sum)), and M_i(t + dt) = M_i(t) + delta_i with delta_i of
+ * Eq. "changemass", all M_j taken at time t.  Enqueued on the stream; returns the launch status.  Calls of
  * four or more steps capture two steps as a CUDA graph on first use and
  * replay it (same results as step-by-step launches). */
 int mtpt_step(mtpt_handle* h, int64_t nsteps);
@@ -193,27 +212,32 @@ int mtpt_step(mtpt_handle* h, int64_t nsteps);
  * when MTPT_DO_WALK is set. */
 int mtpt_step_ex(mtpt_handle* h, int64_t nsteps, int32_t flags);
 
-/* Copy the masses, in input order, to a HOST buffer of n doubles.  Syncs and
- * reports any latched device error. */
+/* Copy the masses, in input order, to a HOST buffer of n doubles.  Defining
+ * passage: the particle masses M_i(t) of Sec. 3 (the paper turns them into
+ * concentrations as C = N M / L^d, end of Sec. 3).  Syncs and reports any
+ * latched device error. */
 int mtpt_get_masses(mtpt_handle* h, double* out);
 
 /* As mtpt_get_masses into a DEVICE buffer of n doubles (stream-ordered). */
 int mtpt_get_masses_device(mtpt_handle* h, double* out_dev);
 
 /* Copy the positions, in input order, to a HOST buffer of dim x n doubles
- * (SoA).  Syncs. */
+ * (SoA).  Defining passage: the positions X_i(t) produced by the random walk
+ * with reflection of Sec. 3.  Syncs. */
 int mtpt_get_positions(mtpt_handle* h, double* out);
 
 /* As mtpt_get_positions into a DEVICE buffer of dim x n doubles. */
 int mtpt_get_positions_device(mtpt_handle* h, double* out_dev);
 
-/* Row sums r_i = sum_j K_ij (self term included, in the paper's units, i.e.
+/* Row sums r_i = sum_j K_ij of the normalisation of W (Sec. 3; self term
+ * included, in the paper's units, i.e.
  * with the factor (2 pi h^2)^(-d/2)) of the most recent transfer step, in
  * input order, to a HOST buffer of n doubles.  MTPT_ERR_STATE before the first
  * transfer step. */
 int mtpt_get_row_sums(mtpt_handle* h, double* out);
 
-/* Neighbour pairs of the CURRENT positions: every ordered pair (i, j), i != j,
+/* Neighbour pairs of the CURRENT positions -- the neighbour list within psi
+ * (Eq. "cutoff") that the search of Sec. 3 provides: every ordered pair (i, j), i != j,
  * with ||x_i - x_j||^2 <= psi^2, as input-order indices, written to the HOST
  * arrays pair_i / pair_j of capacity `cap` (in no particular order).
  * *count receives the number of pairs; if it exceeds cap, only cap pairs are
@@ -221,16 +245,19 @@ int mtpt_get_row_sums(mtpt_handle* h, double* out);
 int mtpt_get_pairs(mtpt_handle* h, int64_t cap, int64_t* count, uint32_t* pair_i,
                    uint32_t* pair_j);
 
-/* Derived quantities and counters.  Syncs. */
+/* Derived quantities of Sec. 3 (D_RW, D_MT, h^2, psi of Eq. "cutoff", the
+ * kernel's constant) and counters.  Syncs. */
 int mtpt_get_info(mtpt_handle* h, mtpt_info* out);
 
-/* Overwrite the walk's step counter (checkpoint resume: a run restarted from
+/* Overwrite the walk's step counter (checkpoint resume, no counterpart in the
+ * paper: a run restarted from
  * saved positions and masses with the saved counter reproduces the
  * uninterrupted run bit for bit). */
 int mtpt_set_step(mtpt_handle* h, uint64_t step);
 
 /* Wait for the handle's stream (and the copy streams of the *_async calls)
- * and report any latched device error. */
+ * and report any latched device error.  Execution control: no counterpart in
+ * the paper. */
 int mtpt_sync(mtpt_handle* h);
 
 /* Pipelined host I/O (no counterpart in the paper: host traffic around the
@@ -248,7 +275,8 @@ int mtpt_sync(mtpt_handle* h);
  * needs page-locked host memory; pageable memory gives the same results with
  * the copies serialised by the driver. */
 
-/* Enqueue a load of n particles from HOST buffers laid out as for
+/* Pipelined host I/O (no counterpart in the paper).  Enqueue a load of n
+ * particles from HOST buffers laid out as for
  * mtpt_set_particles.  n must equal the handle's current particle count
  * (MTPT_ERR_INVALID_ARG otherwise, also for a handle of more than one
  * realisation; MTPT_ERR_STATE before the first load).  The device checks the
@@ -260,7 +288,8 @@ int mtpt_sync(mtpt_handle* h);
  * MTPT_ERR_INVALID_ARG for a mass. */
 int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const double* mass);
 
-/* Enqueue a copy of the masses, in input order, into a HOST buffer of n
+/* Pipelined host I/O (no counterpart in the paper).  Enqueue a copy of the
+ * masses, in input order, into a HOST buffer of n
  * doubles: the masses as they stand after the work queued on the handle so
  * far.  The values are in `out` once mtpt_sync returns.  MTPT_ERR_STATE
  * before the first load; MTPT_ERR_INVALID_ARG for a null `out` with n > 0. */
@@ -276,14 +305,16 @@ typedef struct mtpt_kernel_stat {
     double total_ms;        /* summed event-to-event time of those launches */
 } mtpt_kernel_stat;
 
-/* Start (on != 0) or stop timing; stopping keeps the collected figures. */
+/* Start (on != 0) or stop timing; stopping keeps the collected figures.
+ * Tracing: no counterpart in the paper (which profiles with gprof, Sec. 6). */
 int mtpt_timing_enable(mtpt_handle* h, int32_t on);
 
-/* Synchronise, fold pending events into the per-kernel sums, and copy up to
+/* Tracing (no counterpart in the paper).  Synchronise, fold pending events
+ * into the per-kernel sums, and copy up to
  * `cap` entries into `out`; *count receives the number of distinct kernels. */
 int mtpt_timing_read(mtpt_handle* h, int32_t cap, mtpt_kernel_stat* out, int32_t* count);
 
-/* Clear the per-kernel sums. */
+/* Clear the per-kernel sums (tracing: no counterpart in the paper). */
 int mtpt_timing_reset(mtpt_handle* h);
 
 /* One full time step (walk, then mass transfer) on caller-owned DEVICE
@@ -326,7 +357,7 @@ int mtpt_timing_reset(mtpt_handle* h);
 int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step, double* pos_dev,
                       double* mass_dev, void* stream);
 
-/* Adjoint of a run (spec form 3; the paper has no gradient).  For a
+/* Adjoint of a run (no counterpart in the paper, which has no gradient).  For a
  * loss L(M_T) of the final masses, gives dL/dM_0 and dL/dD along the run's own
  * random path (the normals xi stay fixed: pathwise derivative).  The mass
  * update is linear, M_{t+1} = A_t M_t with A_t = I + beta (W_t - diag(W_t 1))
@@ -337,14 +368,16 @@ int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step, doubl
  * in binary64 in both precision forms (for MTPT_FP32W they differentiate the
  * binary64 model at the run's positions, which are the same in both forms). */
 
-/* Advance nsteps full steps from the loaded state, as mtpt_step does, while
+/* Adjoint (no counterpart in the paper).  Advance nsteps full steps from the
+ * loaded state, as mtpt_step does, while
  * recording a checkpoint of the state every `checkpoint_every` steps and the
  * position tangents dX/dD.  Memory: (nsteps / checkpoint_every +
  * checkpoint_every + 1) snapshots of (4 dim + 12) bytes per particle.
  * Synchronises. */
 int mtpt_adjoint_forward(mtpt_handle* h, int64_t nsteps, int64_t checkpoint_every);
 
-/* Reverse sweep of the run recorded by mtpt_adjoint_forward: gmass_dev holds
+/* Adjoint (no counterpart in the paper).  Reverse sweep of the run recorded
+ * by mtpt_adjoint_forward: gmass_dev holds
  * dL/dM_T (n doubles, DEVICE, input order); gmass0_dev receives dL/dM_0 (n
  * doubles, DEVICE, input order); *dldD receives dL/dD (HOST).  Recomputes
  * each segment forward from its checkpoint, then steps back through it.
@@ -365,14 +398,16 @@ typedef struct mtpt_tuning {
     int32_t pad;
 } mtpt_tuning;
 
-/* Apply a tuning (MTPT_ERR_INVALID_ARG outside the ranges above); the cell
+/* Launch tuning (no counterpart in the paper).  Apply a tuning
+ * (MTPT_ERR_INVALID_ARG outside the ranges above); the cell
  * list is rebuilt on the next step. */
 int mtpt_set_tuning(mtpt_handle* h, const mtpt_tuning* t);
 
-/* Current tuning. */
+/* Current tuning (no counterpart in the paper). */
 int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out);
 
-/* Autotuner: times `trial_steps` full steps (after one warm-up step) of the
+/* Autotuner (no counterpart in the paper): times `trial_steps` full steps
+ * (after one warm-up step) of the
  * loaded particles for every cell_scale in {1, 1.25, 1.5, 2} and pair_block
  * in {128, 256}, keeps the fastest, and restores the particles, masses, step
  * counter and pair counter to their state before the call.  Allocates a
@@ -380,7 +415,8 @@ int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out);
  * Synchronises. */
 int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen);
 
-/* Human-readable text of a status code (static storage). */
+/* Human-readable text of a status code (static storage).  Error reporting:
+ * no counterpart in the paper. */
 const char* mtpt_status_string(int status);
 
 #ifdef __cplusplus

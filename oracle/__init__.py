@@ -12,9 +12,13 @@ no fast-math); ``oracle.py`` is a ctypes binding over numpy arrays and
 Parity status of each oracle function (what pins it to something other than
 itself; the tests named are under ``tests/``):
 
-* ``philox4x32_10``     -- pinned by test_oracle_rng.py: the round structure
-  checked against an independent big-integer restatement of the published
-  definition, bijectivity on a sample, and bit statistics.
+* ``philox4x32_10``     -- pinned by test_oracle_rng.py word for word to a
+  third-party implementation of the same published generator (PyTorch's
+  host-side Philox engine, called as a library routine) over random and
+  edge-case counters and keys, plus avalanche and uniformity statistics.
+* ``box_muller``        -- pinned to the float64 Box-Muller formula on the
+  same words (which word gives the radius, which the angle, and the uniform
+  map), and ``normals`` to ``box_muller`` of the library's words.
 * ``log_f32``, ``sincos_2pi_f32`` -- pinned to numpy's float64 log/sin/cos
   over every input the walk can produce (error bounds in ulps).
 * ``normals``           -- pinned by a Kolmogorov-Smirnov test against N(0,1)

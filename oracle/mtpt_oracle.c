@@ -152,15 +152,9 @@ void orc_sincos_2pi_many(int64_t n, const uint32_t* k, float* s, float* c) {
     for (int64_t i = 0; i < n; ++i) orc_sincos_2pi_f32(k[i], s + i, c + i);
 }
 
-/* Four N(0,1) draws for (particle id, step).  Counter (id, step mod 2^32,
- * step div 2^32, 0), key (seed mod 2^32, seed div 2^32).  Normals 0,1 come
- * from words (0,1) and normals 2,3 from words (2,3); axis a of the walk uses
- * normal a. */
-void orc_normals4(uint64_t seed, uint32_t id, uint64_t step, float out[4]) {
-    uint32_t ctr[4] = { id, (uint32_t)step, (uint32_t)(step >> 32), 0u };
-    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
-    uint32_t w[4];
-    orc_philox4x32_10(ctr, key, w);
+/* Four N(0,1) draws from one block of four generator words: normals 0,1
+ * come from words (0,1) and normals 2,3 from words (2,3). */
+void orc_box_muller4(const uint32_t w[4], float out[4]) {
     for (int pair = 0; pair < 2; ++pair) {
         uint32_t ka = (w[2 * pair] >> 8) + 1u;        /* in [1, 2^24] */
         uint32_t kb = (w[2 * pair + 1] >> 8) + 1u;
@@ -171,6 +165,21 @@ void orc_normals4(uint64_t seed, uint32_t id, uint64_t step, float out[4]) {
         out[2 * pair] = radius * cs;
         out[2 * pair + 1] = radius * sn;
     }
+}
+
+void orc_box_muller_many(int64_t n, const uint32_t* w /* n x 4 */, float* out /* n x 4 */) {
+    for (int64_t i = 0; i < n; ++i) orc_box_muller4(w + 4 * i, out + 4 * i);
+}
+
+/* Four N(0,1) draws for (particle id, step).  Counter (id, step mod 2^32,
+ * step div 2^32, 0), key (seed mod 2^32, seed div 2^32); axis a of the walk
+ * uses normal a. */
+void orc_normals4(uint64_t seed, uint32_t id, uint64_t step, float out[4]) {
+    uint32_t ctr[4] = { id, (uint32_t)step, (uint32_t)(step >> 32), 0u };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    orc_box_muller4(w, out);
 }
 
 void orc_normals_many(uint64_t seed, int64_t n, const uint32_t* id, uint64_t step,

@@ -22,7 +22,7 @@ _lib = None
 
 __all__ = [
     "OracleParams", "build", "load", "derived", "philox4x32_10", "log_f32",
-    "sincos_2pi_f32", "normals", "reflect", "random_walk", "pairs",
+    "sincos_2pi_f32", "box_muller", "normals", "reflect", "random_walk", "pairs",
     "mass_transfer", "run",
 ]
 
@@ -88,6 +88,7 @@ def load():
     lib.orc_philox_many.argtypes = [ctypes.c_int64, u32p, u32p, u32p]
     lib.orc_log_f32_many.argtypes = [ctypes.c_int64, f32p, f32p]
     lib.orc_sincos_2pi_many.argtypes = [ctypes.c_int64, u32p, f32p, f32p]
+    lib.orc_box_muller_many.argtypes = [ctypes.c_int64, u32p, f32p]
     lib.orc_normals_many.argtypes = [ctypes.c_uint64, ctypes.c_int64, u32p,
                                      ctypes.c_uint64, f32p]
     lib.orc_reflect.argtypes = [ctypes.c_double] * 3
@@ -150,6 +151,16 @@ def sincos_2pi_f32(k):
     lib.orc_sincos_2pi_many(k.size, _ptr(k, ctypes.c_uint32), _ptr(s, ctypes.c_float),
                             _ptr(c, ctypes.c_float))
     return s, c
+
+
+def box_muller(words) -> np.ndarray:
+    """The four N(0,1) draws (n x 4 float32) the walk takes from each block
+    of four generator words (n x 4 uint32)."""
+    lib = load()
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(-1, 4))
+    out = np.empty(w.shape, dtype=np.float32)
+    lib.orc_box_muller_many(w.shape[0], _ptr(w, ctypes.c_uint32), _ptr(out, ctypes.c_float))
+    return out
 
 
 def normals(seed: int, ids, step: int) -> np.ndarray:

@@ -32,6 +32,36 @@ def test_header_declares_the_boundary():
     assert set(syms) == set(mtpt.EXPORTED)
 
 
+def _declaration_comments():
+    """The comment block right before each declaration, whitespace and the
+    comment's leading asterisks folded."""
+    text = open(os.path.join(ROOT, "include", "mtpt.h")).read()
+    pat = re.compile(r"(/\*(?:(?!\*/).)*\*/)\s*(?:#define[^\n]*\n\s*)*"
+                     r"(?:int|const char\*)\s+(mtpt_[a-z_]+)\s*\(", re.S)
+    out = {}
+    for m in pat.finditer(text):
+        body = re.sub(r"\s*\n\s*\*?", " ", m.group(1))
+        out[m.group(2)] = re.sub(r"\s+", " ", body)
+    return out
+
+
+def test_every_boundary_call_cites_its_passage():
+    """The calls of the method itself name the section or equation of the
+    paper that defines them; every other declaration either cites one, says
+    that it has no counterpart in the paper, or defers to the call it varies
+    ("As mtpt_...")."""
+    com = _declaration_comments()
+    assert set(com) == set(_declared_symbols())
+    for name in ("mtpt_create", "mtpt_set_particles", "mtpt_step", "mtpt_get_masses",
+                 "mtpt_get_positions", "mtpt_create_batch", "mtpt_get_row_sums",
+                 "mtpt_get_pairs", "mtpt_get_info"):
+        assert "Sec." in com[name] or "Eq." in com[name], name
+    for name, c in com.items():
+        cites = "Sec." in c or "Eq." in c
+        other = "no counterpart in the paper" in c.lower() or re.match(r"/\* As mtpt_", c)
+        assert cites or other, name
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in _declared_symbols():
         assert hasattr(lib, name), name

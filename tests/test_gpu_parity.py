@@ -36,6 +36,29 @@ def test_walk_is_bit_exact_with_the_oracle():
     assert g["info"]["pair_count"] == 0 and g["info"]["step"] == 7
 
 
+@pytest.mark.parametrize("seed,step", [(0, 0), (2 ** 64 - 1, 2 ** 64 - 1), (2204037561, 2 ** 32 + 9)])
+def test_walk_takes_its_normals_from_the_library_generator(seed, step):
+    """Hand-picked ids, seeds and steps (counter (id, step lo, step hi, 0),
+    key = seed): each GPU move equals sigma z with z the Box-Muller normals of
+    the words that a third-party Philox4x32-10 gives for that counter."""
+    from philox_library import philox4x32_10 as library_philox
+    ids = np.array([0, 1, 2, 3, 31, 32, 255, 256, 1000], dtype=np.uint32)
+    n = ids.size
+    p = mtpt.Params(dim=3, D=2.0, kappa=1.0, dt=0.1, lo=(0.0,) * 3, hi=(100.0,) * 3, seed=seed)
+    pos = np.full((3, n), 50.0)
+    with mtpt.Simulation(p, pos, np.ones(n)) as sim:
+        sim.set_step(step)
+        sim.step(1)
+        got = sim.positions()
+    ctr = np.stack([ids, np.full(n, step & 0xFFFFFFFF, np.uint32),
+                    np.full(n, step >> 32, np.uint32), np.zeros(n, np.uint32)], axis=1)
+    z = O.box_muller(library_philox(ctr, [seed & 0xFFFFFFFF, seed >> 32]))
+    sigma = np.sqrt(2.0 * 2.0 * 0.1)
+    want = 50.0 + sigma * z[:, :3].T.astype(np.float64)   # one rounding each, no fma
+    assert np.all(np.abs(want - 50.0) < 50.0)              # no wall reached
+    assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("dim", [1, 2, 3])
 def test_walk_with_walls_bit_exact_3d(dim):
     rng = np.random.default_rng(dim)

@@ -1,16 +1,19 @@
 """Pins of the oracle's random-number path (Sec. 3 random walk: xi_i standard
 normal; the generator itself is this project's reading, the paper names none).
 
-Pinned to things other than the oracle: numpy's float64 log/sin/cos (library
-routines) over every input the walk can produce, the N(0,1) distribution
-(Kolmogorov-Smirnov and moments), and the avalanche / uniformity properties
-that a correct 10-round Philox has and a truncated or mis-keyed one lacks.
+Pinned to things other than the oracle: a third-party Philox4x32-10 (PyTorch's
+host-side engine, called as a library routine) word for word over random and
+edge-case counters and keys; numpy's float64 log/sin/cos (library routines)
+over every input the walk can produce; the float64 Box-Muller formula on the
+library's words; the N(0,1) distribution (Kolmogorov-Smirnov and moments);
+and the avalanche / uniformity properties of a correct 10-round Philox.
 """
 import numpy as np
 import pytest
 from scipy import stats
 
 import oracle as O
+from philox_library import philox4x32_10 as library_philox
 
 pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
 
@@ -104,3 +107,51 @@ def test_philox_avalanche_and_uniformity():
     assert chi.pvalue > 1e-4
     # distinct counters give distinct blocks
     assert len({tuple(r) for r in out[:20000].tolist()}) == 20000
+
+
+def _edge_counters():
+    """Counters whose words sit at 0, 1 and 2^32 - 1 in every combination
+    (the carries and wrap-arounds of the round arithmetic)."""
+    vals = np.array([0, 1, 0xFFFFFFFF], dtype=np.uint64)
+    grid = np.stack(np.meshgrid(vals, vals, vals, vals, indexing="ij"), axis=-1)
+    return grid.reshape(-1, 4).astype(np.uint32)
+
+
+def test_philox_matches_an_independent_library_implementation():
+    rng = np.random.default_rng(2204)
+    keys = [np.array([0, 0], np.uint32), np.array([0xFFFFFFFF, 0xFFFFFFFF], np.uint32),
+            np.array([0x243F6A88, 0x85A308D3], np.uint32)]
+    keys += [rng.integers(0, 2 ** 32, size=2, dtype=np.uint64).astype(np.uint32)
+             for _ in range(5)]
+    rand_ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    for key in keys:
+        for ctr in (_edge_counters(), rand_ctr):
+            got = O.philox4x32_10(ctr, key)
+            ref = library_philox(ctr, key)
+            assert np.array_equal(got, ref), (key, np.argwhere(got != ref)[:4])
+    # the walk's counters: (id, step low word, step high word, 0) under the seed
+    ids = np.arange(64, dtype=np.uint32)
+    for seed, step in ((0, 0), (2204037561, 3), (2 ** 64 - 1, 2 ** 64 - 1), (7, 2 ** 32 + 5)):
+        ctr = np.stack([ids, np.full_like(ids, step & 0xFFFFFFFF),
+                        np.full_like(ids, step >> 32), np.zeros_like(ids)], axis=1)
+        key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+        assert np.array_equal(O.philox4x32_10(ctr, key), library_philox(ctr, key))
+
+
+def test_walk_normals_are_box_muller_of_the_library_words():
+    ids = np.arange(0, 5000, 7, dtype=np.uint32)
+    for seed, step in ((0, 0), (2204037561, 41), (2 ** 64 - 1, 2 ** 64 - 1)):
+        ctr = np.stack([ids, np.full_like(ids, step & 0xFFFFFFFF),
+                        np.full_like(ids, step >> 32), np.zeros_like(ids)], axis=1)
+        words = library_philox(ctr, [seed & 0xFFFFFFFF, seed >> 32])
+        z = O.normals(seed, ids, step)
+        assert np.array_equal(z, O.box_muller(words))
+        # the word -> normal map against the Box-Muller formula in float64:
+        # u = ((w >> 8) + 1) 2^-24, radius from words 0 and 2, angle from 1 and 3
+        u = ((words >> np.uint32(8)).astype(np.float64) + 1.0) * 2.0 ** -24
+        rad = np.sqrt(-2.0 * np.log(u[:, [0, 2]]))
+        th = 2.0 * np.pi * u[:, [1, 3]]
+        ref = np.empty((ids.size, 4))
+        ref[:, 0], ref[:, 1] = rad[:, 0] * np.cos(th[:, 0]), rad[:, 0] * np.sin(th[:, 0])
+        ref[:, 2], ref[:, 3] = rad[:, 1] * np.cos(th[:, 1]), rad[:, 1] * np.sin(th[:, 1])
+        assert np.abs(z - ref).max() <= 2e-6 * np.maximum(1.0, np.abs(ref)).max()
