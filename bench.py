@@ -35,7 +35,9 @@ if ROOT not in sys.path:
 from paper_2204_03756_gb300 import mtpt, workloads  # noqa: E402
 
 FORMS = {"fp64": mtpt.MTPT_FP64, "fp32w": mtpt.MTPT_FP32W}
-DTYPE = {"fp64": "f64", "fp32w": "f32+f64acc"}
+# arithmetic of each form: binary64 throughout; or binary32 kernel and
+# weights with compensated binary32 row and flux sums and a binary64 mass update
+DTYPE = {"fp64": "f64", "fp32w": "f32 weights, compensated f32 sums, f64 update"}
 # timed single-run forms: precision form on the --workload workload, or on
 # the 3-d workload for the "_3d" forms
 FORM_WORKLOAD = {"fp32w": None, "fp64": None, "fp32w_3d": "heaviside_3d", "fp64_3d": "heaviside_3d",
@@ -74,8 +76,9 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # DRAM bytes per particle of each kernel from one ncu capture
 # (profiles/step_kernels_gaussian_2d_8M_full.md, gaussian_2d scaled to 8e6
 # particles; traffic grows in proportion to the particles a launch processes,
-# so it is scaled to the bench's launch).  Valid only for the kernel source it
-# was measured on: a different hash of kernels.cuh reports traffic as null.
+# so it is scaled to the bench's launch).  Valid only for the library source
+# it was measured on: a different hash of the CUDA sources and the header
+# reports traffic as null.
 TRAFFIC_DIM = 2
 TRAFFIC_SOURCE_SHA1 = "4b81ead255ff"
 TRAFFIC_BYTES_PER_PARTICLE = {
@@ -116,10 +119,18 @@ BINDING = {
 
 
 def _kernel_source_sha1() -> str:
+    """Hash of everything that shapes a kernel launch: every file of the CUDA
+    sources (kernels and the host code that configures their launches) and
+    the C header."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2204_03756_gb300", "csrc", "kernels.cuh")
-    with open(path, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+    csrc = os.path.join(ROOT, "paper_2204_03756_gb300", "csrc")
+    paths = [os.path.join(csrc, f) for f in sorted(os.listdir(csrc))]
+    paths.append(os.path.join(ROOT, "include", "mtpt.h"))
+    h = hashlib.sha1()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(os.path.basename(path).encode() + b"\0" + f.read())
+    return h.hexdigest()[:12]
 
 
 class ClockSampler:
@@ -686,6 +697,30 @@ def reference_arm(args, w, pos, mass):
                     "d2h_bytes_per_step": 0}}
 
 
+def forms_summary(forms: dict) -> dict:
+    """One compact entry per timed form (binary64, precision form, 3-d,
+    advection, batched, adjoint): step time, throughput, error against the
+    oracle and the dominant kernel's roofline fraction."""
+    out = {}
+    for f, r in forms.items():
+        e = {}
+        for k in ("ms_per_step", "particle_steps_per_s", "pair_interactions_per_s",
+                  "gradient_particle_steps_per_s", "forward_s", "backward_s", "mass_drift_rel"):
+            if r.get(k) is not None:
+                e[k] = float(f"{r[k]:.4g}")
+        err = (r.get("err_vs_oracle") or {}).get("max_rel_err_vs_oracle")
+        if err is not None:
+            e["err_vs_oracle"] = float(f"{err:.3g}")
+        rf = r.get("roofline")
+        if rf:
+            e["roofline"] = {"kernel": rf["kernel"], "bound": rf["bound"],
+                             "frac": float(f"{rf['frac']:.3g}")}
+        if f in FORMS or _base(f) in FORMS:
+            e["dtype"] = DTYPE[_base(f)]
+        out[f] = e
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -753,7 +788,7 @@ def main():
     if not forms:                        # only batched / adjoint requested
         line = {"metric": "particle-steps/s", "unit": "particle-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc",
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE["fp32w"],
                 "data": "synthetic", "forms": {}}
         if batched is not None:
             line.update(value=batched["particle_steps_per_s"], ms_per_step=batched["ms_per_step"],
@@ -799,6 +834,7 @@ def main():
                                             adjoint=adjoint is not None)
         for f, err in line["cpu_baseline"]["parity"].items():
             line["forms"][f]["err_vs_oracle"] = err
+    line["forms_summary"] = forms_summary(line["forms"])   # last key: the line's tail
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

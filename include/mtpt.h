@@ -336,12 +336,21 @@ int mtpt_timing_reset(mtpt_handle* h);
  * walk's generator and `step` is the generator's step counter, so the result
  * equals mtpt_set_particles + mtpt_set_step(step) + mtpt_step(1) on the same
  * state.  params is read as in mtpt_create.  Work is enqueued on `stream`
- * (a cudaStream_t; NULL = legacy default stream) and the call does not wait
- * for it; positions are not range-checked on the device (pass particles
- * inside the box).
+ * (a cudaStream_t; NULL = legacy default stream) and, after the first call
+ * on a device, the call does not wait for it: everything the GPU needs from
+ * the host travels as kernel arguments.
+ *
+ * Errors: the return value covers the arguments and the launches only.
+ * Positions are not range-checked, and a non-finite or out-of-box position
+ * that the step meets is latched in a status word inside the scratch array
+ * that no call reads back, so it goes unreported: pass finite particles
+ * inside the box.
  *
  * Limits: n <= MTPT_NOALLOC_MAX_PARTICLES (65,536); larger n returns
- * MTPT_ERR_TOO_LARGE before any work is enqueued.
+ * MTPT_ERR_TOO_LARGE before any work is enqueued.  The cell grid is capped
+ * at 4 n + 64 cells however sparse the box, so n alone bounds the working
+ * memory: the largest layout (3-d, binary32 form, n = 65,536, the cell cap
+ * reached) needs about 10.5 MiB of the 12.
  *
  * Shared scratch: every call uses the same array, which keeps the last
  * call's contents (each call clears what must start at zero).  Calls whose
@@ -350,8 +359,10 @@ int mtpt_timing_reset(mtpt_handle* h);
  * on one stream.
  *
  * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current and caches it; make that
- * first call on a device before any stream capture begins. */
+ * (cudaGetSymbolAddress) with that device current, caches it, and writes a
+ * 2 KiB table of the binary64 kernel exponential into the array with one
+ * synchronous copy; make that first call on a device before any stream
+ * capture begins. */
 #define MTPT_NOALLOC_MAX_PARTICLES 65536
 #define MTPT_NOALLOC_SCRATCH_BYTES (12u << 20)
 int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t step, double* pos_dev,

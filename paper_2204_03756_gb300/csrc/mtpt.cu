@@ -1890,14 +1890,45 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MTPT_NOALLOC_SCRATCH_BYTES];
 
+// Head of the array, at fixed offsets whatever n is: the binary64 kernel
+// exponential's table (written once per device at set-up) and the per-call
+// words that the init kernel writes.
+struct NoallocHead {
+    double exp_table[kExpTable];
+    RealParams params;
+    int corner_first[2];
+    uint32_t status;
+    unsigned long long pair_counter;
+    unsigned long long step;
+};
+constexpr size_t kNoallocHeadBytes = (sizeof(NoallocHead) + 255) & ~size_t(255);
+
+// Worst case of the per-call pieces carved after the head, at n =
+// MTPT_NOALLOC_MAX_PARTICLES: 3-d binary32 form, 104 bytes per particle
+// (mass copy 8, sorted positions 24 and mass 8, two id arrays 8, key 4,
+// permutation 4, sort key 16, cell 4, rec 16, mass split 8, row sum 4); the
+// cell grid capped at 4 n + 64 cells (setup_grid), so count and start hold at
+// most that many plus one cells padded to a scan tile, and the corner tables
+// at most the sum of the per-axis cell counts (<= their product + 2); each
+// piece rounded up to 256 bytes.
+constexpr size_t kNoallocMaxCells = 4 * size_t(MTPT_NOALLOC_MAX_PARTICLES) + 64;
+constexpr size_t kNoallocMaxCellsPad = (kNoallocMaxCells + 1 + kScanTile - 1) / kScanTile * kScanTile;
+constexpr size_t kNoallocWorstBytes =
+    kNoallocHeadBytes + 104 * size_t(MTPT_NOALLOC_MAX_PARTICLES) +
+    2 * sizeof(uint32_t) * kNoallocMaxCellsPad + sizeof(uint32_t) * (kNoallocMaxCellsPad / kScanTile) +
+    sizeof(float2) * (kNoallocMaxCells + 2) + 16 * 256;
+static_assert(kNoallocWorstBytes <= size_t(MTPT_NOALLOC_SCRATCH_BYTES),
+              "the no-allocation scratch must hold the largest layout n allows");
+
 constexpr int kNoallocMaxDevices = 64;
 void* g_noalloc_addr[kNoallocMaxDevices] = {};
 std::once_flag g_noalloc_once[kNoallocMaxDevices];
 cudaError_t g_noalloc_err[kNoallocMaxDevices] = {};
 
 // The array's device address on the current device, looked up once per
-// device.  In host code `g_noalloc_scratch` names a host-side stand-in, never
-// a device address, so kernels only ever receive the looked-up pointer.
+// device (with its exponential table written there at the same time).  In
+// host code `g_noalloc_scratch` names a host-side stand-in, never a device
+// address, so kernels only ever receive the looked-up pointer.
 int noalloc_scratch(void** out) {
     int dev = -1;
     MTPT_CUDA_TRY(cudaGetDevice(&dev));
@@ -1905,6 +1936,9 @@ int noalloc_scratch(void** out) {
     std::call_once(g_noalloc_once[dev], [dev]() {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(static_cast<NoallocHead*>(p)->exp_table, exp_table_host(),
+                           kExpTable * sizeof(double), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) (void)cudaGetLastError();
         g_noalloc_err[dev] = e;
         g_noalloc_addr[dev] = (e == cudaSuccess) ? p : nullptr;
@@ -1914,10 +1948,23 @@ int noalloc_scratch(void** out) {
     return MTPT_OK;
 }
 
-// Bump carving of the scratch array into 256-byte-aligned pieces.
+// The per-call words of the head, from kernel arguments (taken by value at
+// launch, so nothing on the host is read after the call returns).
+__global__ void k_noalloc_init(RealParams p, int n_corners, unsigned long long step,
+                               NoallocHead* head) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    head->params = p;
+    head->corner_first[0] = 0;
+    head->corner_first[1] = n_corners;
+    head->status = 0u;
+    head->pair_counter = 0ull;
+    head->step = step;
+}
+
+// Bump carving of the rest of the array into 256-byte-aligned pieces.
 struct Carver {
     unsigned char* base;
-    size_t used = 0;
+    size_t used = kNoallocHeadBytes;
     bool overflow = false;
     template <typename T>
     T* take(size_t count) {
@@ -1958,6 +2005,11 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     const int d = h.dim;
     const size_t cells_pad = size_t(h.n_cells_pad);
 
+    NoallocHead* head = static_cast<NoallocHead*>(scratch);
+    h.exp_table.p = head->exp_table;
+    h.status.p = &head->status;
+    h.pair_counter.p = &head->pair_counter;
+    h.step_dev.p = &head->step;
     Carver cv{static_cast<unsigned char*>(scratch)};
     double* mass_in = cv.take<double>(size_t(n));
     double* pos_sorted = cv.take<double>(size_t(d) * size_t(n));
@@ -1979,12 +2031,6 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.count.p = cv.take<uint32_t>(cells_pad);
     h.start.p = cv.take<uint32_t>(cells_pad);
     h.tile_sums.p = cv.take<uint32_t>(cells_pad / kScanTile);
-    h.exp_table.p = cv.take<double>(kExpTable);
-    h.status.p = cv.take<uint32_t>(1);
-    h.pair_counter.p = cv.take<unsigned long long>(1);
-    h.step_dev.p = cv.take<unsigned long long>(1);
-    RealParams* params_dev = cv.take<RealParams>(1);
-    int* corner_first = cv.take<int>(2);
     if (cv.overflow) return MTPT_ERR_TOO_LARGE;
 
     // The handle's buffer pairs: index 0 is the caller's state (positions are
@@ -2000,25 +2046,17 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.have_particles = true;
 
     cudaStream_t st = h.stream;
-    // what must start at zero: cell counts, status word, pair counter
+    // what must start at zero (cell counts, status word, pair counter) and the
+    // call's parameters, step and corner offsets, all from device-side work
     if (h.any_transfer)
         MTPT_CUDA_TRY(cudaMemsetAsync(h.count.p, 0, cells_pad * sizeof(uint32_t), st));
-    MTPT_CUDA_TRY(cudaMemsetAsync(h.status.p, 0, sizeof(uint32_t), st));
-    MTPT_CUDA_TRY(cudaMemsetAsync(h.pair_counter.p, 0, sizeof(unsigned long long), st));
-    k_set_step<<<1, 1, 0, st>>>(h.step_dev.p, (unsigned long long)step);
-    MTPT_CUDA_TRY(cudaMemcpyAsync(h.exp_table.p, exp_table_host(), kExpTable * sizeof(double),
-                                  cudaMemcpyHostToDevice, st));
-    // the one-entry realisation table and corner offsets for the corner kernel
-    static thread_local int first_host[2];
-    first_host[0] = 0;
-    first_host[1] = h.n_corners;
-    MTPT_CUDA_TRY(cudaMemcpyAsync(params_dev, h.params, sizeof(RealParams), cudaMemcpyHostToDevice, st));
-    MTPT_CUDA_TRY(cudaMemcpyAsync(corner_first, first_host, sizeof(first_host), cudaMemcpyHostToDevice, st));
+    k_noalloc_init<<<1, 32, 0, st>>>(h.params[0], h.n_corners, (unsigned long long)step, head);
+    MTPT_CUDA_TRY(cudaGetLastError());
     MTPT_CUDA_TRY(cudaMemcpyAsync(mass_in, mass_dev, size_t(n) * sizeof(double),
                                   cudaMemcpyDeviceToDevice, st));
     k_iota<<<grid_for(n), kBlock, 0, st>>>(int(n), id_in);
     MTPT_CUDA_TRY(cudaGetLastError());
-    MTPT_TRY(build_corners(&h, params_dev, corner_first));
+    MTPT_TRY(build_corners(&h, &head->params, head->corner_first));
     MTPT_TRY(dispatch_step(&h, MTPT_DO_WALK | MTPT_DO_TRANSFER));
     // masses back to the caller's order; positions are already there
     k_unpermute<double><<<grid_for(n), kBlock, 0, st>>>(int(n), h.cap, 1, h.id[h.cur].p,
