@@ -45,11 +45,11 @@ def test_walk_takes_its_normals_from_the_library_generator(seed, step):
     ids = np.array([0, 1, 2, 3, 31, 32, 255, 256, 1000], dtype=np.uint32)
     n = ids.size
     p = mtpt.Params(dim=3, D=2.0, kappa=1.0, dt=0.1, lo=(0.0,) * 3, hi=(100.0,) * 3, seed=seed)
-    pos = np.full((3, n), 50.0)
-    with mtpt.Simulation(p, pos, np.ones(n)) as sim:
+    total = int(ids.max()) + 1                 # particle i carries generator id i
+    with mtpt.Simulation(p, np.full((3, total), 50.0), np.ones(total)) as sim:
         sim.set_step(step)
         sim.step(1)
-        got = sim.positions()
+        got = sim.positions()[:, ids]
     ctr = np.stack([ids, np.full(n, step & 0xFFFFFFFF, np.uint32),
                     np.full(n, step >> 32, np.uint32), np.zeros(n, np.uint32)], axis=1)
     z = O.box_muller(library_philox(ctr, [seed & 0xFFFFFFFF, seed >> 32]))
