@@ -276,6 +276,113 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
     }
 
 
+def time_split(w, pos, mass, form, steps, warmup, rank, world, dist, e2e_steps):
+    """One domain cut into a checkerboard of `world` tiles (Secs. 4-5), one
+    tile per rank: every step walks each tile's natives, exchanges the
+    migrating particles and the 2 psi ghost pads with one all-to-all (NCCL
+    on device buffers) and runs the mass transfer.  The whole job processes
+    the workload's n particles per step whatever the number of ranks
+    ("scaling": "strong").  `e2e` loads the tile's natives from pinned host
+    memory before every step and reads its masses back after it."""
+    import torch
+    from paper_2204_03756_gb300 import ddc
+    p = _params(w, form, 0)
+    tiles = mtpt.mtpt_tiling_factors(w.dim, w.lo, w.hi, world)
+    mine = ddc.tile_of(pos, w.lo, w.hi, tiles) == rank
+    ids = np.flatnonzero(mine).astype(np.uint32)
+    my_pos, my_mass = np.ascontiguousarray(pos[:, mine]), np.ascontiguousarray(mass[mine])
+
+    class _One:                            # a single rank: no exchange partner
+        def get_rank(self): return 0
+        def get_world_size(self): return 1
+        def get_backend(self): return "nccl"
+        def all_to_all_single(self, out, inp, out_split=None, in_split=None): out.copy_(inp)
+    group = dist if dist is not None else _One()
+    sd = ddc.Subdomain(p, w.n, my_pos, my_mass, ids, group, tiles)
+    stream = torch.cuda.current_stream()
+    try:
+        sd.step(warmup)
+        torch.cuda.synchronize()
+        pairs0 = sd.info()["pair_count"]
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        time.sleep(0.3)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sd.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        pairs = sd.info()["pair_count"] - pairs0
+        # second pass with per-kernel events: the launches of a step
+        mtpt.mtpt_timing_reset(sd.h)
+        mtpt.mtpt_timing_enable(sd.h, True)
+        sd.step(steps)
+        kstats = mtpt.mtpt_timing_read(sd.h)
+        mtpt.mtpt_timing_enable(sd.h, False)
+        # end to end: natives in from pinned host memory, one step, masses out
+        lib = mtpt.load()
+        pin_pos = torch.from_numpy(my_pos).pin_memory()
+        pin_mass = torch.from_numpy(my_mass).pin_memory()
+        pin_ids = torch.from_numpy(ids.view(np.int32)).pin_memory()
+        out = torch.empty(max(1, 2 * len(ids)), dtype=torch.float64).pin_memory()
+        h2d = d2h = 0
+
+        def e2e_step():
+            nonlocal h2d, d2h
+            rc = lib.mtpt_set_particles_tile(sd.h, len(ids), pin_pos.data_ptr(),
+                                             pin_mass.data_ptr(), pin_ids.data_ptr())
+            if rc:
+                raise mtpt.MtptError(rc, "mtpt_set_particles_tile")
+            sd.step(1)
+            n_now = sd.info()["n"]
+            if n_now > out.numel():
+                raise RuntimeError("e2e output buffer too small")
+            rc = lib.mtpt_get_masses(sd.h, out.data_ptr())
+            if rc:
+                raise mtpt.MtptError(rc, "mtpt_get_masses")
+            h2d += pin_pos.numel() * 8 + pin_mass.numel() * 8 + pin_ids.numel() * 4
+            d2h += n_now * 8
+
+        for _ in range(3):
+            e2e_step()
+        h2d = d2h = 0
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3
+    finally:
+        sd.close()
+    max_ms, pairs_all = reduce_over_ranks(ms, pairs, dist)
+    e2e_max, _ = reduce_over_ranks(e2e_ms, 0.0, dist)
+    io, _ = reduce_over_ranks(0.0, float(h2d + d2h), dist)
+    sec = max_ms / 1e3
+    return {
+        "form": form, "workload": w.name, "n": w.n, "ms": max_ms, "ms_per_step": max_ms / steps,
+        "particle_steps_per_s": w.n * steps / sec,
+        "pair_interactions_per_s": pairs_all / sec,
+        "pairs_per_particle_step": pairs_all / (w.n * steps), "clocks": clocks,
+        "tiles": list(tiles), "kernels": kstats,
+        "launches_per_step": sum(v[0] for v in kstats.values()) / steps,
+        "e2e": {"value": w.n * e2e_steps / (e2e_max / 1e3), "unit": "particle-steps/s",
+                "ms_per_step": e2e_max / e2e_steps, "steps": e2e_steps,
+                "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "api": "mtpt_set_particles_tile + tile step + mtpt_get_masses per step"},
+    }
+
+
 def time_batched(steps, warmup, rank, world, dist, nreal=512, autotune_steps=4):
     """The ensemble workload (independent 2-d realisations with uneven counts,
     densities and D) in the precision form, one launch per kernel per step
@@ -736,6 +843,9 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="scale the workload to n particles at the same density "
                          "(profiling runs; the default is the workload's own size)")
+    ap.add_argument("--split", default="auto", choices=["auto", "on", "off"],
+                    help="one domain cut into one tile per rank (auto: with more than "
+                         "one rank); off: independent replicas per rank")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -776,6 +886,33 @@ def main():
             states[name] = (wf,) + tuple(workloads.initial_state(wf))
         return states[name]
 
+    split = args.split == "on" or (args.split == "auto" and world > 1)
+    if split:
+        f = forms[0] if forms else "fp32w"
+        r = time_split(w, pos, mass, f, args.steps, args.warmup, rank, world, dist,
+                       args.e2e_steps)
+        e2e = dict(r.pop("e2e"))
+        line = {
+            "metric": "particle-steps/s", "value": r["particle_steps_per_s"],
+            "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": DTYPE[_base(f)], "data": "synthetic",
+            "config": dict(workload_config(w, f, world),
+                           parallelism=f"checkerboard {'x'.join(map(str, r['tiles']))}"),
+            "pair_interactions_per_s": r["pair_interactions_per_s"],
+            "gpu_launches": int(round(r["launches_per_step"] * args.steps)),
+            "clocks": r.pop("clocks"), "e2e": e2e, "split": r,
+        }
+        # host copies per step of the whole job: every rank's natives in, masses out
+        e2e["h2d_bytes_per_step"] = int(pos.nbytes + mass.nbytes + 4 * w.n)
+        e2e["d2h_bytes_per_step"] = int(mass.nbytes)
+        if rank == 0:
+            print(json.dumps(line))
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
     results = {}
     for f in forms:
         wf, pf, mf = state_of(f)

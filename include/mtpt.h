@@ -426,6 +426,101 @@ int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out);
  * Synchronises. */
 int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen);
 
+/* Split domain (Secs. 4-5): one handle per tile of a checkerboard over the
+ * box, the tiles exchanging particles once per time step.
+ *
+ * The box is cut into tiles[a] equal slabs per axis (Sec. 4.2); a particle
+ * is native to the tile that contains it (coordinate a in tile
+ * floor((x_a - lo_a) / width_a), clamped to the last tile at the upper
+ * wall).  Besides its natives a tile holds, for the mass transfer, ghost
+ * copies of the particles of other tiles within a pad of its box (Sec. 5).
+ * The pad is 2 psi (the paper's is psi): every ghost within psi of the tile
+ * then has all its own neighbours in the tile too, so its row sum, which
+ * enters the weights W_ij of the natives it touches, is the undivided run's.
+ * The tile's cell grid is the undivided run's grid restricted to the tile
+ * and its pad, so with ghosts exchanged every step the natives' positions,
+ * masses and pair counts are those of one handle holding all n_global
+ * particles, bit for bit (the paper's equivalence of the decomposed and the
+ * single-domain runs, Sec. 5).  Only natives walk and only natives' masses
+ * are kept (Sec. 5).  Generator ids are global, below 2^31.
+ *
+ * One time step of every tile:
+ *   mtpt_step_ex(h, 1, MTPT_DO_WALK);            walk the natives
+ *   mtpt_tile_pack(h, cap, send, counts);         records for the other tiles
+ *   (the caller moves the records between tiles: all-to-all)
+ *   mtpt_tile_transfer(h, n_recv, recv);          mass transfer, natives kept
+ * A record is dim + 2 doubles: the coordinates, the mass, the generator id
+ * (an integer-valued double).
+ *
+ * A tiled handle is a single realisation; it refuses the calls that need
+ * its whole particle set at once (mtpt_step / mtpt_step_ex with
+ * MTPT_DO_TRANSFER, the other loads, mtpt_get_pairs, tuning, autotuning, the
+ * adjoint) with MTPT_ERR_STATE.  mtpt_get_masses / mtpt_get_positions /
+ * mtpt_get_ids give its natives in the handle's own order, which changes
+ * from step to step; mtpt_get_info's n and pair_count are the natives'. */
+
+/* Tiles per axis of a checkerboard of `ntiles` tiles over the box [lo, hi]
+ * of `dim` axes, into factors[3] (1 on unused axes).  Defining passage:
+ * Eq. "minimization" (Sec. 4.2) in 2-d: f1 <= f2 with f1 f2 = ntiles and
+ * |f2 / f1 - A| least for the box's aspect ratio A >= 1, the longer side
+ * cut into f2 tiles (the smallest f1 among equals).  In 3-d, where the paper
+ * asks only for tiles closest to cubes, the triple whose largest tile edge
+ * over its smallest is least (the first in lexicographic order among
+ * equals); in 1-d, ntiles slices (Sec. 4.1).  Host arithmetic only. */
+int mtpt_tiling_factors(int32_t dim, const double* lo, const double* hi, int32_t ntiles,
+                        int32_t* factors);
+
+/* Tile of a checkerboard. */
+typedef struct mtpt_tiling {
+    int32_t tiles[3];       /* tiles per axis (1 on unused axes) */
+    int32_t tile;           /* this tile: t0 + tiles[0] (t1 + tiles[1] t2) */
+    int64_t n_global;       /* particles in the whole box (fixes the cell grid) */
+} mtpt_tiling;
+
+/* Make h (a single realisation without particles; MTPT_ERR_STATE otherwise)
+ * hold one tile of a checkerboard over its box (the subdomains of Sec. 4.2
+ * with the ghost pad of Sec. 5).  Every tile must
+ * be at least the pad 2 psi wide on each axis cut into more than one tile
+ * (MTPT_ERR_INVALID_ARG otherwise); n_global must be below 2^31. */
+int mtpt_set_tiling(mtpt_handle* h, const mtpt_tiling* t);
+
+/* Load the tile's natives from HOST buffers: pos (dim x n SoA), mass (n),
+ * ids (n global generator ids).  Defining passage: the particle state of
+ * Sec. 2.1 and Sec. 3, of one subdomain (Sec. 4).  Every particle must be
+ * native to the tile (MTPT_ERR_OUT_OF_DOMAIN otherwise), every mass finite
+ * and, in the precision form, at most 1e30 in magnitude, every id below
+ * 2^31 (MTPT_ERR_INVALID_ARG otherwise); a rejected load leaves the handle
+ * without particles.  Resets the step and pair counters.  Syncs. */
+int mtpt_set_particles_tile(mtpt_handle* h, int64_t n, const double* pos, const double* mass,
+                            const uint32_t* ids);
+
+/* After the walk of a step: pack, for every other tile, the particles it
+ * owns or holds in its pad (Sec. 5) into the DEVICE buffer send_dev of `cap`
+ * records -- tile 0's first, then tile 1's and so on, each tile's natives
+ * before its ghosts -- and keep this tile's own share on the device for
+ * mtpt_tile_transfer.  counts (HOST, 2 x number of tiles) receives for tile t
+ * the natives counts[2 t] and ghosts counts[2 t + 1] packed for it; this
+ * tile's own entries count what it keeps, and nothing is packed for it.
+ * When the records exceed cap, nothing is packed, counts still holds the
+ * numbers, and MTPT_ERR_CAPACITY is returned: call again with a larger
+ * buffer.  The packed buffer is complete when the handle's stream reaches
+ * this point.  Syncs once (for the counts). */
+int mtpt_tile_pack(mtpt_handle* h, int64_t cap, double* send_dev, int64_t* counts);
+
+/* Finish a step: the tile's set is what mtpt_tile_pack kept plus the n_recv
+ * records received from the other tiles (DEVICE buffer, any order); the
+ * mass transfer of Sec. 3 runs on natives and ghosts alike, then the ghosts
+ * are dropped (Sec. 5: only natives are updated).  A received record outside
+ * the tile's pad box or with a bad id gives MTPT_ERR_INVALID_ARG (it was
+ * treated as a ghost and changed no native).  Syncs once. */
+int mtpt_tile_transfer(mtpt_handle* h, int64_t n_recv, const double* recv_dev);
+
+/* Generator ids of the particles in the order mtpt_get_masses and
+ * mtpt_get_positions use, to a HOST buffer of n: i for particle i of a plain
+ * handle, the global ids of a tile's natives.  Identification: no
+ * counterpart in the paper.  Syncs. */
+int mtpt_get_ids(mtpt_handle* h, uint32_t* out);
+
 /* Human-readable text of a status code (static storage).  Error reporting:
  * no counterpart in the paper. */
 const char* mtpt_status_string(int status);

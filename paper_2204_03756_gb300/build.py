@@ -44,8 +44,11 @@ def nvcc_path() -> str:
 
 
 def build_command(out_path: str = LIB_PATH, extra=()) -> list:
+    # host code without contraction into fused multiply-adds: the same host
+    # arithmetic (grid and tile tables) on x86 and Arm builds
     return [nvcc_path(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17",
-            "-Xcompiler", "-fPIC", "-shared", "-I", INCLUDE_DIR, *extra,
+            "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-shared", "-I",
+            INCLUDE_DIR, *extra,
             "-o", out_path, os.path.join(SRC_DIR, "mtpt.cu")]
 
 

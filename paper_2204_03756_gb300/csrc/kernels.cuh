@@ -30,6 +30,10 @@ namespace mtpt {
 
 enum : uint32_t { kStatusNonFinite = 1u, kStatusOutOfDomain = 2u };
 
+// Generator ids are below 2^31; a tile marks its ghost copies of other tiles'
+// particles with this bit (see tiles.cuh).
+constexpr uint32_t kGhostBit = 0x80000000u;
+
 // Bounds-checked build (compiled with -DMTPT_CHECKED; the tests load it as a
 // second library): index invariants that hold by construction are verified at
 // run time; a violation sets its bit in a device word and the access is
@@ -62,7 +66,10 @@ struct Box {
 };
 
 struct Grid {
-    int n[3];          // cells per axis (1 on unused axes)
+    int n[3];          // cells per axis of this grid (1 on unused axes)
+    int nglob[3];      // cells per axis of the whole box's grid (equal to n unless
+                       // the grid is one tile's part of it)
+    int off[3];        // global index of this grid's first cell per axis (0 unless tiled)
     double lo[3];      // lower corner of the box
     double w[3];       // cell width per axis, >= psi
     double inv_w[3];   // 1 / w
@@ -238,12 +245,15 @@ __device__ __forceinline__ uint32_t cell_of(const double* x, const Grid& g, bool
             float hi, lo;
             split_double(x[a], &hi, &lo);
             const float u = __fmul_rn(__fsub_rn(hi, g.lo_f[a]), g.inv_w_f[a]);
-            if (!not_finite(x[a])) c = clamp_cell(u, g.n[a]);
+            if (!not_finite(x[a])) c = clamp_cell(u, g.nglob[a]);
         } else {
             const double u = __dmul_rn(__dsub_rn(x[a], g.lo[a]), g.inv_w[a]);
-            if (u == u) c = u <= 0.0 ? 0 : (u >= double(g.n[a] - 1) ? g.n[a] - 1 : __double2int_rz(u));
+            if (u == u) c = u <= 0.0 ? 0 : (u >= double(g.nglob[a] - 1) ? g.nglob[a] - 1 : __double2int_rz(u));
             else *bad = true;
         }
+        // the whole box's cell index, then this grid's part of it
+        c -= g.off[a];
+        c = c < 0 ? 0 : (c >= g.n[a] ? g.n[a] - 1 : c);
         if (not_finite(x[a])) *bad = true;
         lin += uint32_t(c) * mult;
         mult *= uint32_t(g.n[a]);
@@ -391,7 +401,7 @@ __global__ void k_corners(int total, int nreal, int dim, const RealParams* __res
     int a = 0;
     while (a + 1 < dim && t >= g.corner_off[a + 1]) ++a;
     const int c = t - g.corner_off[a];
-    const double corner = __dadd_rn(g.lo[a], __dmul_rn(double(c), g.w[a]));
+    const double corner = __dadd_rn(g.lo[a], __dmul_rn(double(c + g.off[a]), g.w[a]));
     const float hi_f = __double2float_rn(corner);
     out[t] = make_float2(hi_f, __double2float_rn(__dsub_rn(corner, double(hi_f))));
 }
@@ -554,12 +564,13 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
     const uint32_t b = start[c], e = start[c + 1];
     if (!check(b <= uint32_t(s) && uint32_t(s) < e && e <= uint32_t(n), kChkGather)) return;
     const long long my_x = order_key(me.x);
+    const uint32_t my_rank_id = my_id & ~kGhostBit;   // ghosts rank by their own id
     uint32_t rank = 0;
     for (uint32_t k = b; k < e; ++k) {
         const double2 q = sortkey[k];
         const long long xo = order_key(q.x);
-        const uint32_t ido = uint32_t(__double_as_longlong(q.y));
-        rank += (xo < my_x || (xo == my_x && ido < my_id)) ? 1u : 0u;
+        const uint32_t ido = uint32_t(__double_as_longlong(q.y)) & ~kGhostBit;
+        rank += (xo < my_x || (xo == my_x && ido < my_rank_id)) ? 1u : 0u;
     }
     const uint32_t dst = b + rank;
     if (!check(dst < e, kChkGather)) return;
@@ -665,12 +676,13 @@ k_gather_rec(int n, int64_t stride, const double2* __restrict__ recs,
     const uint32_t b = start[c], e = start[c + 1];
     if (!check(b <= uint32_t(s) && uint32_t(s) < e && e <= uint32_t(n), kChkGather)) return;
     const long long my_x = order_key(lane[0]);
+    const uint32_t my_rank_id = my_id & ~kGhostBit;   // ghosts rank by their own id
     uint32_t rank = 0;
     for (uint32_t k = b; k < e; ++k) {
         const double2 q = recs[size_t(k) * R::kChunks];
         const long long xo = order_key(q.x);
-        const uint32_t ido = uint32_t(__double_as_longlong(q.y));
-        rank += (xo < my_x || (xo == my_x && ido < my_id)) ? 1u : 0u;
+        const uint32_t ido = uint32_t(__double_as_longlong(q.y)) & ~kGhostBit;
+        rank += (xo < my_x || (xo == my_x && ido < my_rank_id)) ? 1u : 0u;
     }
     const uint32_t dst = b + rank;
     if (!check(dst < e, kChkGather)) return;
@@ -1023,6 +1035,16 @@ struct NbList {
 };
 using NbList64 = NbList<double>;
 
+// Precision-form neighbour lists: pass 1 stores each accepted neighbour
+// j != s with its binary32 kernel value as {j, K bits} in slot k of s (entry
+// at k * stride + s); count[s] is the full number.  Pass 2 of a warp whose
+// lanes all fit their lists walks them instead of searching.
+struct NbList32 {
+    uint2* e;
+    uint32_t* count;
+    int cap;           // 0: no list
+};
+
 // Phases A-C for the calling warp (every lane of the warp must call it; lanes
 // with valid = false walk nothing).  eval(owner_s, j, d2f) returns the pair
 // term (d2f is 0 unless D2); add(term) is called by each lane for its own
@@ -1195,7 +1217,7 @@ k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
              const double* __restrict__ exp_table, const __grid_constant__ View v,
              double* __restrict__ r_out, unsigned long long* __restrict__ pair_counter,
-             NbList64 nb) {
+             NbList64 nb, const uint32_t* __restrict__ ghost_id) {
     __shared__ double table[kExpTable];
     __shared__ SegShared<kWarpsPerBlock, double, false> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
@@ -1213,7 +1235,9 @@ k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4
         [&](double K) { r = __dadd_rn(r, K); }, nb);
     if (s < n) r_out[s] = r;
     if (nb.cap > 0 && s < n) nb.count[s] = valid ? cnt : 0u;
-    add_pair_count(valid ? cnt : 0u, pair_counter);
+    // with ghost_id (a tile), pairs are counted for the tile's own particles only
+    const bool counted = valid && !(ghost_id && (ghost_id[s] & kGhostBit));
+    add_pair_count(counted ? cnt : 0u, pair_counter);
 }
 
 // Pass 2, binary64 form: M'_s = M_s + beta sum_j (M_j - M_s) 2 K_sj / (r_s + r_j).
@@ -1258,35 +1282,49 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
 }
 
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
-// hardware ex2, compensated binary32 row sum, rounded to binary32 into r_out.
+// hardware ex2, compensated binary32 row sum, rounded to binary32 into r_out;
+// with nb.cap > 0 also the neighbour lists of pass 2 (accepted j != s with
+// their K, in visiting order: the band's exact accepts come last).
 template <int DIM, class View, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (DIM == 3 ? 1536 : 2048) / BLOCK)
 k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
              const __grid_constant__ View v, float* __restrict__ r_out,
-             unsigned long long* __restrict__ pair_counter) {
+             unsigned long long* __restrict__ pair_counter,
+             const uint32_t* __restrict__ ghost_id, NbList32 nb) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cnt = 0;
     if (s < n) {
         const RealParams& P = v.of_sorted(uint32_t(s));
         float rsum = 0.0f, rc = 0.0f;
+        uint32_t listed = 0;
         if (P.transfer) {
             const float na = -P.pp.a_log2e;
+            const uint32_t cap = uint32_t(nb.cap);
+            uint2* lp = nb.e + s;          // slot `listed` of s
             scan_neighbours<DIM, true>(uint32_t(s), cell[s], stride, rec, pos, start, P,
-                                 [&](uint32_t, float d2f, bool accept) {
+                                 [&](uint32_t j, float d2f, bool accept) {
                                      // Kahan step, kept only for accepted pairs
-                                     const float y = __fsub_rn(ex2_approx(na * d2f), rc);
+                                     const float K = ex2_approx(na * d2f);
+                                     const float y = __fsub_rn(K, rc);
                                      const float t = __fadd_rn(rsum, y);
                                      const float cn = __fsub_rn(__fsub_rn(t, rsum), y);
                                      rsum = accept ? t : rsum;
                                      rc = accept ? cn : rc;
                                      cnt += accept ? 1u : 0u;
+                                     const bool keep = accept && j != uint32_t(s);
+                                     if (keep && listed < cap) *lp = make_uint2(j, __float_as_uint(K));
+                                     if (keep) lp += stride;
+                                     listed += keep ? 1u : 0u;
                                  });
             cnt -= 1;   // the self pair
         } else {
             rsum = 1.0f;
         }
+        if (nb.cap > 0) nb.count[s] = listed;
         r_out[s] = __fsub_rn(rsum, rc);
+        // with ghost_id (a tile), pairs are counted for the tile's own particles only
+        if (ghost_id && (ghost_id[s] & kGhostBit)) cnt = 0;
     }
     add_pair_count(cnt, pair_counter);
 }
@@ -1294,13 +1332,63 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
 // Pass 2, precision form: W = 2K / (r_s + r_j) in binary32 (symmetric bit for
 // bit), mass difference from the binary32 head/tail split (exactly
 // antisymmetric), flux accumulated with compensation, update in binary64.
+// The flux sum of pass 2, precision form: W = 2 beta K / (r_s + r_j) in
+// binary32 (symmetric bit for bit), the mass difference from the binary32
+// head/tail split (exactly antisymmetric), compensated accumulation, and the
+// update in binary64.
+struct FluxSum {
+    float rs, two_beta;
+    float2 ms;
+    float acc = 0.0f, comp = 0.0f;
+    __device__ __forceinline__ void add(const float* __restrict__ r,
+                                        const float2* __restrict__ msplit, uint32_t j, float K,
+                                        bool accept = true) {
+        const float W = __fdividef(two_beta * K, __fadd_rn(rs, __ldg(r + j)));
+        const float2 mj = __ldg(msplit + j);
+        const float dm = __fadd_rn(__fsub_rn(mj.x, ms.x), __fsub_rn(mj.y, ms.y));
+        // a rejected candidate (and the self pair) adds an exact zero
+        neumaier_add(acc, comp, accept ? __fmul_rn(dm, W) : 0.0f);
+    }
+    // two binary64 additions per particle: acc + comp is exact in binary64
+    __device__ __forceinline__ double delta() const {
+        return __dadd_rn(f32_to_f64(acc), f32_to_f64(comp));
+    }
+};
+
+// Pass 2 of one particle by search, as pass 1 visited its candidates (the
+// band's exact accepts last), for a particle whose list overflowed or when
+// there are no lists.  A real call, so its registers do not weigh on the
+// list loop.
+template <int DIM, class View>
+__device__ __noinline__ float2 search_flux(uint32_t s, int64_t stride,
+                                           const double* __restrict__ pos,
+                                           const float4* __restrict__ rec,
+                                           const uint32_t* __restrict__ cell,
+                                           const uint32_t* __restrict__ start, const View& v,
+                                           const float* __restrict__ r,
+                                           const float2* __restrict__ msplit, float rs, float2 ms,
+                                           float two_beta) {
+    const RealParams& P = v.of_sorted(s);
+    const float na = -P.pp.a_log2e;
+    FluxSum g{rs, two_beta, ms};
+    scan_neighbours<DIM, true>(s, cell[s], stride, rec, pos, start, P,
+                         [&](uint32_t j, float d2f, bool accept) {
+                             g.add(r, msplit, j, ex2_approx(na * d2f), accept);
+                         });
+    return make_float2(g.acc, g.comp);
+}
+
+// Pass 2, precision form: each particle walks its neighbour list (the
+// accepted neighbours only, with pass 1's K), or searches when it has none
+// (no lists, or an overflowing one).  Both add the same terms in the same
+// order.
 template <int DIM, class View, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (DIM == 3 ? 1536 : 2048) / BLOCK)
+__global__ void __launch_bounds__(BLOCK, 2048 / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
                const __grid_constant__ View v, const float* __restrict__ r,
                const float2* __restrict__ msplit, const double* __restrict__ mass,
-               double* __restrict__ mass_out) {
+               double* __restrict__ mass_out, NbList32 nb) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const RealParams& P = v.of_sorted(uint32_t(s));
@@ -1308,23 +1396,21 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
         mass_out[s] = mass[s];
         return;
     }
-    const float rs = r[s];
-    const float2 ms = msplit[s];
-    float acc = 0.0f, comp = 0.0f;
-    const float na = -P.pp.a_log2e;
-    const float two_beta = float(2.0 * P.pp.beta);   // beta folded into W (still symmetric)
-    scan_neighbours<DIM, false>(uint32_t(s), cell[s], stride, rec, pos, start, P,
-                         [&](uint32_t j, float d2f, bool accept) {
-                             const float K = ex2_approx(na * d2f);
-                             const float W = __fdividef(two_beta * K, __fadd_rn(rs, __ldg(r + j)));
-                             const float2 mj = __ldg(msplit + j);
-                             const float dm = __fadd_rn(__fsub_rn(mj.x, ms.x), __fsub_rn(mj.y, ms.y));
-                             // a rejected candidate adds an exact zero: no change
-                             neumaier_add(acc, comp, accept ? __fmul_rn(dm, W) : 0.0f);
-                         });
-    // two binary64 additions per particle: acc + comp is exact in binary64
-    const double delta = __dadd_rn(f32_to_f64(acc), f32_to_f64(comp));
-    mass_out[s] = __dadd_rn(mass[s], delta);
+    FluxSum f{r[s], float(2.0 * P.pp.beta), msplit[s]};   // beta folded into W (still symmetric)
+    const uint32_t listed = nb.cap > 0 ? nb.count[s] : 0xffffffffu;
+    if (listed <= uint32_t(nb.cap)) {
+        const uint2* e = nb.e + s;
+        for (uint32_t k = 0; k < listed; ++k, e += stride) {
+            const uint2 q = __ldg(e);
+            f.add(r, msplit, q.x, __uint_as_float(q.y));
+        }
+    } else {
+        const float2 sum = search_flux<DIM>(uint32_t(s), stride, pos, rec, cell, start, v, r,
+                                            msplit, f.rs, f.ms, f.two_beta);
+        f.acc = sum.x;
+        f.comp = sum.y;
+    }
+    mass_out[s] = __dadd_rn(mass[s], f.delta());
 }
 
 // Test support: every accepted ordered pair j != s as (id_s, id_j).

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -24,6 +25,7 @@
 #include "../../include/mtpt.h"
 #include "kernels.cuh"
 #include "hostio.cuh"
+#include "tiles.cuh"
 
 using namespace mtpt;
 
@@ -33,10 +35,19 @@ constexpr int kMaxDim = 3;
 constexpr int64_t kGraphMinSteps = 4;   // multi-step calls from this size replay a graph
 constexpr int kSettleBlocks = 152;      // grid-stride blocks of k_load_settle (one per SM)
 
+// With MTPT_DEBUG set in the environment, a failing runtime call is named on
+// stderr (the status code alone does not say which call failed).
+void report_cuda_error(cudaError_t err, const char* expr, int line) {
+    static const bool on = std::getenv("MTPT_DEBUG") != nullptr;
+    if (on) std::fprintf(stderr, "mtpt: %s failed (line %d): %s\n", expr, line,
+                         cudaGetErrorString(err));
+}
+
 #define MTPT_CUDA_TRY(expr)                                   \
     do {                                                      \
         cudaError_t err_ = (expr);                            \
         if (err_ != cudaSuccess) {                            \
+            report_cuda_error(err_, #expr, __LINE__);         \
             (void)cudaGetLastError();                         \
             return MTPT_ERR_CUDA;                             \
         }                                                     \
@@ -81,6 +92,11 @@ struct RealHost {
     int64_t n = 0;
     int64_t n_cells = 0;
     int n_corners = 0;
+    // one tile of a checkerboard (Secs. 4-5): the cell grid is the whole
+    // box's grid for n_global particles, restricted to the tile and its pad
+    bool tiled = false;
+    int64_t n_global = 0;
+    double tile_lo[3] = {0, 0, 0}, tile_hi[3] = {0, 0, 0}, pad = 0;
 };
 
 }  // namespace
@@ -143,6 +159,9 @@ struct mtpt_handle {
     DevBuf<uint32_t> nb_j, nb_count;      // binary64 form neighbour lists
     DevBuf<double> nb_k;
     int nb_cap = 0;
+    DevBuf<uint2> nb32_e;                 // precision form neighbour lists {j, K}
+    DevBuf<uint32_t> nb32_count;
+    int nb32_cap = 0;
     DevBuf<uint32_t> adj_nb_j, adj_nb_count;     // adjoint (K, dK) lists
     DevBuf<double2> adj_nb_k;
     int adj_cap = 0;
@@ -181,6 +200,18 @@ struct mtpt_handle {
     int graph_cur = -1, graph_flags = -1;
     const double* graph_mass0 = nullptr;
     cudaStream_t capture_stream = nullptr;
+    // split domain: this handle's tile and its pack / keep buffers
+    TileGeom tile{};
+    int ntiles = 0;
+    std::vector<long long> tile_tables;   // per axis: edge keys (f + 1), near_lo (f), near_hi (f)
+    int tile_table_off[3] = {0, 0, 0};
+    DevBuf<long long> tile_tables_dev;
+    DevBuf<unsigned long long> tile_counts, tile_base, tile_cursor, tile_native;
+    DevBuf<uint32_t> tile_flag;
+    DevBuf<double> tile_keep, tile_stage;
+    std::vector<unsigned long long> tile_host;
+    int64_t keep_n = 0;
+    bool keep_ready = false;
     // per-kernel timing
     bool timing = false;
     struct PendingEvent { const char* name; cudaEvent_t a, b; };
@@ -341,7 +372,7 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
         double k = P.transfer ? std::floor(L / psi_eff) : 1.0;
         ncell[a] = std::max(1.0, std::min(k, double(1 << 30)));
     }
-    const double cap = std::max(4.0 * double(R.n) + 64.0, 64.0);
+    const double cap = std::max(4.0 * double(R.tiled ? R.n_global : R.n) + 64.0, 64.0);
     double total = ncell[0] * ncell[1] * ncell[2];
     for (int guard = 0; guard < 64 && total > cap; ++guard) {
         const double f = std::pow(cap / total, 1.0 / p.dim);
@@ -356,10 +387,28 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
         }
     }
     if (total > 2.0e9) return MTPT_ERR_INVALID_ARG;
+    // a tile keeps the cells of the whole box's grid that cover it and its
+    // pad (one cell of margin each side for the cell index's rounding), so
+    // its cell corners, offsets and in-row orders are the undivided run's
+    double nloc[3] = {ncell[0], ncell[1], ncell[2]}, first[3] = {0, 0, 0};
+    if (R.tiled && P.transfer) {
+        for (int a = 0; a < p.dim; ++a) {
+            const double w = (p.hi[a] - p.lo[a]) / ncell[a];
+            const double plo = std::max(p.lo[a], R.tile_lo[a] - R.pad);
+            const double phi = std::min(p.hi[a], R.tile_hi[a] + R.pad);
+            const double c0 = std::max(0.0, std::floor((plo - p.lo[a]) / w) - 1.0);
+            const double c1 = std::min(ncell[a] - 1.0, std::floor((phi - p.lo[a]) / w) + 1.0);
+            first[a] = c0;
+            nloc[a] = std::max(1.0, c1 - c0 + 1.0);
+        }
+        total = nloc[0] * nloc[1] * nloc[2];
+    }
     double sum_w = 0.0, sum_b = 0.0;
     int off = corner_base;
     for (int a = 0; a < 3; ++a) {
-        g.n[a] = int(ncell[a]);
+        g.n[a] = int(nloc[a]);
+        g.nglob[a] = int(ncell[a]);
+        g.off[a] = int(first[a]);
         g.lo[a] = a < p.dim ? p.lo[a] : 0.0;
         g.w[a] = a < p.dim ? (p.hi[a] - p.lo[a]) / ncell[a] : 1.0;
         g.inv_w[a] = 1.0 / g.w[a];
@@ -458,12 +507,13 @@ int setup_grids(mtpt_handle* h) {
         double vol = 1.0;
         for (int a = 0; a < p.dim; ++a) vol *= p.hi[a] - p.lo[a];
         const double ball = p.dim == 1 ? 2.0 : (p.dim == 2 ? M_PI : 4.0 * M_PI / 3.0);
-        expect = std::max(expect, double(h->reals[k].n) / vol * ball *
-                                      std::pow(h->reals[k].psi, double(p.dim)));
+        const double nk = double(h->reals[k].tiled ? h->reals[k].n_global : h->reals[k].n);
+        expect = std::max(expect, nk / vol * ball * std::pow(h->reals[k].psi, double(p.dim)));
     }
     const int list_cap =
         int(std::min(64.0, std::max(8.0, std::ceil(expect + 4.0 * std::sqrt(expect) + 4.0))));
     h->nb_cap = h->precision == MTPT_FP64 ? list_cap : 0;
+    h->nb32_cap = h->precision == MTPT_FP32W ? list_cap : 0;
     h->adj_cap = list_cap;
     h->n_cells = cell_base;
     h->n_corners = corner_base;
@@ -537,6 +587,12 @@ int ensure_cells(mtpt_handle* h) {
         MTPT_TRY(h->nb_j.ensure(slots));
         MTPT_TRY(h->nb_k.ensure(slots));
         MTPT_TRY(h->nb_count.ensure(size_t(h->cap)));
+    }
+    if (h->nb32_cap > 0) {
+        const size_t slots = size_t(h->nb32_cap) * size_t(h->cap);
+        if (slots > h->nb32_e.count || size_t(h->cap) > h->nb32_count.count) drop_graph(h);
+        MTPT_TRY(h->nb32_e.ensure(slots));
+        MTPT_TRY(h->nb32_count.ensure(size_t(h->cap)));
     }
     // counts start (and, after each scatter, end) at zero
     MTPT_CUDA_TRY(cudaMemsetAsync(h->count.p, 0, padded * sizeof(uint32_t), h->stream));
@@ -697,15 +753,17 @@ template <int DIM, class View, int BLOCK>
 int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
                      int o, int c) {
     const int blocks = int((n + BLOCK - 1) / BLOCK);
+    const NbList32 nb{h->nb32_e.p, h->nb32_count.p, h->nb32_e.p ? h->nb32_cap : 0};
     {
         MTPT_TIMED(h, "rowsum_f32");
         k_rowsum_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
-            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->r32.p, h->pair_counter.p);
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->r32.p, h->pair_counter.p,
+            h->ntiles > 0 ? h->id[o].p : nullptr, nb);
     }
     MTPT_TIMED(h, "exchange_f32");
     k_exchange_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
         n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->r32.p, h->msplit.p,
-        h->mass[o].p, h->mass[c].p);
+        h->mass[o].p, h->mass[c].p, nb);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -716,7 +774,15 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
 template <int DIM, class View>
 int launch_step(mtpt_handle* h, int flags) {
     const int n = int(h->n);
-    if (n == 0) return MTPT_OK;
+    if (n == 0) {
+        // an empty handle (e.g. a tile without particles) keeps its walk's
+        // step counter in line with the host mirror
+        if ((flags & MTPT_DO_WALK) && h->step_dev.p) {
+            k_advance_step<<<1, 1, 0, h->stream>>>(h->step_dev.p);
+            MTPT_CUDA_TRY(cudaGetLastError());
+        }
+        return MTPT_OK;
+    }
     const int64_t stride = h->cap;
     const int blocks = grid_for(n);
     cudaStream_t st = h->stream;
@@ -781,7 +847,8 @@ int launch_step(mtpt_handle* h, int flags) {
             MTPT_TIMED(h, "rowsum_f64");
             k_rowsum_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
                 n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
-                h->pair_counter.p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap});
+                h->pair_counter.p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap},
+                h->ntiles > 0 ? h->id[o].p : nullptr);
         }
         MTPT_TIMED(h, "exchange_f64");
         k_exchange_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
@@ -890,6 +957,13 @@ int ensure_out_tmp(mtpt_handle* h) {
 // `out_dev` (stride n, input order).
 int unpermute_to(mtpt_handle* h, const double* src, int naxes, double* out_dev) {
     if (h->n == 0) return MTPT_OK;
+    if (h->ntiles > 0) {            // a tile's particles come and go: its own order
+        MTPT_CUDA_TRY(cudaMemcpy2DAsync(out_dev, size_t(h->n) * sizeof(double), src,
+                                        size_t(h->cap) * sizeof(double),
+                                        size_t(h->n) * sizeof(double), size_t(naxes),
+                                        cudaMemcpyDeviceToDevice, h->stream));
+        return MTPT_OK;
+    }
     k_unpermute<double><<<grid_for(h->n), kBlock, 0, h->stream>>>(
         int(h->n), h->cap, naxes, h->id[h->cur].p, src, 1, 1.0, out_dev);
     MTPT_CUDA_TRY(cudaGetLastError());
@@ -1357,7 +1431,7 @@ extern "C" {
 
 int mtpt_adjoint_forward(mtpt_handle* h, int64_t nsteps, int64_t checkpoint_every) {
     if (!h || nsteps < 1 || checkpoint_every < 1) return MTPT_ERR_INVALID_ARG;
-    if (!h->have_particles) return MTPT_ERR_STATE;
+    if (!h->have_particles || h->ntiles > 0) return MTPT_ERR_STATE;
     if (h->nreal != 1 || !h->any_transfer || !(h->reals[0].prm.D > 0.0)) return MTPT_ERR_INVALID_ARG;
     const int64_t n = h->n;
     const size_t cap = size_t(std::max<int64_t>(h->cap, 1));
@@ -1488,7 +1562,11 @@ int mtpt_destroy(mtpt_handle* h) {
     h->lam_in.release(); h->lam_s.release(); h->lam_new.release(); h->gD.release();
     h->partial.release(); h->acc.release();
     h->nb_j.release(); h->nb_k.release(); h->nb_count.release();
+    h->nb32_e.release(); h->nb32_count.release();
     h->adj_nb_j.release(); h->adj_nb_k.release(); h->adj_nb_count.release();
+    h->tile_counts.release(); h->tile_base.release(); h->tile_cursor.release();
+    h->tile_native.release(); h->tile_flag.release(); h->tile_keep.release();
+    h->tile_stage.release(); h->tile_tables_dev.release();
     for (auto& pe : h->pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);
@@ -1506,6 +1584,7 @@ int mtpt_set_stream(mtpt_handle* h, void* stream) {
 
 int mtpt_set_particles(mtpt_handle* h, int64_t n, const double* pos, const double* mass) {
     if (!h || h->nreal != 1) return MTPT_ERR_INVALID_ARG;
+    if (h->ntiles > 0) return MTPT_ERR_STATE;
     if (n < 0) return MTPT_ERR_INVALID_ARG;
     const double *pd = nullptr, *md = nullptr;
     int in_place = -1;
@@ -1525,6 +1604,7 @@ int mtpt_set_particles_batch(mtpt_handle* h, const int64_t* counts, const double
 int mtpt_set_particles_device(mtpt_handle* h, int64_t n, const double* pos_dev,
                               const double* mass_dev) {
     if (!h || h->nreal != 1 || n < 0) return MTPT_ERR_INVALID_ARG;
+    if (h->ntiles > 0) return MTPT_ERR_STATE;
     MTPT_TRY(load_particles(h, &n, pos_dev, mass_dev, cudaMemcpyDeviceToDevice));
     if (n > 0) {
         if (h->batch) {
@@ -1548,6 +1628,9 @@ int mtpt_step_ex(mtpt_handle* h, int64_t nsteps, int32_t flags) {
     if (!h || nsteps < 0) return MTPT_ERR_INVALID_ARG;
     if (flags & ~(MTPT_DO_WALK | MTPT_DO_TRANSFER)) return MTPT_ERR_INVALID_ARG;
     if (!h->have_particles) return MTPT_ERR_STATE;
+    // a tile's transfer needs its ghosts: mtpt_tile_pack / mtpt_tile_transfer
+    if (h->ntiles > 0 && (flags & MTPT_DO_TRANSFER)) return MTPT_ERR_STATE;
+    if (h->ntiles > 0) h->keep_ready = false;
     return run_steps(h, nsteps, flags);
 }
 
@@ -1571,6 +1654,7 @@ int mtpt_get_masses(mtpt_handle* h, double* out) {
 
 int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const double* mass) {
     if (!h || h->nreal != 1) return MTPT_ERR_INVALID_ARG;
+    if (h->ntiles > 0) return MTPT_ERR_STATE;
     if (!h->have_particles) return MTPT_ERR_STATE;
     if (n != h->n || (n > 0 && (!pos || !mass))) return MTPT_ERR_INVALID_ARG;
     if (n == 0) return MTPT_OK;
@@ -1654,7 +1738,7 @@ int mtpt_get_row_sums(mtpt_handle* h, double* out) {
 int mtpt_get_pairs(mtpt_handle* h, int64_t cap, int64_t* count, uint32_t* pair_i,
                    uint32_t* pair_j) {
     if (!h || !count || cap < 0 || (cap > 0 && (!pair_i || !pair_j))) return MTPT_ERR_INVALID_ARG;
-    if (!h->have_particles) return MTPT_ERR_STATE;
+    if (!h->have_particles || h->ntiles > 0) return MTPT_ERR_STATE;
     *count = 0;
     if (h->n == 0 || !h->any_transfer) return read_status(h);
     MTPT_TRY(h->emit_counter.ensure(1));
@@ -1747,6 +1831,7 @@ int mtpt_timing_reset(mtpt_handle* h) {
 
 int mtpt_set_tuning(mtpt_handle* h, const mtpt_tuning* t) {
     if (!h || !t) return MTPT_ERR_INVALID_ARG;
+    if (h->ntiles > 0) return MTPT_ERR_STATE;   // a tile's grid is the whole box's
     if (!(t->cell_scale >= 1.0 && t->cell_scale <= 8.0)) return MTPT_ERR_INVALID_ARG;
     if (t->pair_block != 128 && t->pair_block != 256) return MTPT_ERR_INVALID_ARG;
     const bool regrid = t->cell_scale != h->cell_scale;
@@ -1772,7 +1857,7 @@ int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out) {
 
 int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
     if (!h || trial_steps < 1) return MTPT_ERR_INVALID_ARG;
-    if (!h->have_particles) return MTPT_ERR_STATE;
+    if (!h->have_particles || h->ntiles > 0) return MTPT_ERR_STATE;
     const bool timing0 = h->timing;
     h->timing = false;
     // snapshot of the current state (the trials step it)
@@ -1861,6 +1946,347 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
     srid.release();
     if (rc == MTPT_OK && chosen) *chosen = best;
     return rc;
+}
+
+// --- split domain (Secs. 4-5) ------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+// The tile's particle set from n_keep kept records and n_recv received ones
+// (records of dim + 2 binary64 values), natives first classified by the
+// tile that owns them; *flags receives the assembly's error bits.
+template <int DIM>
+int tile_install_t(mtpt_handle* h, int64_t n_keep, const double* keep, int64_t n_recv,
+                   const double* recv, bool strict, double mass_limit) {
+    const int64_t n = n_keep + n_recv;
+    if (n > int64_t(0x7fffffff) - kBlock) return MTPT_ERR_INVALID_ARG;
+    const bool first = !h->have_particles;
+    const int64_t cap0 = h->cap;
+    h->n = n;
+    h->reals[0].n = n;
+    // headroom: a tile's particle count drifts from step to step
+    MTPT_TRY(ensure_capacity(h, n > h->cap ? n + n / 8 : n));
+    // the grid and its cell arrays (ensure_cells allocates the corner tables
+    // that upload_tables fills), as the plain load does them
+    if (first) MTPT_TRY(setup_grids(h));
+    if ((first || h->cap != cap0) && h->any_transfer) MTPT_TRY(ensure_cells(h));
+    if (first) {
+        // the tile geometry's edge tables (device copies, pointers into them)
+        const size_t nt = std::max<size_t>(h->tile_tables.size(), 1);
+        MTPT_TRY(h->tile_tables_dev.ensure(nt));
+        if (!h->tile_tables.empty())
+            MTPT_CUDA_TRY(cudaMemcpyAsync(h->tile_tables_dev.p, h->tile_tables.data(),
+                                          h->tile_tables.size() * sizeof(long long),
+                                          cudaMemcpyHostToDevice, h->stream));
+        for (int a = 0; a < 3; ++a) {
+            const int aa = a < h->dim ? a : 0;
+            const int f = h->tile.f[aa];
+            const long long* base = h->tile_tables_dev.p + h->tile_table_off[aa];
+            h->tile.edge[a] = base;
+            h->tile.near_lo[a] = base + f + 1;
+            h->tile.near_hi[a] = base + 2 * f + 1;
+        }
+        if (!h->exp_table.p) {
+            MTPT_TRY(h->exp_table.ensure(kExpTable));
+            MTPT_CUDA_TRY(cudaMemcpyAsync(h->exp_table.p, exp_table_host(),
+                                          kExpTable * sizeof(double), cudaMemcpyHostToDevice,
+                                          h->stream));
+        }
+        MTPT_TRY(upload_tables(h));
+    }
+    MTPT_TRY(h->tile_flag.ensure(1));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->tile_flag.p, 0, sizeof(uint32_t), h->stream));
+    drop_graph(h);
+    h->cur = 0;
+    if (n > 0) {
+        MTPT_TIMED(h, "tile_assemble");
+        k_tile_assemble<DIM><<<grid_for(n), kBlock, 0, h->stream>>>(
+            int(n_keep), keep, int(n_recv), recv, h->tile, strict ? 1 : 0, mass_limit, h->cap,
+            h->pos[0].p, h->mass[0].p, h->id[0].p, h->tile_flag.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    h->fresh = true;
+    h->have_particles = true;
+    h->have_row_sums = false;
+    return MTPT_OK;
+}
+
+template <int DIM>
+int tile_pack_t(mtpt_handle* h, int64_t cap, double* send, int64_t* counts) {
+    const int P = h->ntiles;
+    const int n = int(h->n);
+    constexpr int K = DIM + 2;
+    MTPT_TRY(h->tile_counts.ensure(size_t(2 * P)));
+    MTPT_TRY(h->tile_base.ensure(size_t(2 * P)));
+    MTPT_TRY(h->tile_cursor.ensure(size_t(2 * P)));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->tile_counts.p, 0, size_t(2 * P) * 8, h->stream));
+    if (n > 0) {
+        MTPT_TIMED(h, "tile_count");
+        k_tile_count<DIM><<<grid_for(n), kBlock, 0, h->stream>>>(n, h->cap, h->pos[h->cur].p,
+                                                                 h->tile, h->tile_counts.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    h->tile_host.assign(size_t(4 * P), 0ull);
+    unsigned long long* cnt = h->tile_host.data();
+    unsigned long long* base = cnt + 2 * P;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(cnt, h->tile_counts.p, size_t(2 * P) * 8,
+                                  cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const int self = h->tile.self;
+    unsigned long long total = 0;
+    for (int t = 0; t < P; ++t) {
+        counts[2 * t] = int64_t(cnt[2 * t]);
+        counts[2 * t + 1] = int64_t(cnt[2 * t + 1]);
+        if (t == self) continue;
+        base[2 * t] = total;
+        total += cnt[2 * t];
+        base[2 * t + 1] = total;
+        total += cnt[2 * t + 1];
+    }
+    base[2 * self] = 0;
+    base[2 * self + 1] = cnt[2 * self];
+    h->keep_ready = false;
+    if (int64_t(total) > cap) return MTPT_ERR_CAPACITY;
+    if (total > 0 && !send) return MTPT_ERR_INVALID_ARG;
+    const int64_t kept = int64_t(cnt[2 * self] + cnt[2 * self + 1]);
+    MTPT_TRY(h->tile_keep.ensure(size_t(K) * size_t(std::max<int64_t>(kept, 1))));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h->tile_base.p, base, size_t(2 * P) * 8,
+                                  cudaMemcpyHostToDevice, h->stream));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->tile_cursor.p, 0, size_t(2 * P) * 8, h->stream));
+    if (n > 0) {
+        MTPT_TIMED(h, "tile_scatter");
+        k_tile_scatter<DIM><<<grid_for(n), kBlock, 0, h->stream>>>(
+            n, h->cap, h->pos[h->cur].p, h->mass[h->cur].p, h->id[h->cur].p, h->tile,
+            h->tile_base.p, h->tile_cursor.p, send, h->tile_keep.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    h->keep_n = kept;
+    h->keep_ready = true;
+    return MTPT_OK;
+}
+
+template <int DIM>
+int tile_transfer_t(mtpt_handle* h, int64_t n_recv, const double* recv) {
+    MTPT_TRY(tile_install_t<DIM>(h, h->keep_n, h->tile_keep.p, n_recv, recv, false, HUGE_VAL));
+    h->keep_ready = false;
+    MTPT_TRY(dispatch_step(h, MTPT_DO_TRANSFER));
+    // keep the natives
+    MTPT_TRY(h->tile_native.ensure(1));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->tile_native.p, 0, 8, h->stream));
+    const int c = h->cur, o = 1 - h->cur;
+    if (h->n > 0) {
+        MTPT_TIMED(h, "tile_compact");
+        k_tile_compact<DIM><<<grid_for(h->n), kBlock, 0, h->stream>>>(
+            int(h->n), h->cap, h->pos[c].p, h->mass[c].p, h->id[c].p, h->pos[o].p,
+            h->mass[o].p, h->id[o].p, h->tile_native.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    unsigned long long natives = 0;
+    uint32_t flag = 0, st = 0;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&natives, h->tile_native.p, 8, cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&flag, h->tile_flag.p, 4, cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&st, h->status.p, 4, cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->cur = o;
+    h->n = int64_t(natives);
+    h->reals[0].n = h->n;
+    h->have_row_sums = false;
+    if (flag) return MTPT_ERR_INVALID_ARG;
+    return status_code(h, st);
+}
+
+template <int DIM>
+int tile_load_t(mtpt_handle* h, int64_t n, const double* pos, const double* mass,
+                const uint32_t* ids) {
+    constexpr int K = DIM + 2;
+    const size_t nn = size_t(std::max<int64_t>(n, 1));
+    MTPT_TRY(h->tile_stage.ensure(size_t(DIM + 1) * nn + (nn + 1) / 2));
+    MTPT_TRY(h->tile_keep.ensure(size_t(K) * nn));
+    double* sp = h->tile_stage.p;
+    double* sm = sp + size_t(DIM) * nn;
+    uint32_t* si = reinterpret_cast<uint32_t*>(sm + nn);
+    if (n > 0) {
+        MTPT_CUDA_TRY(cudaMemcpyAsync(sp, pos, size_t(DIM) * size_t(n) * 8,
+                                      cudaMemcpyHostToDevice, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(sm, mass, size_t(n) * 8, cudaMemcpyHostToDevice, h->stream));
+        MTPT_CUDA_TRY(cudaMemcpyAsync(si, ids, size_t(n) * 4, cudaMemcpyHostToDevice, h->stream));
+        // the positions' SoA stride is n in the staging copy
+        k_tile_records<DIM><<<grid_for(n), kBlock, 0, h->stream>>>(int(n), sp, sm, si,
+                                                                  h->tile_keep.p);
+        MTPT_CUDA_TRY(cudaGetLastError());
+    }
+    h->have_particles = false;
+    const double mass_limit = h->precision == MTPT_FP32W ? 1e30 : HUGE_VAL;
+    MTPT_TRY(tile_install_t<DIM>(h, n, h->tile_keep.p, 0, nullptr, true, mass_limit));
+    uint32_t flag = 0;
+    MTPT_CUDA_TRY(cudaMemcpyAsync(&flag, h->tile_flag.p, 4, cudaMemcpyDeviceToHost, h->stream));
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (flag) {
+        h->have_particles = false;
+        h->n = 0;
+        h->reals[0].n = 0;
+        if (flag & kTileErrForeign) return MTPT_ERR_OUT_OF_DOMAIN;
+        return MTPT_ERR_INVALID_ARG;
+    }
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(uint32_t), h->stream));
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->pair_counter.p, 0, sizeof(unsigned long long), h->stream));
+    MTPT_TRY(set_step_dev(h, 0));
+    h->keep_ready = false;
+    return MTPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mtpt_tiling_factors(int32_t dim, const double* lo, const double* hi, int32_t ntiles,
+                        int32_t* factors) {
+    if (!lo || !hi || !factors || dim < 1 || dim > kMaxDim || ntiles < 1 || ntiles > (1 << 20))
+        return MTPT_ERR_INVALID_ARG;
+    double L[3] = {1, 1, 1};
+    for (int a = 0; a < dim; ++a) {
+        if (!(hi[a] > lo[a]) || !std::isfinite(hi[a] - lo[a])) return MTPT_ERR_INVALID_ARG;
+        L[a] = hi[a] - lo[a];
+    }
+    factors[0] = ntiles;
+    factors[1] = factors[2] = 1;
+    if (dim == 2) {
+        // Eq. "minimization": f1 <= f2, f1 f2 = N, |f2 / f1 - A| least for the
+        // aspect ratio A >= 1; the longer side takes f2 tiles
+        const int wide = L[0] >= L[1] ? 0 : 1;
+        const double A = L[wide] / L[1 - wide];
+        int best1 = 1;
+        double best = INFINITY;
+        for (int f1 = 1; int64_t(f1) * f1 <= ntiles; ++f1) {
+            if (ntiles % f1) continue;
+            const double e = std::fabs(double(ntiles / f1) / double(f1) - A);
+            if (e < best) {
+                best = e;
+                best1 = f1;
+            }
+        }
+        factors[wide] = ntiles / best1;
+        factors[1 - wide] = best1;
+    } else if (dim == 3) {
+        // the 3-d counterpart (the paper asks for tiles closest to cubes):
+        // the factor triple whose largest tile edge over its smallest is least
+        double best = INFINITY;
+        for (int f0 = 1; f0 <= ntiles; ++f0) {
+            if (ntiles % f0) continue;
+            const int rest = ntiles / f0;
+            for (int f1 = 1; f1 <= rest; ++f1) {
+                if (rest % f1) continue;
+                const int f2 = rest / f1;
+                const double e[3] = {L[0] / f0, L[1] / f1, L[2] / f2};
+                const double r = std::max({e[0], e[1], e[2]}) / std::min({e[0], e[1], e[2]});
+                if (r < best) {
+                    best = r;
+                    factors[0] = f0;
+                    factors[1] = f1;
+                    factors[2] = f2;
+                }
+            }
+        }
+    }
+    return MTPT_OK;
+}
+
+int mtpt_set_tiling(mtpt_handle* h, const mtpt_tiling* t) {
+    if (!h || !t) return MTPT_ERR_INVALID_ARG;
+    if (h->nreal != 1 || h->batch || h->have_particles) return MTPT_ERR_STATE;
+    RealHost& R = h->reals[0];
+    const mtpt_params& p = R.prm;
+    int64_t total = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (t->tiles[a] < 1 || (a >= p.dim && t->tiles[a] != 1)) return MTPT_ERR_INVALID_ARG;
+        total *= t->tiles[a];
+    }
+    if (total > (1 << 20) || t->tile < 0 || t->tile >= total) return MTPT_ERR_INVALID_ARG;
+    if (t->n_global < 0 || t->n_global > int64_t(0x7fffffff) - kBlock) return MTPT_ERR_INVALID_ARG;
+    const double pad = R.psi > 0.0 ? 2.0 * R.psi * (1.0 + 1e-6) : 0.0;
+    TileGeom g{};
+    int at[3] = {t->tile % t->tiles[0], (t->tile / t->tiles[0]) % t->tiles[1],
+                 t->tile / (t->tiles[0] * t->tiles[1])};
+    // edge tables: e_t = lo + t width, e_t + pad, e_(t+1) - pad as order keys
+    std::vector<long long> tables;
+    int table_off[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        const int f = t->tiles[a];
+        g.f[a] = f;
+        table_off[a] = int(tables.size());
+        if (a >= p.dim) {
+            g.lo_f[a] = 0.0f;
+            g.inv_w_f[a] = 1.0f;
+            R.tile_lo[a] = R.tile_hi[a] = 0.0;
+            continue;
+        }
+        const double width = (p.hi[a] - p.lo[a]) / double(f);
+        // every tile at least a pad wide, so a pad reaches the next tile only
+        if (f > 1 && !(width >= pad)) return MTPT_ERR_INVALID_ARG;
+        g.lo_f[a] = float(p.lo[a]);
+        g.inv_w_f[a] = float(1.0 / width);
+        std::vector<double> e(size_t(f) + 1);
+        for (int k = 0; k <= f; ++k) e[size_t(k)] = p.lo[a] + double(k) * width;
+        for (int k = 0; k <= f; ++k) tables.push_back(host_order_key(e[size_t(k)]));
+        for (int k = 0; k < f; ++k) tables.push_back(host_order_key(e[size_t(k)] + pad));
+        for (int k = 0; k < f; ++k) tables.push_back(host_order_key(e[size_t(k) + 1] - pad));
+        R.tile_lo[a] = e[size_t(at[a])];
+        R.tile_hi[a] = e[size_t(at[a]) + 1];
+    }
+    g.self = t->tile;
+    R.tiled = true;
+    R.n_global = t->n_global;
+    R.pad = pad;
+    h->tile = g;
+    h->tile_tables = std::move(tables);
+    for (int a = 0; a < 3; ++a) h->tile_table_off[a] = table_off[a];
+    h->ntiles = int(total);
+    return MTPT_OK;
+}
+
+int mtpt_set_particles_tile(mtpt_handle* h, int64_t n, const double* pos, const double* mass,
+                            const uint32_t* ids) {
+    if (!h || n < 0 || (n > 0 && (!pos || !mass || !ids))) return MTPT_ERR_INVALID_ARG;
+    if (h->ntiles == 0) return MTPT_ERR_STATE;
+    switch (h->dim) {
+        case 1: return tile_load_t<1>(h, n, pos, mass, ids);
+        case 2: return tile_load_t<2>(h, n, pos, mass, ids);
+        default: return tile_load_t<3>(h, n, pos, mass, ids);
+    }
+}
+
+int mtpt_tile_pack(mtpt_handle* h, int64_t cap, double* send_dev, int64_t* counts) {
+    if (!h || !counts || cap < 0) return MTPT_ERR_INVALID_ARG;
+    if (h->ntiles == 0 || !h->have_particles) return MTPT_ERR_STATE;
+    switch (h->dim) {
+        case 1: return tile_pack_t<1>(h, cap, send_dev, counts);
+        case 2: return tile_pack_t<2>(h, cap, send_dev, counts);
+        default: return tile_pack_t<3>(h, cap, send_dev, counts);
+    }
+}
+
+int mtpt_tile_transfer(mtpt_handle* h, int64_t n_recv, const double* recv_dev) {
+    if (!h || n_recv < 0 || (n_recv > 0 && !recv_dev)) return MTPT_ERR_INVALID_ARG;
+    if (h->ntiles == 0 || !h->have_particles || !h->keep_ready) return MTPT_ERR_STATE;
+    switch (h->dim) {
+        case 1: return tile_transfer_t<1>(h, n_recv, recv_dev);
+        case 2: return tile_transfer_t<2>(h, n_recv, recv_dev);
+        default: return tile_transfer_t<3>(h, n_recv, recv_dev);
+    }
+}
+
+int mtpt_get_ids(mtpt_handle* h, uint32_t* out) {
+    if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->have_particles) return MTPT_ERR_STATE;
+    if (h->n == 0) return MTPT_OK;
+    if (h->ntiles == 0) {
+        for (int64_t i = 0; i < h->n; ++i) out[i] = uint32_t(i);
+        return MTPT_OK;
+    }
+    MTPT_CUDA_TRY(cudaMemcpyAsync(out, h->id[h->cur].p, size_t(h->n) * 4, cudaMemcpyDeviceToHost,
+                                  h->stream));
+    return read_status(h);
 }
 
 const char* mtpt_status_string(int status) {
@@ -2002,6 +2428,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.params[0].id_offset = 0;
     MTPT_TRY(setup_grids(&h));
     h.nb_cap = 0;                        // no neighbour lists: pass 2 searches
+    h.nb32_cap = 0;
     const int d = h.dim;
     const size_t cells_pad = size_t(h.n_cells_pad);
 

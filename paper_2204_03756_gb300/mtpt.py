@@ -41,7 +41,9 @@ EXPORTED = [
     "mtpt_create_batch", "mtpt_set_particles_batch", "mtpt_get_realisation_info",
     "mtpt_set_tuning", "mtpt_get_tuning", "mtpt_autotune", "mtpt_adjoint_forward",
     "mtpt_adjoint_backward", "mtpt_status_string", "mtpt_check_word",
-    "mtpt_set_particles_async", "mtpt_get_masses_async",
+    "mtpt_set_particles_async", "mtpt_get_masses_async", "mtpt_tiling_factors",
+    "mtpt_set_tiling", "mtpt_set_particles_tile", "mtpt_tile_pack", "mtpt_tile_transfer",
+    "mtpt_get_ids",
 ]
 
 
@@ -68,6 +70,11 @@ class _KernelStat(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("cell_scale", ctypes.c_double), ("pair_block", ctypes.c_int32),
                 ("pad", ctypes.c_int32)]
+
+
+class _Tiling(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_int32 * 3), ("tile", ctypes.c_int32),
+                ("n_global", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
@@ -159,6 +166,13 @@ def load():
     lib.mtpt_set_particles_batch.argtypes = [vp, P(ctypes.c_int64), vp, vp]
     lib.mtpt_get_realisation_info.argtypes = [vp, ctypes.c_int32, P(_Info)]
     lib.mtpt_step_noalloc.argtypes = [P(_Params), ctypes.c_int64, ctypes.c_uint64, vp, vp, vp]
+    lib.mtpt_tiling_factors.argtypes = [ctypes.c_int32, vp, vp, ctypes.c_int32,
+                                        P(ctypes.c_int32)]
+    lib.mtpt_set_tiling.argtypes = [vp, P(_Tiling)]
+    lib.mtpt_set_particles_tile.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
+    lib.mtpt_tile_pack.argtypes = [vp, ctypes.c_int64, vp, P(ctypes.c_int64)]
+    lib.mtpt_tile_transfer.argtypes = [vp, ctypes.c_int64, vp]
+    lib.mtpt_get_ids.argtypes = [vp, vp]
     lib.mtpt_status_string.argtypes = [ctypes.c_int]
     lib.mtpt_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -449,6 +463,61 @@ def mtpt_step_noalloc(params: Params, step: int, pos, mass) -> None:
                                     _dev_ptr(pos, "float64", params.dim * n),
                                     _dev_ptr(mass, "float64", n), _torch_stream()),
            "mtpt_step_noalloc")
+
+
+def mtpt_tiling_factors(dim: int, lo, hi, ntiles: int) -> tuple:
+    """Tiles per axis of a checkerboard of `ntiles` tiles (Eq. "minimization")."""
+    lo = np.ascontiguousarray(np.asarray(lo, dtype=np.float64))
+    hi = np.ascontiguousarray(np.asarray(hi, dtype=np.float64))
+    out = (ctypes.c_int32 * 3)()
+    _check(load().mtpt_tiling_factors(dim, lo.ctypes.data, hi.ctypes.data, ntiles, out),
+           "mtpt_tiling_factors")
+    return tuple(int(v) for v in out)
+
+
+def mtpt_set_tiling(h, tiles, tile: int, n_global: int) -> None:
+    t = _Tiling((ctypes.c_int32 * 3)(*(list(tiles) + [1] * (3 - len(tiles)))), tile, n_global)
+    _check(load().mtpt_set_tiling(h, ctypes.byref(t)), "mtpt_set_tiling")
+
+
+def mtpt_set_particles_tile(h, dim: int, pos, mass, ids) -> None:
+    mass = np.ascontiguousarray(np.asarray(mass, dtype=np.float64)).ravel()
+    n = mass.size
+    pos = _host_f64(pos, (dim, n))
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint32)).ravel()
+    if ids.size != n:
+        raise ValueError(f"expected {n} ids, got {ids.size}")
+    _check(load().mtpt_set_particles_tile(h, n, pos.ctypes.data, mass.ctypes.data,
+                                          ids.ctypes.data), "mtpt_set_particles_tile")
+
+
+def mtpt_tile_pack(h, send, ntiles: int):
+    """Packs into the CUDA float64 tensor `send` (records of dim + 2 values,
+    capacity send.numel() // (dim + 2) records).  Returns (status, counts),
+    counts an int64 array of 2 x ntiles; status MTPT_ERR_CAPACITY asks for a
+    larger buffer, anything else but MTPT_OK raises."""
+    import torch
+    if not (isinstance(send, torch.Tensor) and send.is_cuda and send.is_contiguous()
+            and send.dtype == torch.float64 and send.dim() == 2):
+        raise ValueError("expected a contiguous 2-d CUDA float64 tensor of records")
+    counts = np.zeros(2 * ntiles, dtype=np.int64)
+    rc = load().mtpt_tile_pack(h, send.shape[0], ctypes.c_void_p(send.data_ptr()),
+                               counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    if rc not in (MTPT_OK, MTPT_ERR_CAPACITY):
+        raise MtptError(rc, "mtpt_tile_pack")
+    return rc, counts
+
+
+def mtpt_tile_transfer(h, recv) -> None:
+    """recv: contiguous 2-d CUDA float64 tensor of received records."""
+    _check(load().mtpt_tile_transfer(h, recv.shape[0], ctypes.c_void_p(recv.data_ptr())
+                                     if recv.numel() else None), "mtpt_tile_transfer")
+
+
+def mtpt_get_ids(h, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint32)
+    _check(load().mtpt_get_ids(h, out.ctypes.data), "mtpt_get_ids")
+    return out
 
 
 def mtpt_status_string(code: int) -> str:

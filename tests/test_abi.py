@@ -62,6 +62,13 @@ def test_every_boundary_call_cites_its_passage():
         assert cites or other, name
 
 
+def test_binding_declares_every_signature(lib):
+    """ctypes passes undeclared arguments as C int: every entry point the
+    binding exports has its argument types declared."""
+    for name in mtpt.EXPORTED:
+        assert getattr(lib, name).argtypes is not None, name
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in _declared_symbols():
         assert hasattr(lib, name), name
