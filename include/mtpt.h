@@ -350,7 +350,7 @@ int mtpt_timing_reset(mtpt_handle* h);
  * MTPT_ERR_TOO_LARGE before any work is enqueued.  The cell grid is capped
  * at 4 n + 64 cells however sparse the box, so n alone bounds the working
  * memory: the largest layout (3-d, binary32 form, n = 65,536, the cell cap
- * reached) needs about 10.5 MiB of the 12.
+ * reached) needs about 10.8 MiB of the 12.
  *
  * Shared scratch: every call uses the same array, which keeps the last
  * call's contents (each call clears what must start at zero).  Calls whose
@@ -399,10 +399,12 @@ int mtpt_adjoint_backward(mtpt_handle* h, const double* gmass_dev, double* gmass
                           double* dldD);
 
 /* Launch tuning.  cell_scale >= 1 widens every cell to cell_scale x psi
- * (fewer, fuller cells; more candidates per particle); pair_block is the
- * thread-block size of the binary32 pair passes (128 or 256).  Results do not
- * depend on the tuning beyond rounding (the neighbour sums visit the same
- * pairs in a different order). */
+ * (fewer, fuller cells; more candidates per particle); cell_scale = 0.5 makes
+ * the cells half the cutoff wide, a neighbour then up to two cells away per
+ * axis (more, narrower candidate windows closer to the cutoff ball);
+ * pair_block is the thread-block size of the binary32 pair passes (128 or
+ * 256).  Results do not depend on the tuning beyond rounding (the neighbour
+ * sums visit the same pairs in a different order). */
 typedef struct mtpt_tuning {
     double cell_scale;
     int32_t pair_block;
@@ -419,7 +421,7 @@ int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out);
 
 /* Autotuner (no counterpart in the paper): times `trial_steps` full steps
  * (after one warm-up step) of the
- * loaded particles for every cell_scale in {1, 1.25, 1.5, 2} and pair_block
+ * loaded particles for every cell_scale in {0.5, 1, 1.25, 1.5, 2} and pair_block
  * in {128, 256}, keeps the fastest, and restores the particles, masses, step
  * counter and pair counter to their state before the call.  Allocates a
  * temporary snapshot of the state.  *chosen (may be NULL) receives the pick.
@@ -520,6 +522,17 @@ int mtpt_tile_transfer(mtpt_handle* h, int64_t n_recv, const double* recv_dev);
  * handle, the global ids of a tile's natives.  Identification: no
  * counterpart in the paper.  Syncs. */
 int mtpt_get_ids(mtpt_handle* h, uint32_t* out);
+
+/* Failure injection for tests (no counterpart in the paper): from this call
+ * on, the nth device allocation that the library attempts (in this process,
+ * on any handle) fails as if the device were out of memory; nth = 0 turns the
+ * injection off.  *remaining (may be NULL) receives how many allocations the
+ * previous setting still had to go (0: it fired or was off).  A call that
+ * meets the failure returns MTPT_ERR_NO_MEMORY: loads, retuning and the
+ * autotuner leave the handle's particles, counters and tuning as they were;
+ * the adjoint's recording allocates before it steps; time steps allocate
+ * nothing. */
+int mtpt_debug_fail_alloc(int64_t nth, int64_t* remaining);
 
 /* Human-readable text of a status code (static storage).  Error reporting:
  * no counterpart in the paper. */

@@ -77,6 +77,7 @@ struct Grid {
     float lo_f[3];     // lo rounded to binary32 (binary32 cell index)
     float inv_w_f[3];  // 1 / w in binary32
     int cell_f32;      // 1: cell index from binary32 arithmetic (margin in w), 0: binary64
+    int reach;         // cells a neighbour can be away per axis: 1 (w >= psi) or 2 (w >= psi / 2)
     int corner_off[3]; // offset of axis a's corner table in `corners`
 };
 
@@ -412,8 +413,9 @@ __global__ void k_iota(int n, uint32_t* __restrict__ id) {
 }
 
 // ---------------------------------------------------------------------------
-// Step 2a: exclusive prefix sum of the cell counts (three launches:
-// per-tile sums, scan of the tile sums, per-tile scan plus offset).  The
+// Step 2a: exclusive prefix sum of the cell counts (two launches: per-tile
+// sums with the scan of the tile sums by the last tile, then per-tile scan
+// plus offset).  The
 // count array is padded with zeros to whole tiles, so start[n_cells] = n.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
@@ -447,30 +449,41 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return excl;
 }
 
+// Per-tile sums of the counts; the last tile to finish (an atomic ticket,
+// nothing waits) then turns the tile sums into exclusive offsets in place,
+// resets the ticket, and advances the walk's step counter (device-resident,
+// so a captured graph of steps replays with the right counters) when
+// `advance` is set -- every kernel of the step that reads the counter has
+// completed by then.
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_tile_sums(const uint4* __restrict__ count4, uint32_t* __restrict__ tile_sums) {
+k_scan_tiles(const uint4* __restrict__ count4, uint32_t* __restrict__ tile_sums, int ntiles,
+             unsigned int* __restrict__ ticket, unsigned long long* __restrict__ step_dev,
+             int advance) {
     const uint4 v = count4[size_t(blockIdx.x) * kScanThreads + threadIdx.x];
     uint32_t total;
     block_exclusive_scan(v.x + v.y + v.z + v.w, &total);
-    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
-}
-
-// Also advances the walk's step counter (device-resident, so a captured graph
-// of steps replays with the right counters) when `advance` is set; every
-// kernel of the step that reads the counter has completed by then.
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_tile_offsets(uint32_t* __restrict__ tile_sums, int ntiles,
-                    unsigned long long* __restrict__ step_dev, int advance) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        tile_sums[blockIdx.x] = total;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == unsigned(ntiles - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
     uint32_t carry = 0;
     for (int base = 0; base < ntiles; base += kScanThreads) {
         const int t = base + threadIdx.x;
-        const uint32_t v = t < ntiles ? tile_sums[t] : 0u;
-        uint32_t total;
-        const uint32_t excl = block_exclusive_scan(v, &total);
+        const uint32_t c = t < ntiles ? __ldcg(tile_sums + t) : 0u;   // other tiles' writes, via L2
+        uint32_t tot;
+        const uint32_t excl = block_exclusive_scan(c, &tot);
         if (t < ntiles) tile_sums[t] = carry + excl;
-        carry += total;
+        carry += tot;
     }
-    if (advance && threadIdx.x == 0) *step_dev += 1ull;
+    if (threadIdx.x == 0) {
+        *ticket = 0u;
+        if (advance) *step_dev += 1ull;
+    }
 }
 
 // Step counter updates for steps without a scan (walk only) and for resets.
@@ -536,16 +549,15 @@ k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ 
 // own; the rest of the payload comes from the source index.  Also writes the
 // particle's cell, its binary32 offset from the cell corner (from the
 // binary32 head/tail split of the coordinate and of the corner: error below
-// 2^-23 w, no binary64 instruction) and, in the precision form, the mass's
-// head/tail split.
-template <int DIM, bool SPLIT_MASS, class View, bool TANGENT = false>
+// 2^-23 w, no binary64 instruction).
+template <int DIM, class View, bool TANGENT = false>
 __global__ void __launch_bounds__(kBlock)
 k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
          const double2* __restrict__ sortkey, const uint32_t* __restrict__ start,
          const double* __restrict__ pos_in, const double* __restrict__ mass_in,
          uint32_t* __restrict__ id_out, double* __restrict__ pos_out,
          double* __restrict__ mass_out, uint32_t* __restrict__ cell_out,
-         float4* __restrict__ rec_out, float2* __restrict__ msplit_out,
+         float4* __restrict__ rec_out,
          const float2* __restrict__ corners, uint32_t* __restrict__ rid_out,
          const __grid_constant__ View v, const double* __restrict__ tan_in = nullptr,
          double* __restrict__ tan_out = nullptr) {
@@ -579,11 +591,6 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
     if constexpr (View::kBatch) rid_out[dst] = __ldg(v.rid_input + src);
     const RealParams& P = v.of_input(src);
     mass_out[dst] = m;
-    if (SPLIT_MASS) {
-        float hi, lo;
-        split_double(m, &hi, &lo);
-        msplit_out[dst] = make_float2(hi, lo);
-    }
     float off[3] = {0.0f, 0.0f, 0.0f};
     uint32_t rest = c - P.cell_base;
 #pragma unroll
@@ -652,13 +659,13 @@ k_scatter_rec(int n, int64_t stride, const uint32_t* __restrict__ key,
 
 // Gather from the records: the rank inside the cell by (x order key, id)
 // reads chunk 0 of the cell's records; outputs as k_gather's.
-template <int DIM, bool SPLIT_MASS, bool TANGENT>
+template <int DIM, bool TANGENT>
 __global__ void __launch_bounds__(kBlock)
 k_gather_rec(int n, int64_t stride, const double2* __restrict__ recs,
              const uint32_t* __restrict__ start, uint32_t* __restrict__ id_out,
              double* __restrict__ pos_out, double* __restrict__ mass_out,
              uint32_t* __restrict__ cell_out, float4* __restrict__ rec_out,
-             float2* __restrict__ msplit_out, const float2* __restrict__ corners,
+             const float2* __restrict__ corners,
              const __grid_constant__ SingleView v, double* __restrict__ tan_out) {
     using R = SortRec<DIM, TANGENT>;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -691,11 +698,6 @@ k_gather_rec(int n, int64_t stride, const double2* __restrict__ recs,
     const RealParams& P = v.p;
     const double m = lane[DIM + 1];
     mass_out[dst] = m;
-    if (SPLIT_MASS) {
-        float hi, lo;
-        split_double(m, &hi, &lo);
-        msplit_out[dst] = make_float2(hi, lo);
-    }
     float off[3] = {0.0f, 0.0f, 0.0f};
     uint32_t rest = c - P.cell_base;
 #pragma unroll
@@ -769,8 +771,8 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 }
 
 // Binary32 x difference of candidate o from particle me (cells cx_o - cx_me
-// apart, |cx_o - cx_me| <= 1 so the shift is exact): changes sign exactly
-// when the pair swaps.
+// apart, |cx_o - cx_me| <= reach <= 2, so the shift is a power-of-two multiple
+// of wx and exact): changes sign exactly when the pair swaps.
 __device__ __forceinline__ float dx_f32(const float4& me, const float4& o, float wx) {
     return __fadd_rn(__fsub_rn(o.x, me.x), __fmul_rn(__fsub_rn(o.w, me.w), wx));
 }
@@ -785,8 +787,22 @@ __device__ __forceinline__ float d2_f32(float dx, const float4& me, const float4
     return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
 }
 
+// Lower bound of |dy_f| over the particles of the row `d` cells away along an
+// axis (d = 0: the particle's own row, bound 0): the rows below hold offsets
+// up to w from their cells' corners, those above offsets from 0, so the gap
+// is the particle's own offset (or w minus it) plus |d| - 1 whole cells, less
+// the slack that covers the roundings.
+__device__ __forceinline__ float row_gap(int d, float off, float w, float eps) {
+    if (d == 0) return 0.0f;
+    const float near = d < 0 ? off : __fsub_rn(w, off);
+    const int far = d < 0 ? -d - 1 : d - 1;
+    const float gap = far == 0 ? near : __fmaf_rn(float(far), w, near);
+    return fmaxf(__fsub_rn(gap, eps), 0.0f);
+}
+
 // Per-row candidate windows.  Row (dy, dz) of particle s is the particle
-// range [j0, j3) of cells cx-1..cx+1 at y index cy+dy (z index cz+dz); the
+// range [j0, j3) of cells cx-R..cx+R at y index cy+dy (z index cz+dz), R the
+// grid's reach (|dy|, |dz| <= R); the
 // gather sorts it by x up to a slack.  Every accepted candidate has
 // d2f <= band_hi, so with g a lower bound of |dy_f| (and |dz_f|) over the row
 // its binary32 dx satisfies dx^2 <= reach2 - g^2 (reach2 carries the
@@ -815,26 +831,21 @@ __device__ __forceinline__ void for_each_row(uint32_t cell, const float4& me,
             rest /= uint32_t(g.n[a]);
         }
     }
-    const int xlo = c[0] > 0 ? c[0] - 1 : 0;
-    const int xhi = c[0] < g.n[0] - 1 ? c[0] + 1 : c[0];
-    const int zlo = DIM == 3 ? (c[2] > 0 ? -1 : 0) : 0;
-    const int zhi = DIM == 3 ? (c[2] < g.n[2] - 1 ? 1 : 0) : 0;
-    const int ylo = DIM >= 2 ? (c[1] > 0 ? -1 : 0) : 0;
-    const int yhi = DIM >= 2 ? (c[1] < g.n[1] - 1 ? 1 : 0) : 0;
+    const int R = g.reach;
+    const int xlo = max(c[0] - R, 0);
+    const int xhi = min(c[0] + R, g.n[0] - 1);
+    const int zlo = DIM == 3 ? max(-R, -c[2]) : 0;
+    const int zhi = DIM == 3 ? min(R, g.n[2] - 1 - c[2]) : 0;
+    const int ylo = DIM >= 2 ? max(-R, -c[1]) : 0;
+    const int yhi = DIM >= 2 ? min(R, g.n[1] - 1 - c[1]) : 0;
     const float eps = pp.trim_eps;
-    // lower bounds of |dy_f| over the rows below and above (likewise z): a
-    // row below holds offsets <= w, one above offsets >= 0, up to the slack
-    const float gy_below = DIM >= 2 ? fmaxf(__fsub_rn(me.y, eps), 0.0f) : 0.0f;
-    const float gy_above = DIM >= 2 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[1], me.y), eps), 0.0f) : 0.0f;
-    const float gz_below = DIM == 3 ? fmaxf(__fsub_rn(me.z, eps), 0.0f) : 0.0f;
-    const float gz_above = DIM == 3 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[2], me.z), eps), 0.0f) : 0.0f;
     const float wx = g.wf[0];
     for (int dz = zlo; dz <= zhi; ++dz) {
         const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
-        const float gz = dz < 0 ? gz_below : (dz > 0 ? gz_above : 0.0f);
+        const float gz = DIM == 3 ? row_gap(dz, me.z, g.wf[2], eps) : 0.0f;
         for (int dy = ylo; dy <= yhi; ++dy) {
             const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
-            const float gy = dy < 0 ? gy_below : (dy > 0 ? gy_above : 0.0f);
+            const float gy = DIM >= 2 ? row_gap(dy, me.y, g.wf[1], eps) : 0.0f;
             const float r2 = __fsub_rn(pp.reach2, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
             if (r2 < 0.0f) continue;
             const float rx = __fadd_rn(sqrt_approx(r2), eps);
@@ -1103,20 +1114,17 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
             rest /= uint32_t(g.n[a]);
         }
     }
-    const int xlo = c[0] > 0 ? c[0] - 1 : 0;
-    const int xhi = c[0] < g.n[0] - 1 ? c[0] + 1 : c[0];
+    const int R = g.reach;
+    const int xlo = max(c[0] - R, 0);
+    const int xhi = min(c[0] + R, g.n[0] - 1);
     const float eps = pp.trim_eps;
-    const float gy_below = DIM >= 2 ? fmaxf(__fsub_rn(me.y, eps), 0.0f) : 0.0f;
-    const float gy_above = DIM >= 2 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[1], me.y), eps), 0.0f) : 0.0f;
-    const float gz_below = DIM == 3 ? fmaxf(__fsub_rn(me.z, eps), 0.0f) : 0.0f;
-    const float gz_above = DIM == 3 ? fmaxf(__fsub_rn(__fsub_rn(g.wf[2], me.z), eps), 0.0f) : 0.0f;
     const float wx = g.wf[0];
     // rows in a fixed order for the whole warp; a lane whose row is outside
     // the grid or beyond the cutoff (see for_each_row) gets an empty window
 #pragma unroll 1
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+    for (int dz = (DIM == 3 ? -R : 0); dz <= (DIM == 3 ? R : 0); ++dz) {
 #pragma unroll 1
-        for (int dy = (DIM >= 2 ? -1 : 0); dy <= (DIM >= 2 ? 1 : 0); ++dy) {
+        for (int dy = (DIM >= 2 ? -R : 0); dy <= (DIM >= 2 ? R : 0); ++dy) {
             const float sy = DIM >= 2 ? float(dy) * g.wf[1] : 0.0f;
             const float sz = DIM == 3 ? float(dz) * g.wf[2] : 0.0f;
             uint32_t j = 0, j3 = 0;
@@ -1124,8 +1132,8 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
             const bool in_grid = valid && (DIM < 2 || (c[1] + dy >= 0 && c[1] + dy < g.n[1])) &&
                                  (DIM < 3 || (c[2] + dz >= 0 && c[2] + dz < g.n[2]));
             if (in_grid) {
-                const float gy = dy < 0 ? gy_below : (dy > 0 ? gy_above : 0.0f);
-                const float gz = dz < 0 ? gz_below : (dz > 0 ? gz_above : 0.0f);
+                const float gy = DIM >= 2 ? row_gap(dy, me.y, g.wf[1], eps) : 0.0f;
+                const float gz = DIM == 3 ? row_gap(dz, me.z, g.wf[2], eps) : 0.0f;
                 const float r2 = __fsub_rn(pp.reach2, __fmaf_rn(gy, gy, __fmul_rn(gz, gz)));
                 if (r2 >= 0.0f) {
                     rx = __fadd_rn(sqrt_approx(r2), eps);
@@ -1282,15 +1290,17 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
 }
 
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
-// hardware ex2, compensated binary32 row sum, rounded to binary32 into r_out;
+// hardware ex2, compensated binary32 row sum, rounded to binary32; written
+// with the binary32 head/tail split of the mass as the particle's record
+// ex[s] = {m_hi, m_lo, r, 0} that pass 2 reads once per neighbour;
 // with nb.cap > 0 also the neighbour lists of pass 2 (accepted j != s with
 // their K, in visiting order: the band's exact accepts come last).
 template <int DIM, class View, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (DIM == 3 ? 1536 : 2048) / BLOCK)
 k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
              const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
-             const __grid_constant__ View v, float* __restrict__ r_out,
-             unsigned long long* __restrict__ pair_counter,
+             const __grid_constant__ View v, const double* __restrict__ mass,
+             float4* __restrict__ ex, unsigned long long* __restrict__ pair_counter,
              const uint32_t* __restrict__ ghost_id, NbList32 nb) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t cnt = 0;
@@ -1322,7 +1332,9 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
             rsum = 1.0f;
         }
         if (nb.cap > 0) nb.count[s] = listed;
-        r_out[s] = __fsub_rn(rsum, rc);
+        float mhi, mlo;
+        split_double(mass[s], &mhi, &mlo);
+        ex[s] = make_float4(mhi, mlo, __fsub_rn(rsum, rc), 0.0f);
         // with ghost_id (a tile), pairs are counted for the tile's own particles only
         if (ghost_id && (ghost_id[s] & kGhostBit)) cnt = 0;
     }
@@ -1335,17 +1347,15 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
 // The flux sum of pass 2, precision form: W = 2 beta K / (r_s + r_j) in
 // binary32 (symmetric bit for bit), the mass difference from the binary32
 // head/tail split (exactly antisymmetric), compensated accumulation, and the
-// update in binary64.
+// update in binary64.  Each particle's record ex = {m_hi, m_lo, r, 0} is one
+// 16-byte load per neighbour.
 struct FluxSum {
     float rs, two_beta;
     float2 ms;
     float acc = 0.0f, comp = 0.0f;
-    __device__ __forceinline__ void add(const float* __restrict__ r,
-                                        const float2* __restrict__ msplit, uint32_t j, float K,
-                                        bool accept = true) {
-        const float W = __fdividef(two_beta * K, __fadd_rn(rs, __ldg(r + j)));
-        const float2 mj = __ldg(msplit + j);
-        const float dm = __fadd_rn(__fsub_rn(mj.x, ms.x), __fsub_rn(mj.y, ms.y));
+    __device__ __forceinline__ void add(const float4& xj, float K, bool accept = true) {
+        const float W = __fdividef(two_beta * K, __fadd_rn(rs, xj.z));
+        const float dm = __fadd_rn(__fsub_rn(xj.x, ms.x), __fsub_rn(xj.y, ms.y));
         // a rejected candidate (and the self pair) adds an exact zero
         neumaier_add(acc, comp, accept ? __fmul_rn(dm, W) : 0.0f);
     }
@@ -1365,30 +1375,28 @@ __device__ __noinline__ float2 search_flux(uint32_t s, int64_t stride,
                                            const float4* __restrict__ rec,
                                            const uint32_t* __restrict__ cell,
                                            const uint32_t* __restrict__ start, const View& v,
-                                           const float* __restrict__ r,
-                                           const float2* __restrict__ msplit, float rs, float2 ms,
+                                           const float4* __restrict__ ex, float rs, float2 ms,
                                            float two_beta) {
     const RealParams& P = v.of_sorted(s);
     const float na = -P.pp.a_log2e;
     FluxSum g{rs, two_beta, ms};
     scan_neighbours<DIM, true>(s, cell[s], stride, rec, pos, start, P,
                          [&](uint32_t j, float d2f, bool accept) {
-                             g.add(r, msplit, j, ex2_approx(na * d2f), accept);
+                             g.add(__ldg(ex + j), ex2_approx(na * d2f), accept);
                          });
     return make_float2(g.acc, g.comp);
 }
 
 // Pass 2, precision form: each particle walks its neighbour list (the
-// accepted neighbours only, with pass 1's K), or searches when it has none
-// (no lists, or an overflowing one).  Both add the same terms in the same
-// order.
+// accepted neighbours only, with pass 1's K), two entries at a time so two
+// gathers are in flight, or searches when it has none (no lists, or an
+// overflowing one).  Both add the same terms in the same order.
 template <int DIM, class View, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
-               const __grid_constant__ View v, const float* __restrict__ r,
-               const float2* __restrict__ msplit, const double* __restrict__ mass,
-               double* __restrict__ mass_out, NbList32 nb) {
+               const __grid_constant__ View v, const float4* __restrict__ ex,
+               const double* __restrict__ mass, double* __restrict__ mass_out, NbList32 nb) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const RealParams& P = v.of_sorted(uint32_t(s));
@@ -1396,17 +1404,25 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
         mass_out[s] = mass[s];
         return;
     }
-    FluxSum f{r[s], float(2.0 * P.pp.beta), msplit[s]};   // beta folded into W (still symmetric)
+    const float4 xs = ex[s];
+    FluxSum f{xs.z, float(2.0 * P.pp.beta), make_float2(xs.x, xs.y)};   // beta folded into W
     const uint32_t listed = nb.cap > 0 ? nb.count[s] : 0xffffffffu;
     if (listed <= uint32_t(nb.cap)) {
         const uint2* e = nb.e + s;
-        for (uint32_t k = 0; k < listed; ++k, e += stride) {
+        uint32_t k = 0;
+        for (; k + 2 <= listed; k += 2, e += 2 * stride) {
+            const uint2 q0 = __ldg(e), q1 = __ldg(e + stride);
+            const float4 x0 = __ldg(ex + q0.x), x1 = __ldg(ex + q1.x);
+            f.add(x0, __uint_as_float(q0.y));
+            f.add(x1, __uint_as_float(q1.y));
+        }
+        if (k < listed) {
             const uint2 q = __ldg(e);
-            f.add(r, msplit, q.x, __uint_as_float(q.y));
+            f.add(__ldg(ex + q.x), __uint_as_float(q.y));
         }
     } else {
-        const float2 sum = search_flux<DIM>(uint32_t(s), stride, pos, rec, cell, start, v, r,
-                                            msplit, f.rs, f.ms, f.two_beta);
+        const float2 sum = search_flux<DIM>(uint32_t(s), stride, pos, rec, cell, start, v, ex,
+                                            f.rs, f.ms, f.two_beta);
         f.acc = sum.x;
         f.comp = sum.y;
     }

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -59,20 +60,41 @@ void report_cuda_error(cudaError_t err, const char* expr, int line) {
         if (rc_ != MTPT_OK) return rc_; \
     } while (0)
 
+// Failure injection for the tests (mtpt_debug_fail_alloc): when positive,
+// the countdown's allocation fails as if the device were out of memory.
+std::atomic<int64_t> g_fail_alloc{0};
+
+bool injected_alloc_failure() {
+    int64_t v = g_fail_alloc.load();
+    while (v > 0)
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 1;
+    return false;
+}
+
+// Every device allocation of the library goes through here.
+int device_alloc(void** out, size_t bytes) {
+    *out = nullptr;
+    if (injected_alloc_failure()) return MTPT_ERR_NO_MEMORY;
+    if (cudaMalloc(out, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *out = nullptr;
+        return MTPT_ERR_NO_MEMORY;
+    }
+    return MTPT_OK;
+}
+
+// A device buffer that only grows.  A growth allocates before it releases,
+// so a failed one leaves the old buffer (and its contents) in place.
 template <typename T>
 struct DevBuf {
     T* p = nullptr;
     size_t count = 0;
     int ensure(size_t n) {
-        if (n <= count && p) return MTPT_OK;
+        if (n == 0 || (n <= count && p)) return MTPT_OK;
+        void* q = nullptr;
+        MTPT_TRY(device_alloc(&q, n * sizeof(T)));
         release();
-        if (n == 0) return MTPT_OK;
-        if (cudaMalloc(reinterpret_cast<void**>(&p), n * sizeof(T)) != cudaSuccess) {
-            (void)cudaGetLastError();
-            p = nullptr;
-            count = 0;
-            return MTPT_ERR_NO_MEMORY;
-        }
+        p = static_cast<T*>(q);
         count = n;
         return MTPT_OK;
     }
@@ -80,6 +102,53 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         count = 0;
+    }
+};
+
+// Grows several buffers all or nothing: every new allocation is made before
+// any old buffer is released, and after a failure nothing has changed.
+struct GrowAll {
+    struct Item { void** p; size_t* count; void* q; size_t n; };
+    static constexpr int kMax = 48;
+    Item items[kMax];
+    int k = 0;
+    int rc = MTPT_OK;
+    template <typename T>
+    void want(DevBuf<T>& b, size_t n) {
+        if (rc != MTPT_OK || n == 0 || (n <= b.count && b.p)) return;
+        if (k == kMax) {
+            rc = MTPT_ERR_NO_MEMORY;
+            return;
+        }
+        void* q = nullptr;
+        rc = device_alloc(&q, n * sizeof(T));
+        if (rc == MTPT_OK) items[k++] = {reinterpret_cast<void**>(&b.p), &b.count, q, n};
+    }
+    bool grows() const { return k > 0; }
+    // Installs the new buffers; the old ones are freed, or, with keep_old,
+    // kept (in `olds`) until release_old(), so their contents can be copied.
+    void* olds[kMax];
+    int nold = 0;
+    int commit(bool keep_old = false) {
+        if (rc != MTPT_OK) {
+            for (int i = 0; i < k; ++i) cudaFree(items[i].q);
+            k = 0;
+            return rc;
+        }
+        for (int i = 0; i < k; ++i) {
+            if (*items[i].p) {
+                if (keep_old) olds[nold++] = *items[i].p;
+                else cudaFree(*items[i].p);
+            }
+            *items[i].p = items[i].q;
+            *items[i].count = items[i].n;
+        }
+        k = 0;
+        return MTPT_OK;
+    }
+    void release_old() {
+        for (int i = 0; i < nold; ++i) cudaFree(olds[i]);
+        nold = 0;
     }
 };
 
@@ -154,8 +223,7 @@ struct mtpt_handle {
     DevBuf<uint32_t> id_first;
     DevBuf<RealParams> params_dev;
     DevBuf<double> r64;
-    DevBuf<float> r32;
-    DevBuf<float2> msplit;
+    DevBuf<float4> ex;                // precision form: {m_hi, m_lo, r, 0} per particle
     DevBuf<uint32_t> nb_j, nb_count;      // binary64 form neighbour lists
     DevBuf<double> nb_k;
     int nb_cap = 0;
@@ -364,8 +432,12 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
         dc = std::max(dc, 3.0 * u * (B + (p.hi[a] - p.lo[a])) / R.psi);
     }
     g.cell_f32 = (P.transfer && dc <= 1e-2) ? 1 : 0;
+    // scale 1/2: cells half the cutoff wide, neighbours up to two cells away
+    // (reach 2); a reach of R needs R w >= psi plus twice the cell index's
+    // error, dc psi in length, on both sides: w >= psi (1 + 2 dc) / R
+    g.reach = scale < 1.0 ? 2 : 1;
     const double widen = g.cell_f32 ? 1.0 / (1.0 - 2.0 * dc) : 1.0;
-    const double psi_eff = R.psi * widen * scale * (1.0 + 1e-9);
+    const double psi_eff = R.psi * widen * (g.reach == 2 ? 0.5 : scale) * (1.0 + 1e-9);
     double ncell[3] = {1, 1, 1};
     for (int a = 0; a < p.dim; ++a) {
         const double L = p.hi[a] - p.lo[a];
@@ -435,7 +507,10 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
     // for every candidate within reach of the cutoff.  Twice that bound is the
     // band half-width eta.
     PairParams& pp = P.pp;
-    const double eta = 2.0 * (u * (3.0 + 14.0 * (1.0 + dc) * sum_w) + std::ldexp(sum_b, -43)) + 1e-14;
+    // (with reach 2 the x difference can span three cells instead of two, one
+    // more u w in its bound: 2 (6 + reach) in place of 14)
+    const double kdx = 2.0 * (6.0 + g.reach);
+    const double eta = 2.0 * (u * (3.0 + kdx * (1.0 + dc) * sum_w) + std::ldexp(sum_b, -43)) + 1e-14;
     R.band_eta = eta;
     pp.psi2 = R.psi2;
     pp.band_lo = std::nextafter(float(R.psi2 * (1.0 - eta)), 0.0f);
@@ -453,8 +528,9 @@ int setup_grid(RealHost& R, RealParams& P, int64_t cell_base, int corner_base, d
         double eps = 0.0;
         for (int a = 0; a < p.dim; ++a) {
             const double B = std::max(std::fabs(p.lo[a]), std::fabs(p.hi[a])) + g.w[a];
-            eps = std::max(eps, 2.0 * (2.0 * dc_cells * g.w[a] + std::ldexp(g.w[a], -16) +
-                                       std::ldexp(B, -40)));
+            // the cell index's error is dc_cells psi in length, whatever w is
+            eps = std::max(eps, 2.0 * (2.0 * dc_cells * std::max(g.w[a], R.psi) +
+                                       std::ldexp(g.w[a], -16) + std::ldexp(B, -40)));
         }
         pp.trim_eps = std::nextafter(float(eps), INFINITY);
     }
@@ -541,59 +617,100 @@ int build_corners(mtpt_handle* h, const RealParams* params_dev, const int* first
     return MTPT_OK;
 }
 
-int ensure_capacity(mtpt_handle* h, int64_t n) {
+// Payload-record chunks per particle of the record sort, tangents included
+// (the adjoint's), so one allocation serves every record sort.
+int64_t sort_rec_chunks(int dim) { return (2 + 2 * dim + 1) / 2; }
+
+// State and per-step buffers for n particles, grown all or nothing (a failed
+// growth leaves the handle's state and buffers as they were).  A growth
+// carries the first `keep` particles of the current state half over into the
+// new buffers, so a later failure of the same load can still go back to
+// them.  The record sort's buffer of a single run is grown here too, so no
+// step allocates.
+int ensure_capacity(mtpt_handle* h, int64_t n, int64_t keep = 0) {
     const int d = h->dim;
     const int64_t cap = std::max<int64_t>(n, 1);
+    const int c = h->cur;
+    const int64_t old_cap = h->cap;
+    const double* old_pos = h->pos[c].p;
+    const double* old_mass = h->mass[c].p;
+    const uint32_t* old_id = h->id[c].p;
+    const uint32_t* old_rid = h->rid[c].p;
+    GrowAll g;
     if (cap > h->cap) {
-        drop_graph(h);
         for (int b = 0; b < 2; ++b) {
-            MTPT_TRY(h->pos[b].ensure(size_t(d) * cap));
-            MTPT_TRY(h->mass[b].ensure(cap));
-            MTPT_TRY(h->id[b].ensure(cap));
-            if (h->batch) MTPT_TRY(h->rid[b].ensure(cap));
+            g.want(h->pos[b], size_t(d) * cap);
+            g.want(h->mass[b], size_t(cap));
+            g.want(h->id[b], size_t(cap));
+            if (h->batch) g.want(h->rid[b], size_t(cap));
         }
-        MTPT_TRY(h->key.ensure(cap));
-        MTPT_TRY(h->perm.ensure(cap));
-        MTPT_TRY(h->sortkey.ensure(cap));
-        MTPT_TRY(h->cell.ensure(cap));
-        MTPT_TRY(h->rec.ensure(cap));
-        if (h->precision == MTPT_FP64) {
-            MTPT_TRY(h->r64.ensure(cap));
-        } else {
-            MTPT_TRY(h->msplit.ensure(cap));
-            MTPT_TRY(h->r32.ensure(cap));
-        }
-        h->cap = cap;
+        g.want(h->key, size_t(cap));
+        g.want(h->perm, size_t(cap));
+        g.want(h->sortkey, size_t(cap));
+        g.want(h->cell, size_t(cap));
+        g.want(h->rec, size_t(cap));
+        if (h->precision == MTPT_FP64) g.want(h->r64, size_t(cap));
+        else g.want(h->ex, size_t(cap));
     }
-    MTPT_TRY(h->status.ensure(1));
-    MTPT_TRY(h->pair_counter.ensure(1));
-    MTPT_TRY(h->step_dev.ensure(1));
+    if (!h->batch) g.want(h->sortrec, size_t(sort_rec_chunks(d)) * size_t(std::max(cap, h->cap)));
+    g.want(h->status, 1);
+    g.want(h->pair_counter, 1);
+    g.want(h->step_dev, 1);
+    if (g.grows()) drop_graph(h);
+    const bool carry = keep > 0 && cap > old_cap && old_pos;
+    MTPT_TRY(g.commit(carry));
+    if (carry) {
+        const size_t row = size_t(keep) * sizeof(double);
+        int rc = MTPT_OK;
+        if (cudaMemcpy2DAsync(h->pos[c].p, size_t(cap) * sizeof(double), old_pos,
+                              size_t(old_cap) * sizeof(double), row, size_t(d),
+                              cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+            cudaMemcpyAsync(h->mass[c].p, old_mass, row, cudaMemcpyDeviceToDevice,
+                            h->stream) != cudaSuccess ||
+            cudaMemcpyAsync(h->id[c].p, old_id, size_t(keep) * 4, cudaMemcpyDeviceToDevice,
+                            h->stream) != cudaSuccess ||
+            (h->batch && old_rid &&
+             cudaMemcpyAsync(h->rid[c].p, old_rid, size_t(keep) * 4, cudaMemcpyDeviceToDevice,
+                             h->stream) != cudaSuccess) ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            (void)cudaGetLastError();
+            rc = MTPT_ERR_CUDA;
+        }
+        g.release_old();
+        MTPT_TRY(rc);
+    }
+    if (cap > h->cap) h->cap = cap;
     return MTPT_OK;
 }
 
+// The cell-count scan's ticket: the word after the tile sums (zero between
+// scans; the last tile of each scan resets it).
+unsigned int* scan_ticket(mtpt_handle* h) {
+    return reinterpret_cast<unsigned int*>(h->tile_sums.p + h->n_cells_pad / kScanTile);
+}
+
+// The cell list's arrays for the current grid, grown all or nothing.
 int ensure_cells(mtpt_handle* h) {
     const size_t padded = size_t(h->n_cells_pad);
-    if (padded > h->count.count) {
-        drop_graph(h);
-        MTPT_TRY(h->count.ensure(padded));
-        MTPT_TRY(h->start.ensure(padded));
-        MTPT_TRY(h->tile_sums.ensure(padded / kScanTile));
-    }
-    if (size_t(std::max(h->n_corners, 1)) > h->corners.count) drop_graph(h);
-    MTPT_TRY(h->corners.ensure(size_t(std::max(h->n_corners, 1))));
+    GrowAll g;
+    g.want(h->count, padded);
+    g.want(h->start, padded);
+    g.want(h->tile_sums, padded / kScanTile + 1);   // + the scan's ticket
+    g.want(h->corners, size_t(std::max(h->n_corners, 1)));
     if (h->nb_cap > 0) {
         const size_t slots = size_t(h->nb_cap) * size_t(h->cap);
-        if (slots > h->nb_j.count || size_t(h->cap) > h->nb_count.count) drop_graph(h);
-        MTPT_TRY(h->nb_j.ensure(slots));
-        MTPT_TRY(h->nb_k.ensure(slots));
-        MTPT_TRY(h->nb_count.ensure(size_t(h->cap)));
+        g.want(h->nb_j, slots);
+        g.want(h->nb_k, slots);
+        g.want(h->nb_count, size_t(h->cap));
     }
     if (h->nb32_cap > 0) {
-        const size_t slots = size_t(h->nb32_cap) * size_t(h->cap);
-        if (slots > h->nb32_e.count || size_t(h->cap) > h->nb32_count.count) drop_graph(h);
-        MTPT_TRY(h->nb32_e.ensure(slots));
-        MTPT_TRY(h->nb32_count.ensure(size_t(h->cap)));
+        g.want(h->nb32_e, size_t(h->nb32_cap) * size_t(h->cap));
+        g.want(h->nb32_count, size_t(h->cap));
     }
+    if (g.grows()) drop_graph(h);
+    MTPT_TRY(g.commit());
+    // the ticket sits after this grid's tile sums: zero it wherever that is now
+    MTPT_CUDA_TRY(cudaMemsetAsync(scan_ticket(h), 0, sizeof(unsigned int), h->stream));
     // counts start (and, after each scatter, end) at zero
     MTPT_CUDA_TRY(cudaMemsetAsync(h->count.p, 0, padded * sizeof(uint32_t), h->stream));
     return MTPT_OK;
@@ -689,16 +806,10 @@ int launch_sort_t(mtpt_handle* h, int c, int o, const View& vin) {
         MTPT_CUDA_TRY(cudaGetLastError());
     }
     MTPT_TIMED(h, "gather");
-    if (h->precision == MTPT_FP32W)
-        k_gather<DIM, true, View, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->perm.p, h->sortkey.p, h->start.p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->msplit.p,
-            h->corners.p, rid_out, vin, tan_in, tan_out);
-    else
-        k_gather<DIM, false, View, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->perm.p, h->sortkey.p, h->start.p, h->pos[c].p, h->mass[c].p,
-            h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, nullptr, h->corners.p,
-            rid_out, vin, tan_in, tan_out);
+    k_gather<DIM, View, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
+        n, stride, h->perm.p, h->sortkey.p, h->start.p, h->pos[c].p, h->mass[c].p, h->id[o].p,
+        h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->corners.p, rid_out, vin, tan_in,
+        tan_out);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -720,14 +831,9 @@ int launch_sort_rec(mtpt_handle* h, int c, int o, const SingleView& vin) {
     }
     MTPT_TIMED(h, "gather");
     double* tan_out = TANGENT ? h->tan[o].p : nullptr;
-    if (h->precision == MTPT_FP32W)
-        k_gather_rec<DIM, true, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->sortrec.p, h->start.p, h->id[o].p, h->pos[o].p, h->mass[o].p,
-            h->cell.p, h->rec.p, h->msplit.p, h->corners.p, vin, tan_out);
-    else
-        k_gather_rec<DIM, false, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
-            n, stride, h->sortrec.p, h->start.p, h->id[o].p, h->pos[o].p, h->mass[o].p,
-            h->cell.p, h->rec.p, nullptr, h->corners.p, vin, tan_out);
+    k_gather_rec<DIM, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
+        n, stride, h->sortrec.p, h->start.p, h->id[o].p, h->pos[o].p, h->mass[o].p, h->cell.p,
+        h->rec.p, h->corners.p, vin, tan_out);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -757,13 +863,14 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
     {
         MTPT_TIMED(h, "rowsum_f32");
         k_rowsum_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
-            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->r32.p, h->pair_counter.p,
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->mass[o].p, h->ex.p,
+            h->pair_counter.p,
             h->ntiles > 0 ? h->id[o].p : nullptr, nb);
     }
     MTPT_TIMED(h, "exchange_f32");
     k_exchange_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
-        n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->r32.p, h->msplit.p,
-        h->mass[o].p, h->mass[c].p, nb);
+        n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
+        h->mass[c].p, nb);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -824,13 +931,10 @@ int launch_step(mtpt_handle* h, int flags) {
     const int ntiles = int(h->n_cells_pad / kScanTile);
     const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
     {
-        MTPT_TIMED(h, "scan_tile_sums");
-        k_scan_tile_sums<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p);
-    }
-    {
-        MTPT_TIMED(h, "scan_tile_offsets");
-        k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(h->tile_sums.p, ntiles, h->step_dev.p,
-                                                        advance ? 1 : 0);
+        MTPT_TIMED(h, "scan_tiles");
+        k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p, ntiles,
+                                                      scan_ticket(h), h->step_dev.p,
+                                                      advance ? 1 : 0);
     }
     {
         MTPT_TIMED(h, "scan_apply");
@@ -986,11 +1090,79 @@ int set_step_dev(mtpt_handle* h, uint64_t step) {
     return MTPT_OK;
 }
 
+// Host-side bookkeeping of a handle's particles and grid, saved before a load
+// or a retuning and put back when that fails part of the way (the device
+// buffers grow all or nothing and never lose the state they hold).
+struct HostSnapshot {
+    std::vector<RealHost> reals;
+    std::vector<RealParams> params;
+    int64_t n = 0, n_cells = 0, n_cells_pad = 0;
+    int n_corners = 0, nb_cap = 0, nb32_cap = 0, adj_cap = 0, cur = 0, pair_block = 256;
+    bool any_transfer = false, any_walk = false, any_advect = false, fresh = false;
+    bool have_row_sums = false, have_particles = false, adj_ready = false;
+    uint64_t step = 0;
+    double cell_scale = 1.0;
+
+    bool take(const mtpt_handle* h) {
+        try {
+            reals.assign(h->reals, h->reals + h->nreal);
+            params.assign(h->params, h->params + h->nreal);
+        } catch (...) {
+            return false;
+        }
+        n = h->n; n_cells = h->n_cells; n_cells_pad = h->n_cells_pad;
+        n_corners = h->n_corners; nb_cap = h->nb_cap; nb32_cap = h->nb32_cap;
+        adj_cap = h->adj_cap; cur = h->cur; pair_block = h->pair_block;
+        any_transfer = h->any_transfer; any_walk = h->any_walk; any_advect = h->any_advect;
+        fresh = h->fresh; have_row_sums = h->have_row_sums; have_particles = h->have_particles;
+        adj_ready = h->adj_ready; step = h->step; cell_scale = h->cell_scale;
+        return true;
+    }
+    void put(mtpt_handle* h) const {
+        std::copy(reals.begin(), reals.end(), h->reals);
+        std::copy(params.begin(), params.end(), h->params);
+        h->n = n; h->n_cells = n_cells; h->n_cells_pad = n_cells_pad;
+        h->n_corners = n_corners; h->nb_cap = nb_cap; h->nb32_cap = nb32_cap;
+        h->adj_cap = adj_cap; h->cur = cur; h->pair_block = pair_block;
+        h->any_transfer = any_transfer; h->any_walk = any_walk; h->any_advect = any_advect;
+        h->fresh = fresh; h->have_row_sums = have_row_sums; h->have_particles = have_particles;
+        h->adj_ready = adj_ready; h->step = step; h->cell_scale = cell_scale;
+    }
+};
+
+// Puts a snapshot back and rebuilds the device tables of its grid (cell
+// counts at zero, corner tables, realisation table): the arrays only grew,
+// so this allocates nothing.
+int restore_snapshot(mtpt_handle* h, const HostSnapshot& snap) {
+    snap.put(h);
+    drop_graph(h);
+    if (!h->have_particles) return MTPT_OK;
+    if (h->any_transfer) MTPT_TRY(ensure_cells(h));
+    return upload_tables(h);
+}
+
+int load_particles_body(mtpt_handle* h, const int64_t* counts, const double* pos,
+                        const double* mass, cudaMemcpyKind kind, int in_place);
+
 // Loads particles (counts[k] per realisation, concatenated) from host or
-// device buffers.
+// device buffers.  A load that fails before the new particles are in place
+// (an allocation, a grid too large) leaves the old state as it was.
 int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, const double* mass,
                    cudaMemcpyKind kind, int in_place = -1) {
+    HostSnapshot snap;
+    const bool saved = h->have_particles && snap.take(h);
+    const int rc = load_particles_body(h, counts, pos, mass, kind, in_place);
+    if (rc != MTPT_OK && saved && restore_snapshot(h, snap) != MTPT_OK) {
+        h->have_particles = false;   // the old grid's tables could not be rebuilt
+        h->n = 0;
+    }
+    return rc;
+}
+
+int load_particles_body(mtpt_handle* h, const int64_t* counts, const double* pos,
+                        const double* mass, cudaMemcpyKind kind, int in_place) {
     const int d = h->dim;
+    const int64_t held = h->have_particles ? h->n : 0;   // carried over if buffers grow
     int64_t n = 0;
     for (int k = 0; k < h->nreal; ++k) {
         if (counts[k] < 0) return MTPT_ERR_INVALID_ARG;
@@ -1005,7 +1177,7 @@ int load_particles(mtpt_handle* h, const int64_t* counts, const double* pos, con
         off += counts[k];
     }
     h->n = n;
-    MTPT_TRY(ensure_capacity(h, n));
+    MTPT_TRY(ensure_capacity(h, n, held));
     MTPT_TRY(setup_grids(h));
     if (h->any_transfer) MTPT_TRY(ensure_cells(h));
     drop_graph(h);
@@ -1288,8 +1460,8 @@ int launch_emit(mtpt_handle* h, int64_t cap) {
                                                             h->count.p, h->status.p);
     const int ntiles = int(h->n_cells_pad / kScanTile);
     const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
-    k_scan_tile_sums<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p);
-    k_scan_tile_offsets<<<1, kScanThreads, 0, h->stream>>>(h->tile_sums.p, ntiles, h->step_dev.p, 0);
+    k_scan_tiles<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p, ntiles,
+                                                         scan_ticket(h), h->step_dev.p, 0);
     k_scan_apply<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p,
                                                          reinterpret_cast<uint4*>(h->start.p));
     MTPT_TRY((launch_sort<DIM, View>(h, c, o, vin)));
@@ -1393,8 +1565,8 @@ int launch_adjoint_step(mtpt_handle* h) {
             h->key.p, h->count.p, h->status.p, h->tan[c].p);
     const int ntiles = int(h->n_cells_pad / kScanTile);
     const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
-    k_scan_tile_sums<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p);
-    k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(h->tile_sums.p, ntiles, h->step_dev.p, 1);
+    k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p, ntiles, scan_ticket(h),
+                                                  h->step_dev.p, 1);
     k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p,
                                                   reinterpret_cast<uint4*>(h->start.p));
     MTPT_CUDA_TRY(cudaGetLastError());
@@ -1553,7 +1725,7 @@ int mtpt_destroy(mtpt_handle* h) {
     h->key.release(); h->perm.release(); h->sortkey.release(); h->sortrec.release(); h->cell.release(); h->count.release();
     h->start.release(); h->tile_sums.release(); h->rec.release(); h->corners.release();
     h->corner_first.release(); h->id_first.release(); h->params_dev.release();
-    h->r64.release(); h->r32.release(); h->msplit.release(); h->out_tmp.release();
+    h->r64.release(); h->ex.release(); h->out_tmp.release();
     h->exp_table.release();
     h->stage.release(); h->chk_box.release(); h->chk_first.release(); h->chk_flag.release();
     h->status.release(); h->pair_counter.release(); h->step_dev.release();
@@ -1728,8 +1900,9 @@ int mtpt_get_row_sums(mtpt_handle* h, double* out) {
             if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, double>(h, h->r64.p, 1)));
             else MTPT_TRY((launch_row_sums_out<SingleView, double>(h, h->r64.p, 1)));
         } else {
-            if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, float>(h, h->r32.p, 1)));
-            else MTPT_TRY((launch_row_sums_out<SingleView, float>(h, h->r32.p, 1)));
+            const float* r = reinterpret_cast<const float*>(h->ex.p) + 2;   // ex[s].z
+            if (h->batch) MTPT_TRY((launch_row_sums_out<BatchView, float>(h, r, 4)));
+            else MTPT_TRY((launch_row_sums_out<SingleView, float>(h, r, 4)));
         }
     }
     return copy_out_host(h, 1, out);
@@ -1832,16 +2005,28 @@ int mtpt_timing_reset(mtpt_handle* h) {
 int mtpt_set_tuning(mtpt_handle* h, const mtpt_tuning* t) {
     if (!h || !t) return MTPT_ERR_INVALID_ARG;
     if (h->ntiles > 0) return MTPT_ERR_STATE;   // a tile's grid is the whole box's
-    if (!(t->cell_scale >= 1.0 && t->cell_scale <= 8.0)) return MTPT_ERR_INVALID_ARG;
+    if (!(t->cell_scale == 0.5 || (t->cell_scale >= 1.0 && t->cell_scale <= 8.0)))
+        return MTPT_ERR_INVALID_ARG;
     if (t->pair_block != 128 && t->pair_block != 256) return MTPT_ERR_INVALID_ARG;
     const bool regrid = t->cell_scale != h->cell_scale;
+    HostSnapshot snap;
+    const bool saved = regrid && h->have_particles && snap.take(h);
+    if (regrid && h->have_particles && !saved) return MTPT_ERR_NO_MEMORY;
     h->cell_scale = t->cell_scale;
     h->pair_block = t->pair_block;
     drop_graph(h);
     if (regrid && h->have_particles) {
-        MTPT_TRY(setup_grids(h));
-        if (h->any_transfer) MTPT_TRY(ensure_cells(h));
-        MTPT_TRY(upload_tables(h));
+        int rc = setup_grids(h);
+        if (rc == MTPT_OK && h->any_transfer) rc = ensure_cells(h);
+        if (rc == MTPT_OK) rc = upload_tables(h);
+        if (rc != MTPT_OK) {
+            // back to the old grid (its arrays are all still there)
+            if (restore_snapshot(h, snap) != MTPT_OK) {
+                h->have_particles = false;
+                h->n = 0;
+            }
+            return rc;
+        }
         h->have_row_sums = false;
     }
     return MTPT_OK;
@@ -1858,17 +2043,28 @@ int mtpt_get_tuning(mtpt_handle* h, mtpt_tuning* out) {
 int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
     if (!h || trial_steps < 1) return MTPT_ERR_INVALID_ARG;
     if (!h->have_particles || h->ntiles > 0) return MTPT_ERR_STATE;
-    const bool timing0 = h->timing;
-    h->timing = false;
     // snapshot of the current state (the trials step it)
     const int64_t n = h->n;
     const int d = h->dim;
     DevBuf<double> spos, smass;
     DevBuf<uint32_t> sid, srid;
-    MTPT_TRY(spos.ensure(size_t(d) * size_t(std::max<int64_t>(n, 1))));
-    MTPT_TRY(smass.ensure(size_t(std::max<int64_t>(n, 1))));
-    MTPT_TRY(sid.ensure(size_t(std::max<int64_t>(n, 1))));
-    if (h->batch) MTPT_TRY(srid.ensure(size_t(std::max<int64_t>(n, 1))));
+    auto free_snapshot = [&]() {
+        spos.release();
+        smass.release();
+        sid.release();
+        srid.release();
+    };
+    {
+        GrowAll g;
+        g.want(spos, size_t(d) * size_t(std::max<int64_t>(n, 1)));
+        g.want(smass, size_t(std::max<int64_t>(n, 1)));
+        g.want(sid, size_t(std::max<int64_t>(n, 1)));
+        if (h->batch) g.want(srid, size_t(std::max<int64_t>(n, 1)));
+        MTPT_TRY(g.commit());
+    }
+    const bool timing0 = h->timing;
+    h->timing = false;
+    const mtpt_tuning start_tuning{h->cell_scale, h->pair_block, 0};
     const int c0 = h->cur;
     const bool fresh0 = h->fresh;         // every trial starts from the same state
     auto copy_state = [&](bool save) -> int {
@@ -1895,18 +2091,27 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
     };
     const uint64_t step0 = h->step;
     unsigned long long pairs0 = 0;
-    MTPT_CUDA_TRY(cudaMemcpyAsync(&pairs0, h->pair_counter.p, sizeof(pairs0), cudaMemcpyDeviceToHost, h->stream));
-    MTPT_TRY(copy_state(true));
-    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    const double scales[] = {1.0, 1.25, 1.5, 2.0};
+    int rc = MTPT_OK;
+    if (cudaMemcpyAsync(&pairs0, h->pair_counter.p, sizeof(pairs0), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+        rc = MTPT_ERR_CUDA;
+    if (rc == MTPT_OK) rc = copy_state(true);
+    if (rc == MTPT_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = MTPT_ERR_CUDA;
+    if (rc != MTPT_OK) {
+        (void)cudaGetLastError();
+        h->timing = timing0;
+        free_snapshot();
+        return rc;
+    }
+    const double scales[] = {0.5, 1.0, 1.25, 1.5, 2.0};
     const int blocks[] = {128, 256};
     mtpt_tuning best{1.0, 256, 0};
     float best_ms = INFINITY;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    MTPT_CUDA_TRY(cudaEventCreate(&e0));
-    MTPT_CUDA_TRY(cudaEventCreate(&e1));
-    int rc = MTPT_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = MTPT_ERR_CUDA;
     for (double sc : scales) {
+        if (rc != MTPT_OK) break;
         for (int bl : blocks) {
             mtpt_tuning t{sc, bl, 0};
             rc = mtpt_set_tuning(h, &t);
@@ -1926,24 +2131,27 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
         }
         if (rc != MTPT_OK) break;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     (void)cudaGetLastError();
-    if (rc == MTPT_OK) rc = mtpt_set_tuning(h, &best);
-    if (rc == MTPT_OK) rc = copy_state(false);
-    if (rc == MTPT_OK) rc = set_step_dev(h, step0);
-    if (rc == MTPT_OK) {
+    // the pick (or, after a failed trial, the starting tuning) with the state
+    // of before the call; the starting grid's arrays exist, so this allocates
+    // nothing when the trials failed
+    const mtpt_tuning keep = rc == MTPT_OK ? best : start_tuning;
+    int rc2 = mtpt_set_tuning(h, &keep);
+    if (rc2 != MTPT_OK && rc != MTPT_OK) rc2 = mtpt_set_tuning(h, &start_tuning);
+    if (rc2 == MTPT_OK) rc2 = copy_state(false);
+    if (rc2 == MTPT_OK) rc2 = set_step_dev(h, step0);
+    if (rc2 == MTPT_OK) {
         if (cudaMemcpyAsync(h->pair_counter.p, &pairs0, sizeof(pairs0), cudaMemcpyHostToDevice,
                             h->stream) != cudaSuccess ||
             cudaStreamSynchronize(h->stream) != cudaSuccess)
-            rc = MTPT_ERR_CUDA;
+            rc2 = MTPT_ERR_CUDA;
     }
     h->have_row_sums = false;
     h->timing = timing0;
-    spos.release();
-    smass.release();
-    sid.release();
-    srid.release();
+    free_snapshot();
+    if (rc == MTPT_OK) rc = rc2;
     if (rc == MTPT_OK && chosen) *chosen = best;
     return rc;
 }
@@ -2289,6 +2497,13 @@ int mtpt_get_ids(mtpt_handle* h, uint32_t* out) {
     return read_status(h);
 }
 
+int mtpt_debug_fail_alloc(int64_t nth, int64_t* remaining) {
+    if (nth < 0) return MTPT_ERR_INVALID_ARG;
+    const int64_t before = g_fail_alloc.exchange(nth);
+    if (remaining) *remaining = before;
+    return MTPT_OK;
+}
+
 const char* mtpt_status_string(int status) {
     switch (status) {
         case MTPT_OK: return "ok";
@@ -2330,9 +2545,9 @@ struct NoallocHead {
 constexpr size_t kNoallocHeadBytes = (sizeof(NoallocHead) + 255) & ~size_t(255);
 
 // Worst case of the per-call pieces carved after the head, at n =
-// MTPT_NOALLOC_MAX_PARTICLES: 3-d binary32 form, 104 bytes per particle
+// MTPT_NOALLOC_MAX_PARTICLES: 3-d binary32 form, 108 bytes per particle
 // (mass copy 8, sorted positions 24 and mass 8, two id arrays 8, key 4,
-// permutation 4, sort key 16, cell 4, rec 16, mass split 8, row sum 4); the
+// permutation 4, sort key 16, cell 4, rec 16, mass split and row sum 16); the
 // cell grid capped at 4 n + 64 cells (setup_grid), so count and start hold at
 // most that many plus one cells padded to a scan tile, and the corner tables
 // at most the sum of the per-axis cell counts (<= their product + 2); each
@@ -2340,7 +2555,7 @@ constexpr size_t kNoallocHeadBytes = (sizeof(NoallocHead) + 255) & ~size_t(255);
 constexpr size_t kNoallocMaxCells = 4 * size_t(MTPT_NOALLOC_MAX_PARTICLES) + 64;
 constexpr size_t kNoallocMaxCellsPad = (kNoallocMaxCells + 1 + kScanTile - 1) / kScanTile * kScanTile;
 constexpr size_t kNoallocWorstBytes =
-    kNoallocHeadBytes + 104 * size_t(MTPT_NOALLOC_MAX_PARTICLES) +
+    kNoallocHeadBytes + 108 * size_t(MTPT_NOALLOC_MAX_PARTICLES) +
     2 * sizeof(uint32_t) * kNoallocMaxCellsPad + sizeof(uint32_t) * (kNoallocMaxCellsPad / kScanTile) +
     sizeof(float2) * (kNoallocMaxCells + 2) + 16 * 256;
 static_assert(kNoallocWorstBytes <= size_t(MTPT_NOALLOC_SCRATCH_BYTES),
@@ -2451,13 +2666,12 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     if (h.precision == MTPT_FP64) {
         h.r64.p = cv.take<double>(size_t(n));
     } else {
-        h.msplit.p = cv.take<float2>(size_t(n));
-        h.r32.p = cv.take<float>(size_t(n));
+        h.ex.p = cv.take<float4>(size_t(n));
     }
     h.corners.p = cv.take<float2>(size_t(std::max(h.n_corners, 1)));
     h.count.p = cv.take<uint32_t>(cells_pad);
     h.start.p = cv.take<uint32_t>(cells_pad);
-    h.tile_sums.p = cv.take<uint32_t>(cells_pad / kScanTile);
+    h.tile_sums.p = cv.take<uint32_t>(cells_pad / kScanTile + 1);   // + the scan's ticket
     if (cv.overflow) return MTPT_ERR_TOO_LARGE;
 
     // The handle's buffer pairs: index 0 is the caller's state (positions are
@@ -2475,8 +2689,10 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     cudaStream_t st = h.stream;
     // what must start at zero (cell counts, status word, pair counter) and the
     // call's parameters, step and corner offsets, all from device-side work
-    if (h.any_transfer)
+    if (h.any_transfer) {
         MTPT_CUDA_TRY(cudaMemsetAsync(h.count.p, 0, cells_pad * sizeof(uint32_t), st));
+        MTPT_CUDA_TRY(cudaMemsetAsync(scan_ticket(&h), 0, sizeof(unsigned int), st));
+    }
     k_noalloc_init<<<1, 32, 0, st>>>(h.params[0], h.n_corners, (unsigned long long)step, head);
     MTPT_CUDA_TRY(cudaGetLastError());
     MTPT_CUDA_TRY(cudaMemcpyAsync(mass_in, mass_dev, size_t(n) * sizeof(double),

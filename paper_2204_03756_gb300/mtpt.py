@@ -43,7 +43,7 @@ EXPORTED = [
     "mtpt_adjoint_backward", "mtpt_status_string", "mtpt_check_word",
     "mtpt_set_particles_async", "mtpt_get_masses_async", "mtpt_tiling_factors",
     "mtpt_set_tiling", "mtpt_set_particles_tile", "mtpt_tile_pack", "mtpt_tile_transfer",
-    "mtpt_get_ids",
+    "mtpt_get_ids", "mtpt_debug_fail_alloc",
 ]
 
 
@@ -173,6 +173,7 @@ def load():
     lib.mtpt_tile_pack.argtypes = [vp, ctypes.c_int64, vp, P(ctypes.c_int64)]
     lib.mtpt_tile_transfer.argtypes = [vp, ctypes.c_int64, vp]
     lib.mtpt_get_ids.argtypes = [vp, vp]
+    lib.mtpt_debug_fail_alloc.argtypes = [ctypes.c_int64, P(ctypes.c_int64)]
     lib.mtpt_status_string.argtypes = [ctypes.c_int]
     lib.mtpt_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -518,6 +519,14 @@ def mtpt_get_ids(h, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.uint32)
     _check(load().mtpt_get_ids(h, out.ctypes.data), "mtpt_get_ids")
     return out
+
+
+def mtpt_debug_fail_alloc(nth: int) -> int:
+    """Make the nth device allocation from now fail (0: off); returns how many
+    the previous setting still had to go."""
+    left = ctypes.c_int64()
+    _check(load().mtpt_debug_fail_alloc(nth, ctypes.byref(left)), "mtpt_debug_fail_alloc")
+    return int(left.value)
 
 
 def mtpt_status_string(code: int) -> str:

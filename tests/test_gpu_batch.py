@@ -108,7 +108,7 @@ def test_tuned_grids_keep_parity_and_autotune_restores_state(form):
     pos, mass = workloads.initial_state(w)
     p = params_of(w, precision=form)
     xr, mr, npairs = O.run(oracle_params(p), pos, mass, 5)
-    for scale, block in ((2.0, 128), (1.25, 256)):
+    for scale, block in ((2.0, 128), (1.25, 256), (0.5, 256)):
         with mtpt.Simulation(p, pos, mass) as s:
             s.set_tuning(scale, block)
             s.step(5)
@@ -119,7 +119,7 @@ def test_tuned_grids_keep_parity_and_autotune_restores_state(form):
         s.step(2)
         m2, x2, i2 = s.masses(), s.positions(), s.info()
         t = s.autotune(trial_steps=4)
-        assert t["cell_scale"] in (1.0, 1.25, 1.5, 2.0) and t["pair_block"] in (128, 256)
+        assert t["cell_scale"] in (0.5, 1.0, 1.25, 1.5, 2.0) and t["pair_block"] in (128, 256)
         assert np.array_equal(s.masses(), m2) and np.array_equal(s.positions(), x2)
         i3 = s.info()
         assert i3["step"] == i2["step"] and i3["pair_count"] == i2["pair_count"]

@@ -93,6 +93,46 @@ def test_pair_sets_bit_exact_vs_brute_force(form, dim, n, L):
     assert np.array_equal(gi, bi) and np.array_equal(gj, bj)
 
 
+def _pairs_gpu_tuned(p, pos, cell_scale):
+    with mtpt.Simulation(p, pos, np.zeros(pos.shape[1])) as sim:
+        sim.set_tuning(cell_scale, 256)
+        return sim.pairs()
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("dim,n,L", [(1, 1999, 400.0), (2, 2000, 30.0), (3, 1777, 9.0)])
+def test_pair_sets_with_half_width_cells_bit_exact_vs_brute_force(form, dim, n, L):
+    """Cells half the cutoff wide (neighbours up to two cells away per axis)
+    find the same pairs as brute force, lattice points, walls and coincident
+    particles included."""
+    rng = np.random.default_rng(200 + dim)
+    pos = rng.uniform(0, L, size=(dim, n))
+    pos[:, :40] = np.round(pos[:, :40])
+    pos[0, 40:60] = 0.0
+    pos[:, 60:70] = pos[:, 70:80]
+    p = mtpt.Params(dim=dim, D=1.0, kappa=0.5, dt=0.1, lo=(0.0,) * dim, hi=(L,) * dim,
+                    seed=1, precision=form)
+    gi, gj = _pairs_gpu_tuned(p, pos, 0.5)
+    bi, bj = O.pairs(pos, O.derived(oracle_params(p))["psi2"], "brute")
+    assert np.array_equal(gi, bi) and np.array_equal(gj, bj)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("name,n,steps", [("heaviside_2d", 20_003, 6), ("heaviside_3d", 30_001, 4)])
+def test_half_width_cells_step_parity(form, name, n, steps):
+    w = workloads.get(name, n)
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w, precision=form)
+    with mtpt.Simulation(p, pos, mass) as sim:
+        sim.set_tuning(0.5, 128)
+        sim.step(steps)
+        x, m, info = sim.positions(), sim.masses(), sim.info()
+    xr, mr, npairs = O.run(oracle_params(p), pos, mass, steps)
+    assert np.array_equal(x, xr)
+    assert info["pair_count"] == npairs
+    assert rel_err(m, mr) <= TOL[form]
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_pair_sets_on_exact_ties(form):
     # D_MT dt = 0.25 makes psi = lambda exactly; lambda = 1.25, psi^2 = 1.5625 and
@@ -103,11 +143,11 @@ def test_pair_sets_on_exact_ties(form):
     assert d["psi2"] == 1.5625
     base = np.array([[2.0, 2.75, 10.0, 10.75, 10.0 + 1.25, 15.0, 15.0],
                      [2.0, 3.0, 10.0, 11.0, 10.0, 15.0, np.nextafter(16.25, 20.0)]])
-    gi, gj = _pairs_gpu(p, base)
     bi, bj = O.pairs(base, d["psi2"], "brute")
-    assert np.array_equal(gi, bi) and np.array_equal(gj, bj)
-    got = set(zip(gi.tolist(), gj.tolist()))
-    assert (0, 1) in got and (2, 3) in got and (2, 4) in got and (5, 6) not in got
+    for gi, gj in (_pairs_gpu(p, base), _pairs_gpu_tuned(p, base, 0.5)):
+        assert np.array_equal(gi, bi) and np.array_equal(gj, bj)
+        got = set(zip(gi.tolist(), gj.tolist()))
+        assert (0, 1) in got and (2, 3) in got and (2, 4) in got and (5, 6) not in got
 
 
 @pytest.mark.parametrize("form", FORMS)
