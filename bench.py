@@ -231,6 +231,8 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
     try:
         mtpt.mtpt_set_stream(h, stream.cuda_stream)
         mtpt.mtpt_set_particles(h, w.dim, pos, mass)
+        # the autotuner's pick (cell width x pair block), restored state after it
+        tuning = mtpt.mtpt_autotune(h, 4)
         mtpt.mtpt_step(h, warmup)
         mtpt.mtpt_sync(h)
         m_before = float(mtpt.mtpt_get_masses(h, w.n).sum())
@@ -272,7 +274,7 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
         "pairs_per_particle_step": pairs / (w.n * steps * world),
         "mass_drift_rel": abs(m_after - m_before) / abs(m_before),
         "clocks": clocks, "kernels": kstats, "launches_per_step":
-            sum(v[0] for v in kstats.values()) / steps,
+            sum(v[0] for v in kstats.values()) / steps, "tuning": tuning,
     }
 
 
@@ -818,6 +820,8 @@ def forms_summary(forms: dict) -> dict:
         err = (r.get("err_vs_oracle") or {}).get("max_rel_err_vs_oracle")
         if err is not None:
             e["err_vs_oracle"] = float(f"{err:.3g}")
+        if r.get("tuning"):
+            e["tuning"] = r["tuning"]
         rf = r.get("roofline")
         if rf:
             e["roofline"] = {"kernel": rf["kernel"], "bound": rf["bound"],

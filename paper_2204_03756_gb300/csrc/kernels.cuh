@@ -1321,13 +1321,12 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
                                      const float cn = __fsub_rn(__fsub_rn(t, rsum), y);
                                      rsum = accept ? t : rsum;
                                      rc = accept ? cn : rc;
-                                     cnt += accept ? 1u : 0u;
                                      const bool keep = accept && j != uint32_t(s);
                                      if (keep && listed < cap) *lp = make_uint2(j, __float_as_uint(K));
                                      if (keep) lp += stride;
                                      listed += keep ? 1u : 0u;
                                  });
-            cnt -= 1;   // the self pair
+            cnt = listed;   // the accepted pairs but the self pair
         } else {
             rsum = 1.0f;
         }
