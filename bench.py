@@ -223,7 +223,7 @@ def job_throughput(n_per_rank: int, steps: int, world: int, max_ms: float) -> fl
     return n_per_rank * steps * world / (max_ms / 1e3)
 
 
-def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
+def time_form(w, pos, mass, form, steps, warmup, rank, world, dist, autotune_steps=4):
     import torch
     p = _params(w, form, rank)
     stream = torch.cuda.Stream()
@@ -231,8 +231,10 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist):
     try:
         mtpt.mtpt_set_stream(h, stream.cuda_stream)
         mtpt.mtpt_set_particles(h, w.dim, pos, mass)
-        # the autotuner's pick (cell width x pair block), restored state after it
-        tuning = mtpt.mtpt_autotune(h, 4)
+        # the autotuner's pick (cell width x pair block), restored state after
+        # it; without trial steps the default tuning
+        tuning = (mtpt.mtpt_autotune(h, autotune_steps) if autotune_steps > 0
+                  else mtpt.mtpt_get_tuning(h))
         mtpt.mtpt_step(h, warmup)
         mtpt.mtpt_sync(h)
         m_before = float(mtpt.mtpt_get_masses(h, w.n).sum())
@@ -402,7 +404,8 @@ def time_batched(steps, warmup, rank, world, dist, nreal=512, autotune_steps=4):
     try:
         mtpt.mtpt_set_stream(h, stream.cuda_stream)
         mtpt.mtpt_set_particles_batch(h, 2, e.counts, pos, mass)
-        tuning = mtpt.mtpt_autotune(h, autotune_steps)
+        tuning = (mtpt.mtpt_autotune(h, autotune_steps) if autotune_steps > 0
+                  else mtpt.mtpt_get_tuning(h))
         mtpt.mtpt_step(h, warmup)
         mtpt.mtpt_sync(h)
         pairs0 = mtpt.mtpt_get_info(h)["pair_count"]
@@ -842,6 +845,8 @@ def main():
     ap.add_argument("--forms", default="fp32w,fp64,fp32w_3d,fp32w_adv,batched,adjoint",
                     help="comma list; the first is the headline value")
     ap.add_argument("--e2e-steps", type=int, default=30)
+    ap.add_argument("--autotune-steps", type=int, default=4,
+                    help="trial steps per tuning of the autotuner (0: default tuning, no trials)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=200_000)
     ap.add_argument("--n", type=int, default=None,
@@ -920,10 +925,12 @@ def main():
     results = {}
     for f in forms:
         wf, pf, mf = state_of(f)
-        results[f] = time_form(wf, pf, mf, f, args.steps, args.warmup, rank, world, dist)
+        results[f] = time_form(wf, pf, mf, f, args.steps, args.warmup, rank, world, dist,
+                               args.autotune_steps)
     batched = None
     if "batched" in args.forms.split(","):
-        batched = time_batched(args.steps, args.warmup, rank, world, dist)
+        batched = time_batched(args.steps, args.warmup, rank, world, dist,
+                               autotune_steps=args.autotune_steps)
     adjoint = time_adjoint(rank) if "adjoint" in args.forms.split(",") else None
     peaks = _peaks()
     if not forms:                        # only batched / adjoint requested

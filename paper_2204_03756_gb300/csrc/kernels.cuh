@@ -14,7 +14,8 @@
 //   cell[s]              linear cell index of particle s
 //   rec[s]               float4: binary32 offsets of the particle from its
 //                        cell's lower corner (x, y, z), and in .w the cell's
-//                        x index (a small integer, exact in binary32)
+//                        x index (a small integer, exact in binary32); in
+//                        2-d, .z (no offset there) holds the cell's y index
 //   start[c]             first particle of cell c (exclusive prefix sum)
 // Cells are row-major (x fastest), so the three cells (cx-1..cx+1) of one
 // neighbour row are one contiguous particle range; inside a cell particles
@@ -540,6 +541,46 @@ k_scatter(int n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ 
                                                                       (uint64_t(c) << 32))));
 }
 
+// Cell coordinates of a realisation-local cell index (the last axis needs
+// no modulo).
+template <int DIM>
+__device__ __forceinline__ void cell_coords_of(uint32_t local, const Grid& g, int* c) {
+    c[0] = c[1] = c[2] = 0;
+    if constexpr (DIM == 1) {
+        c[0] = int(local);
+    } else if constexpr (DIM == 2) {
+        const uint32_t q = local / uint32_t(g.n[0]);
+        c[0] = int(local - q * uint32_t(g.n[0]));
+        c[1] = int(q);
+    } else {
+        const uint32_t q = local / uint32_t(g.n[0]);
+        c[0] = int(local - q * uint32_t(g.n[0]));
+        const uint32_t r = q / uint32_t(g.n[1]);
+        c[1] = int(q - r * uint32_t(g.n[1]));
+        c[2] = int(r);
+    }
+}
+
+// The same from a particle's record: its x (and, in 2-d, y) cell index is
+// there, so only 3-d reads the cell array (`cell` is cell[s], unused below 3-d).
+template <int DIM>
+__device__ __forceinline__ void cell_coords_rec(uint32_t cell, const float4& me, const RealParams& P,
+                                                int* c) {
+    if constexpr (DIM == 3) {
+        cell_coords_of<3>(cell - P.cell_base, P.g, c);
+    } else {
+        c[0] = int(me.w);
+        c[1] = DIM == 2 ? int(me.z) : 0;
+        c[2] = 0;
+    }
+}
+
+// cell[s] where the pair searches need it (3-d), else nothing is read.
+template <int DIM>
+__device__ __forceinline__ uint32_t cell_arg(const uint32_t* __restrict__ cell, uint32_t s) {
+    return DIM == 3 ? cell[s] : 0u;
+}
+
 // Step 2c: gather into cell order.  The slot order the atomics gave inside a
 // cell is replaced by the rank of (x, id) -- binary64 x in its integer order,
 // the id breaking ties -- so the layout (and every sum over it) is identical
@@ -592,11 +633,11 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
     const RealParams& P = v.of_input(src);
     mass_out[dst] = m;
     float off[3] = {0.0f, 0.0f, 0.0f};
-    uint32_t rest = c - P.cell_base;
+    int cc[3];
+    cell_coords_of<DIM>(c - P.cell_base, P.g, cc);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        const uint32_t ca = rest % uint32_t(P.g.n[a]);
-        rest /= uint32_t(P.g.n[a]);
+        const uint32_t ca = uint32_t(cc[a]);
         const double x = xa[a];
         pos_out[a * stride + dst] = x;
         if constexpr (TANGENT) tan_out[a * stride + dst] = tan_in[a * stride + src];
@@ -607,7 +648,7 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
             off[a] = __fadd_rn(__fsub_rn(xh, cr.x), __fsub_rn(xlo, cr.y));
         }
     }
-    rec_out[dst] = make_float4(off[0], off[1], off[2], float((c - P.cell_base) % uint32_t(P.g.n[0])));
+    rec_out[dst] = make_float4(off[0], off[1], DIM == 2 ? float(cc[1]) : off[2], float(cc[0]));
 }
 
 // Sort of a freshly loaded single run, whose particles arrive in input order
@@ -699,11 +740,11 @@ k_gather_rec(int n, int64_t stride, const double2* __restrict__ recs,
     const double m = lane[DIM + 1];
     mass_out[dst] = m;
     float off[3] = {0.0f, 0.0f, 0.0f};
-    uint32_t rest = c - P.cell_base;
+    int cc[3];
+    cell_coords_of<DIM>(c - P.cell_base, P.g, cc);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        const uint32_t ca = rest % uint32_t(P.g.n[a]);
-        rest /= uint32_t(P.g.n[a]);
+        const uint32_t ca = uint32_t(cc[a]);
         const double x = lane[a == 0 ? 0 : 1 + a];
         pos_out[a * stride + dst] = x;
         if constexpr (TANGENT) tan_out[a * stride + dst] = lane[R::kTan + a];
@@ -714,7 +755,7 @@ k_gather_rec(int n, int64_t stride, const double2* __restrict__ recs,
             off[a] = __fadd_rn(__fsub_rn(xh, cr.x), __fsub_rn(xlo, cr.y));
         }
     }
-    rec_out[dst] = make_float4(off[0], off[1], off[2], float((c - P.cell_base) % uint32_t(P.g.n[0])));
+    rec_out[dst] = make_float4(off[0], off[1], DIM == 2 ? float(cc[1]) : off[2], float(cc[0]));
 }
 
 // ---------------------------------------------------------------------------
@@ -822,15 +863,8 @@ __device__ __forceinline__ void for_each_row(uint32_t cell, const float4& me,
                                              const RealParams& P, Row&& row) {
     const Grid& g = P.g;
     const PairParams& pp = P.pp;
-    int c[3] = {0, 0, 0};
-    {
-        uint32_t rest = cell - P.cell_base;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            c[a] = int(rest % uint32_t(g.n[a]));
-            rest /= uint32_t(g.n[a]);
-        }
-    }
+    int c[3];
+    cell_coords_rec<DIM>(cell, me, P, c);
     const int R = g.reach;
     const int xlo = max(c[0] - R, 0);
     const int xhi = min(c[0] + R, g.n[0] - 1);
@@ -1106,14 +1140,7 @@ __device__ __forceinline__ uint32_t seg_pairs(bool valid, uint32_t s, int64_t st
     const PairParams& pp = P.pp;
     const float4 me = valid ? rec[s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     int c[3] = {0, 0, 0};
-    if (valid) {
-        uint32_t rest = cell[s] - P.cell_base;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            c[a] = int(rest % uint32_t(g.n[a]));
-            rest /= uint32_t(g.n[a]);
-        }
-    }
+    if (valid) cell_coords_rec<DIM>(cell_arg<DIM>(cell, s), me, P, c);
     const int R = g.reach;
     const int xlo = max(c[0] - R, 0);
     const int xhi = min(c[0] + R, g.n[0] - 1);
@@ -1312,7 +1339,7 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
             const float na = -P.pp.a_log2e;
             const uint32_t cap = uint32_t(nb.cap);
             uint2* lp = nb.e + s;          // slot `listed` of s
-            scan_neighbours<DIM, true>(uint32_t(s), cell[s], stride, rec, pos, start, P,
+            scan_neighbours<DIM, true>(uint32_t(s), cell_arg<DIM>(cell, s), stride, rec, pos, start, P,
                                  [&](uint32_t j, float d2f, bool accept) {
                                      // Kahan step, kept only for accepted pairs
                                      const float K = ex2_approx(na * d2f);
@@ -1379,7 +1406,7 @@ __device__ __noinline__ float2 search_flux(uint32_t s, int64_t stride,
     const RealParams& P = v.of_sorted(s);
     const float na = -P.pp.a_log2e;
     FluxSum g{rs, two_beta, ms};
-    scan_neighbours<DIM, true>(s, cell[s], stride, rec, pos, start, P,
+    scan_neighbours<DIM, true>(s, cell_arg<DIM>(cell, s), stride, rec, pos, start, P,
                          [&](uint32_t j, float d2f, bool accept) {
                              g.add(__ldg(ex + j), ex2_approx(na * d2f), accept);
                          });
@@ -1441,7 +1468,7 @@ k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float4
     const RealParams& P = v.of_sorted(uint32_t(s));
     if (!P.transfer) return;
     const uint32_t ids = id[s];
-    visit_neighbours<DIM>(uint32_t(s), cell[s], stride, rec, pos, start, P,
+    visit_neighbours<DIM>(uint32_t(s), cell_arg<DIM>(cell, s), stride, rec, pos, start, P,
                           [&](uint32_t j, float, const float4&) {
                               if (j == uint32_t(s)) return;
                               const unsigned long long k = atomicAdd(counter, 1ull);
