@@ -73,48 +73,48 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
     return float(table.get(kernel, 0))
 
 
-# DRAM bytes per particle of each kernel from one ncu capture
-# (profiles/step_kernels_gaussian_2d_8M_full.md, gaussian_2d scaled to 8e6
-# particles; traffic grows in proportion to the particles a launch processes,
-# so it is scaled to the bench's launch).  Valid only for the library source
-# it was measured on: a different hash of the CUDA sources and the header
-# reports traffic as null.
+# DRAM bytes per particle of each kernel from one-kernel ncu captures of the
+# bench's own launch (profiles/step_kernels_gaussian_2d_4M.md: gaussian_2d,
+# 4e6 particles, precision form, one launch per capture after three steps).
+# Valid only for the library source it was measured on: a different hash of
+# the CUDA sources and the header reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "4b81ead255ff"
+TRAFFIC_SOURCE_SHA1 = "129489bf0c1a"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (177.801216e6 + 118.483200e6) / 8e6,
-    "scatter": (164.016640e6 + 123.912448e6) / 8e6,
-    "gather": (306.041088e6 + 395.330816e6) / 8e6,
-    "rowsum_f32": (177.898752e6 + 25.227264e6) / 8e6,
-    "exchange_f32": (338.003712e6 + 54.502912e6) / 8e6,
+    "walk_key": (88932864 + 28013312) / 4e6,
+    "scatter": (81783552 + 34266880) / 4e6,
+    "gather": (152975616 + 138866432) / 4e6,
+    "rowsum_f32": (237771264 + 292134144) / 4e6,
+    "exchange_f32": (389567232 + 28455936) / 4e6,
 }
 
 
-# Warp instructions per particle of the binary32-form kernels in the same
-# capture (smsp__inst_executed.sum / 8e6): with the live launch time they
-# give the issue rate, against the issue peak of 4 warp instructions per
-# clock per SM (one per scheduler).
+# Warp instructions per particle of the same captures
+# (smsp__inst_executed.sum / 4e6): with the live launch time they give the
+# issue rate, against the issue peak of 4 warp instructions per clock per SM
+# (one per scheduler).
 INSTR_PER_PARTICLE = {
-    "walk_key": 82277063 / 8e6,
-    "scatter": 8250000 / 8e6,
-    "gather": 84628991 / 8e6,
-    "rowsum_f32": 301831677 / 8e6,
-    "exchange_f32": 390664107 / 8e6,
+    "walk_key": 43893462 / 4e6,
+    "scatter": 4125000 / 4e6,
+    "gather": 37149198 / 4e6,
+    "rowsum_f32": 183180239 / 4e6,
+    "exchange_f32": 44836827 / 4e6,
 }
 SMS, SCHEDULERS_PER_SM = 152, 4
 
 
-# What bounds each kernel in that same capture (ncu counters; see
-# profiles/step_kernels_gaussian_2d_8M_full.md), reported beside the roofline
+# What bounds each kernel in those captures (ncu counters; see
+# profiles/step_kernels_gaussian_2d_4M.md), reported beside the roofline
 # while the kernel source hash matches.
 BINDING = {
-    "exchange_f32": "instruction issue: 83 % of issue slots at 19 of 32 active lanes; DRAM 13 %",
-    "rowsum_f32": "instruction issue: 88 % of issue slots at 20 of 32 active lanes; DRAM 9 %",
+    "exchange_f32": ("DRAM 55 % with long-scoreboard stalls on the list reads and the "
+                     "neighbour-record gathers; issue 40 % at 20 of 32 active lanes"),
+    "rowsum_f32": "instruction issue: 72 % of issue slots at 18 of 32 active lanes; DRAM 32 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
-    "gather": "DRAM 71 % (payload reads through the permutation, cell-ordered writes)",
-    "scatter": "DRAM 54 % (slot writes of the permutation and sort keys)",
-    "walk_key": "binary64 pipe 82 % busy (x + sigma xi)",
+    "gather": "DRAM 64 % (payload reads through the permutation, cell-ordered writes)",
+    "scatter": "DRAM 43 % at 11 % issue (slot atomics, permutation and sort-key stores)",
+    "walk_key": "binary64 pipe 80 % busy (x + sigma xi)",
 }
 
 

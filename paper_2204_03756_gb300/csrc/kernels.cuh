@@ -1086,8 +1086,7 @@ using NbList64 = NbList<double>;
 // lanes all fit their lists walks them instead of searching.
 struct NbList32 {
     uint2* e;
-    uint32_t* count;
-    int cap;           // 0: no list
+    int cap;           // 0: no list; a particle's count is in its record ex[s].w
 };
 
 // Phases A-C for the calling warp (every lane of the warp must call it; lanes
@@ -1319,7 +1318,8 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
 // hardware ex2, compensated binary32 row sum, rounded to binary32; written
 // with the binary32 head/tail split of the mass as the particle's record
-// ex[s] = {m_hi, m_lo, r, 0} that pass 2 reads once per neighbour;
+// ex[s] = {m_hi, m_lo, r, list length (bits)} that pass 2 reads once per
+// neighbour (.w only for the particle itself);
 // with nb.cap > 0 also the neighbour lists of pass 2 (accepted j != s with
 // their K, in visiting order: the band's exact accepts come last).
 template <int DIM, class View, int BLOCK>
@@ -1357,10 +1357,9 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
         } else {
             rsum = 1.0f;
         }
-        if (nb.cap > 0) nb.count[s] = listed;
         float mhi, mlo;
         split_double(mass[s], &mhi, &mlo);
-        ex[s] = make_float4(mhi, mlo, __fsub_rn(rsum, rc), 0.0f);
+        ex[s] = make_float4(mhi, mlo, __fsub_rn(rsum, rc), __uint_as_float(listed));
         // with ghost_id (a tile), pairs are counted for the tile's own particles only
         if (ghost_id && (ghost_id[s] & kGhostBit)) cnt = 0;
     }
@@ -1373,7 +1372,7 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
 // The flux sum of pass 2, precision form: W = 2 beta K / (r_s + r_j) in
 // binary32 (symmetric bit for bit), the mass difference from the binary32
 // head/tail split (exactly antisymmetric), compensated accumulation, and the
-// update in binary64.  Each particle's record ex = {m_hi, m_lo, r, 0} is one
+// update in binary64.  Each particle's record ex = {m_hi, m_lo, r, count} is one
 // 16-byte load per neighbour.
 struct FluxSum {
     float rs, two_beta;
@@ -1432,7 +1431,7 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
     }
     const float4 xs = ex[s];
     FluxSum f{xs.z, float(2.0 * P.pp.beta), make_float2(xs.x, xs.y)};   // beta folded into W
-    const uint32_t listed = nb.cap > 0 ? nb.count[s] : 0xffffffffu;
+    const uint32_t listed = nb.cap > 0 ? __float_as_uint(xs.w) : 0xffffffffu;
     if (listed <= uint32_t(nb.cap)) {
         const uint2* e = nb.e + s;
         uint32_t k = 0;

@@ -223,12 +223,11 @@ struct mtpt_handle {
     DevBuf<uint32_t> id_first;
     DevBuf<RealParams> params_dev;
     DevBuf<double> r64;
-    DevBuf<float4> ex;                // precision form: {m_hi, m_lo, r, 0} per particle
+    DevBuf<float4> ex;                // precision form: {m_hi, m_lo, r, list length} per particle
     DevBuf<uint32_t> nb_j, nb_count;      // binary64 form neighbour lists
     DevBuf<double> nb_k;
     int nb_cap = 0;
     DevBuf<uint2> nb32_e;                 // precision form neighbour lists {j, K}
-    DevBuf<uint32_t> nb32_count;
     int nb32_cap = 0;
     DevBuf<uint32_t> adj_nb_j, adj_nb_count;     // adjoint (K, dK) lists
     DevBuf<double2> adj_nb_k;
@@ -705,7 +704,6 @@ int ensure_cells(mtpt_handle* h) {
     }
     if (h->nb32_cap > 0) {
         g.want(h->nb32_e, size_t(h->nb32_cap) * size_t(h->cap));
-        g.want(h->nb32_count, size_t(h->cap));
     }
     if (g.grows()) drop_graph(h);
     MTPT_TRY(g.commit());
@@ -859,7 +857,7 @@ template <int DIM, class View, int BLOCK>
 int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
                      int o, int c) {
     const int blocks = int((n + BLOCK - 1) / BLOCK);
-    const NbList32 nb{h->nb32_e.p, h->nb32_count.p, h->nb32_e.p ? h->nb32_cap : 0};
+    const NbList32 nb{h->nb32_e.p, h->nb32_e.p ? h->nb32_cap : 0};
     {
         MTPT_TIMED(h, "rowsum_f32");
         k_rowsum_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
@@ -1734,7 +1732,7 @@ int mtpt_destroy(mtpt_handle* h) {
     h->lam_in.release(); h->lam_s.release(); h->lam_new.release(); h->gD.release();
     h->partial.release(); h->acc.release();
     h->nb_j.release(); h->nb_k.release(); h->nb_count.release();
-    h->nb32_e.release(); h->nb32_count.release();
+    h->nb32_e.release();
     h->adj_nb_j.release(); h->adj_nb_k.release(); h->adj_nb_count.release();
     h->tile_counts.release(); h->tile_base.release(); h->tile_cursor.release();
     h->tile_native.release(); h->tile_flag.release(); h->tile_keep.release();
