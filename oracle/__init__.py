@@ -36,6 +36,14 @@ itself; the tests named are under ``tests/``):
 * ``run``               -- pinned to the erf solution (pure random walk,
   pure mass transfer and the 50/50 split) and to the spreading of a Gaussian
   point source (variance grows by 2 D t per axis).
+* ``react``             -- (bimolecular reaction A + B -> 0, the reading of
+  the extension named in Sec. 8) pinned to the closed-form solution of the
+  rate law in 50-digit arithmetic (both species, the one in deficit to its
+  relative precision), to the composition of substeps, and to a stiff ODE
+  integrator; ``particle_rate`` to k N / V.
+* ``run_reactive``      -- pinned to plain ``run`` of each species when
+  k = 0 (bit for bit), to the well-mixed solution for uniform species, to
+  the conservation of sum(M_A - M_B) and to positivity.
 """
 from .oracle import *  # noqa: F401,F403
 from . import analytic  # noqa: F401

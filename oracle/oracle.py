@@ -23,7 +23,7 @@ _lib = None
 __all__ = [
     "OracleParams", "build", "load", "derived", "philox4x32_10", "log_f32",
     "sincos_2pi_f32", "box_muller", "normals", "reflect", "random_walk", "pairs",
-    "mass_transfer", "run",
+    "mass_transfer", "run", "react", "particle_rate", "run_reactive",
 ]
 
 
@@ -105,6 +105,13 @@ def load():
                             ctypes.c_uint64, ctypes.c_int64, ctypes.c_int]
     lib.orc_run.restype = ctypes.c_int64
     lib.orc_derived_values.argtypes = [P(_CParams), f64p]
+    lib.orc_react.argtypes = [ctypes.c_int64, f64p, f64p, ctypes.c_double, ctypes.c_double]
+    lib.orc_particle_rate.argtypes = [P(_CParams), ctypes.c_int64, ctypes.c_double]
+    lib.orc_particle_rate.restype = ctypes.c_double
+    lib.orc_run_reactive.argtypes = [P(_CParams), ctypes.c_int64, f64p, f64p, f64p, u32p,
+                                     ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_double]
+    lib.orc_run_reactive.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -252,3 +259,44 @@ def run(p: OracleParams, pos, mass, nsteps: int, step0: int = 0, ids=None,
     if total < 0:
         raise MemoryError("oracle run: allocation failed")
     return pos, mass, int(total)
+
+
+def react(a, b, kp: float, dt: float):
+    """One well-mixed reaction substep A + B -> 0 of length dt on particle
+    masses a, b >= 0 with the particle rate kp (see ``particle_rate``).
+    Returns the new (a, b)."""
+    lib = load()
+    a = np.ascontiguousarray(np.array(a, dtype=np.float64, copy=True))
+    b = np.ascontiguousarray(np.array(b, dtype=np.float64, copy=True))
+    lib.orc_react(a.size, _ptr(a, ctypes.c_double), _ptr(b, ctypes.c_double), kp, dt)
+    return a, b
+
+
+def particle_rate(p: OracleParams, n: int, k: float) -> float:
+    """k_p = k N / V: the rate constant k of the concentration rate law
+    applied to particle masses (C = N M / V)."""
+    cp = p.c()
+    return float(load().orc_particle_rate(ctypes.byref(cp), n, k))
+
+
+def run_reactive(p: OracleParams, pos, ma, mb, nsteps: int, k: float, step0: int = 0,
+                 ids=None, method: str = "kdtree"):
+    """``nsteps`` reactive steps A + B -> 0 (walk; transfer of both species
+    with the same weights; well-mixed reaction per particle with rate
+    constant k).  Returns (pos, ma, mb, total ordered pairs)."""
+    lib = load()
+    pos = np.ascontiguousarray(np.array(pos, dtype=np.float64, copy=True))
+    ma = np.ascontiguousarray(np.array(ma, dtype=np.float64, copy=True))
+    mb = np.ascontiguousarray(np.array(mb, dtype=np.float64, copy=True))
+    n = ma.size
+    if ids is None:
+        ids = np.arange(n, dtype=np.uint32)
+    ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint32))
+    cp = p.c()
+    total = lib.orc_run_reactive(ctypes.byref(cp), n, _ptr(pos, ctypes.c_double),
+                                 _ptr(ma, ctypes.c_double), _ptr(mb, ctypes.c_double),
+                                 _ptr(ids, ctypes.c_uint32), step0, nsteps,
+                                 0 if method == "brute" else 1, k)
+    if total < 0:
+        raise MemoryError("oracle reactive run: allocation failed")
+    return pos, ma, mb, int(total)
