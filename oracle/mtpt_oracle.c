@@ -562,10 +562,13 @@ static double orc_phi(double x) {
     return (x > 0.0) ? -expm1(-x) / x : 1.0;
 }
 
-/* One reaction substep of length dt for masses a, b >= 0 in place. */
+/* One reaction substep of length dt for the masses a, b in place.  A
+ * particle with a negative mass of either species does not react (the rate
+ * law is for non-negative concentrations). */
 void orc_react(int64_t n, double* a, double* b, double kp, double dt) {
     for (int64_t i = 0; i < n; ++i) {
         const double ai = a[i], bi = b[i];
+        if (ai < 0.0 || bi < 0.0) continue;
         if (ai >= bi) {
             const double x = kp * (ai - bi) * dt;
             const double q = 1.0 + kp * bi * dt * orc_phi(x);

@@ -138,3 +138,9 @@ def test_reactive_run_conserves_the_species_difference_and_positivity(dim):
     _, a0, b0, _ = O.run_reactive(p, pos, ma, mb, 15, k=0.0)
     assert a0.sum() == pytest.approx(ma.sum(), rel=1e-12)
     assert b0.sum() == pytest.approx(mb.sum(), rel=1e-12)
+
+
+def test_negative_masses_do_not_react_and_zero_masses_change_nothing():
+    a, b = O.react([-1.0, 0.5, 0.0, -0.0, 2.0], [0.5, -1.0, 0.7, 0.3, 0.0], 3.0, 0.1)
+    assert a.tolist() == [-1.0, 0.5, 0.0, -0.0, 2.0]
+    assert b.tolist() == [0.5, -1.0, 0.7, 0.3, 0.0]
