@@ -41,7 +41,8 @@ DTYPE = {"fp64": "f64", "fp32w": "f32 weights, compensated f32 sums, f64 update"
 # timed single-run forms: precision form on the --workload workload, or on
 # the 3-d workload for the "_3d" forms
 FORM_WORKLOAD = {"fp32w": None, "fp64": None, "fp32w_3d": "heaviside_3d", "fp64_3d": "heaviside_3d",
-                 "fp32w_adv": "advection_2d", "fp64_adv": "advection_2d"}
+                 "fp32w_adv": "advection_2d", "fp64_adv": "advection_2d",
+                 "fp32w_react": "reaction_2d", "fp64_react": "reaction_2d"}
 
 
 def _base(form: str) -> str:
@@ -223,6 +224,15 @@ def job_throughput(n_per_rank: int, steps: int, world: int, max_ms: float) -> fl
     return n_per_rank * steps * world / (max_ms / 1e3)
 
 
+def _conserved(h, w) -> float:
+    """The total the step conserves: the mass, or with A + B -> 0 the
+    difference of the species' masses."""
+    m = mtpt.mtpt_get_masses(h, w.n)
+    if w.react_k > 0.0:
+        return float((m - mtpt.mtpt_get_masses_b(h, w.n)).sum())
+    return float(m.sum())
+
+
 def time_form(w, pos, mass, form, steps, warmup, rank, world, dist, autotune_steps=4):
     import torch
     p = _params(w, form, rank)
@@ -231,13 +241,16 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist, autotune_ste
     try:
         mtpt.mtpt_set_stream(h, stream.cuda_stream)
         mtpt.mtpt_set_particles(h, w.dim, pos, mass)
+        if w.react_k > 0.0:                 # A + B -> 0: species B from the workload
+            mtpt.mtpt_set_reaction(h, w.react_k)
+            mtpt.mtpt_set_masses_b(h, workloads.masses_b(w, pos))
         # the autotuner's pick (cell width x pair block), restored state after
         # it; without trial steps the default tuning
         tuning = (mtpt.mtpt_autotune(h, autotune_steps) if autotune_steps > 0
                   else mtpt.mtpt_get_tuning(h))
         mtpt.mtpt_step(h, warmup)
         mtpt.mtpt_sync(h)
-        m_before = float(mtpt.mtpt_get_masses(h, w.n).sum())
+        m_before = _conserved(h, w)
         pairs0 = mtpt.mtpt_get_info(h)["pair_count"]
         sampler = ClockSampler(torch.cuda.current_device())
         sampler.start()
@@ -258,7 +271,7 @@ def time_form(w, pos, mass, form, steps, warmup, rank, world, dist, autotune_ste
         ms = e0.elapsed_time(e1)
         info = mtpt.mtpt_get_info(h)
         pairs = info["pair_count"] - pairs0
-        m_after = float(mtpt.mtpt_get_masses(h, w.n).sum())
+        m_after = _conserved(h, w)
         # second pass with per-kernel events (same stream, same workload)
         mtpt.mtpt_timing_reset(h)
         mtpt.mtpt_timing_enable(h, True)
@@ -627,6 +640,20 @@ def _step_errors(p, pos, mass, steps, x_ref, m_ref, npairs):
             "pair_count_equal": bool(info["pair_count"] == npairs)}
 
 
+def _reactive_errors(p, k, pos, ma, mb, x_ref, a_ref, b_ref, npairs):
+    """One reactive step against the oracle: both species, error relative to
+    the largest reference mass of either."""
+    with mtpt.Simulation(p, pos, ma) as sim:
+        sim.set_reaction(k, mb)
+        sim.step(1)
+        x, a, b, info = sim.positions(), sim.masses(), sim.masses_b(), sim.info()
+    scale = max(np.abs(a_ref).max(), np.abs(b_ref).max())
+    err = max(np.abs(a - a_ref).max(), np.abs(b - b_ref).max()) / scale
+    return {"max_rel_err_vs_oracle": float(err),
+            "positions_bit_exact": bool(np.array_equal(x, x_ref)),
+            "pair_count_equal": bool(info["pair_count"] == npairs)}
+
+
 def _oracle_params(O, p):
     return O.OracleParams(dim=p.dim, D=p.D, kappa=p.kappa, dt=p.dt, beta=p.beta, lam=p.lam,
                           lo=tuple(p.lo) + (0.0,) * (3 - p.dim),
@@ -657,6 +684,15 @@ def cpu_baseline(w, pos, mass, forms, batched=False, adjoint=False):
         fs = [f for f in forms if FORM_WORKLOAD.get(f) == name]
         wk = workloads.get(name, 200_000)
         pk, mk = workloads.initial_state(wk)
+        if wk.react_k > 0.0:
+            mb = workloads.masses_b(wk, pk)
+            xr, ar, br, nr = O.run_reactive(_oracle_params(O, _params(wk, fs[0], 0)), pk, mk, mb,
+                                            1, wk.react_k)
+            for f in fs:
+                parity[f] = dict(_reactive_errors(_params(wk, f, 0), wk.react_k, pk, mk, mb,
+                                                  xr, ar, br, nr),
+                                 case=f"{name}, n={wk.n}, 1 step, both species")
+            continue
         xr, mr, nr = O.run(_oracle_params(O, _params(wk, fs[0], 0)), pk, mk, 1)
         for f in fs:
             parity[f] = dict(_step_errors(_params(wk, f, 0), pk, mk, 1, xr, mr, nr),
@@ -842,7 +878,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="gaussian_2d", choices=sorted(workloads.WORKLOADS))
-    ap.add_argument("--forms", default="fp32w,fp64,fp32w_3d,fp32w_adv,batched,adjoint",
+    ap.add_argument("--forms", default="fp32w,fp64,fp32w_3d,fp32w_adv,fp32w_react,batched,adjoint",
                     help="comma list; the first is the headline value")
     ap.add_argument("--e2e-steps", type=int, default=30)
     ap.add_argument("--autotune-steps", type=int, default=4,

@@ -517,6 +517,39 @@ int mtpt_tile_pack(mtpt_handle* h, int64_t cap, double* send_dev, int64_t* count
  * treated as a ghost and changed no native).  Syncs once. */
 int mtpt_tile_transfer(mtpt_handle* h, int64_t n_recv, const double* recv_dev);
 
+/* Bimolecular reaction A + B -> 0, the extension Sec. 8 names (the paper
+ * gives no model; this is the library's reading).  Every particle carries a
+ * mass of species A (the masses of the other calls) and of species B; each
+ * step walks the particles, transfers both species with the same weights
+ * W_ij (Sec. 3, Eq. "changemass" for each species), then lets every particle
+ * react well mixed over dt: with concentrations C = N M / V (V the box
+ * volume; the mass-concentration relation of Sec. 3) the rate law
+ * dC_A/dt = dC_B/dt = -k C_A C_B, solved exactly over dt on the particle's
+ * masses (rate k N / V).  A particle with a negative mass of either species
+ * does not react.  The binary64 form reacts in binary64; the precision form
+ * computes the two reaction factors in binary32 and applies them to the
+ * binary64 masses.
+ *
+ * mtpt_set_reaction: turn the reaction on (or change k >= 0, finite;
+ * MTPT_ERR_INVALID_ARG otherwise) for a single-run handle that is not a
+ * tile (MTPT_ERR_STATE for a batch or a tile).  Species B starts at zero on
+ * the loaded particles and on every later load.  Allocates species B's
+ * buffers (MTPT_ERR_NO_MEMORY; the handle is then unchanged).  Reaction runs
+ * refuse the adjoint and tiling (MTPT_ERR_STATE). */
+int mtpt_set_reaction(mtpt_handle* h, double k);
+
+/* Species B's masses from a HOST buffer of n doubles in input order, each
+ * finite and >= 0 (in the precision form at most 1e30; MTPT_ERR_INVALID_ARG
+ * otherwise, nothing changed).  MTPT_ERR_STATE without mtpt_set_reaction or
+ * before the first load.  Syncs.  The particle state of the reaction
+ * extension of Sec. 8 (see mtpt_set_reaction). */
+int mtpt_set_masses_b(mtpt_handle* h, const double* mass_b);
+
+/* Species B's masses in input order to a HOST buffer of n doubles (the
+ * reaction extension of Sec. 8; MTPT_ERR_STATE as mtpt_set_masses_b).
+ * Syncs. */
+int mtpt_get_masses_b(mtpt_handle* h, double* out);
+
 /* Generator ids of the particles in the order mtpt_get_masses and
  * mtpt_get_positions use, to a HOST buffer of n: i for particle i of a plain
  * handle, the global ids of a tile's natives.  Identification: no

@@ -601,7 +601,8 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
          float4* __restrict__ rec_out,
          const float2* __restrict__ corners, uint32_t* __restrict__ rid_out,
          const __grid_constant__ View v, const double* __restrict__ tan_in = nullptr,
-         double* __restrict__ tan_out = nullptr) {
+         double* __restrict__ tan_out = nullptr, const double* __restrict__ mass_b_in = nullptr,
+         double* __restrict__ mass_b_out = nullptr) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t src = perm[s];
@@ -630,6 +631,7 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
     id_out[dst] = my_id;
     cell_out[dst] = c;
     if constexpr (View::kBatch) rid_out[dst] = __ldg(v.rid_input + src);
+    if (mass_b_out) mass_b_out[dst] = mass_b_in[src];   // second species (reactions)
     const RealParams& P = v.of_input(src);
     mass_out[dst] = m;
     float off[3] = {0.0f, 0.0f, 0.0f};
@@ -1476,6 +1478,67 @@ k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float4
                                   out_j[k] = id[j];
                               }
                           });
+}
+
+// ---------------------------------------------------------------------------
+// Bimolecular reaction A + B -> 0 (the extension Sec. 8 names; the model is
+// this library's reading).  After the transfer of both species with the same
+// weights, each particle reacts well mixed over dt: with concentrations
+// C = N M / V the rate law dC_A/dt = dC_B/dt = -k C_A C_B is
+// da/dt = db/dt = -kp a b on its masses, kp = k N / V, solved exactly over
+// dt.  With `big` the larger of a and b, x = kp (big - small) dt,
+// phi(x) = (1 - e^-x) / x (phi(0) = 1) and q = 1 + kp small dt phi(x):
+//   big' = big / q,   small' = small e^-x / q
+// (the closed form a(t) = D a / (a - b e^-kpDt), D = a - b, rearranged so
+// that neither D -> 0 nor the species in deficit loses digits).  A particle
+// with a negative mass of either species (sign bit set) does not react.
+// ---------------------------------------------------------------------------
+
+// The precision form's mass split for pass 2 of species B: ex[s].x/.y take
+// the binary32 head/tail of mass_b[s] (the row sum and the list length stay).
+__global__ void __launch_bounds__(kBlock)
+k_split_mass(int n, const double* __restrict__ mass_b, float4* __restrict__ ex) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float hi, lo;
+    split_double(mass_b[s], &hi, &lo);
+    reinterpret_cast<float2*>(ex)[2 * s] = make_float2(hi, lo);
+}
+
+// F64: binary64 throughout (exp, expm1 and IEEE division).  Otherwise (the
+// precision form) the two factors 1/q and e^-x / q in binary32 from the
+// binary32 heads of the masses (kpdt_f = kp dt rounded to binary32), each
+// applied to its binary64 mass with one binary64 multiply.
+template <bool F64>
+__global__ void __launch_bounds__(kBlock)
+k_react(int n, double* __restrict__ ma, double* __restrict__ mb, double kp, double dt,
+        float kpdt_f) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const double a = ma[s], b = mb[s];
+    const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
+    if ((ka | kb) < 0) return;                       // a negative mass: no reaction
+    const bool a_big = ka >= kb;                     // non-negative values order by their bits
+    const double big = a_big ? a : b, small = a_big ? b : a;
+    double nbig, nsmall;
+    if constexpr (F64) {
+        const double x = __dmul_rn(__dmul_rn(kp, __dsub_rn(big, small)), dt);
+        const double phi = x > 0.0 ? -expm1(-x) / x : 1.0;
+        const double q = __dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(kp, small), dt), phi));
+        nbig = big / q;
+        nsmall = __dmul_rn(small, exp(-x)) / q;
+    } else {
+        float bh, bl, sh, sl;
+        split_double(big, &bh, &bl);
+        split_double(small, &sh, &sl);
+        const float x = __fmul_rn(kpdt_f, __fsub_rn(bh, sh));
+        const float phi = x > 0.0f ? __fdiv_rn(-expm1f(-x), x) : 1.0f;
+        const float rq = __frcp_rn(__fmaf_rn(__fmul_rn(kpdt_f, sh), phi, 1.0f));
+        nbig = __dmul_rn(big, f32_to_f64(rq));
+        nsmall = __dmul_rn(small, f32_to_f64(__fmul_rn(expf(-x), rq)));
+    }
+    ma[s] = a_big ? nbig : nsmall;
+    mb[s] = a_big ? nsmall : nbig;
 }
 
 // ---------------------------------------------------------------------------

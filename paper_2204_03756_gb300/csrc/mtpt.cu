@@ -217,6 +217,11 @@ struct mtpt_handle {
     DevBuf<double2> sortkey;          // (x, id | cell << 32) per slot (k_scatter)
     DevBuf<double2> sortrec;          // payload records per slot (k_scatter_rec)
     bool fresh = false;               // state loaded in input order, not yet sorted
+    // bimolecular reaction A + B -> 0: species B's masses (cell order, double
+    // buffered like `mass`) and the rate constant of the concentration law
+    bool reactive = false;
+    double react_k = 0.0;
+    DevBuf<double> massb[2];
     DevBuf<float4> rec;
     DevBuf<float2> corners;
     DevBuf<int> corner_first;
@@ -635,11 +640,13 @@ int ensure_capacity(mtpt_handle* h, int64_t n, int64_t keep = 0) {
     const double* old_mass = h->mass[c].p;
     const uint32_t* old_id = h->id[c].p;
     const uint32_t* old_rid = h->rid[c].p;
+    const double* old_massb = h->massb[c].p;
     GrowAll g;
     if (cap > h->cap) {
         for (int b = 0; b < 2; ++b) {
             g.want(h->pos[b], size_t(d) * cap);
             g.want(h->mass[b], size_t(cap));
+            if (h->reactive) g.want(h->massb[b], size_t(cap));
             g.want(h->id[b], size_t(cap));
             if (h->batch) g.want(h->rid[b], size_t(cap));
         }
@@ -668,6 +675,9 @@ int ensure_capacity(mtpt_handle* h, int64_t n, int64_t keep = 0) {
                             h->stream) != cudaSuccess ||
             cudaMemcpyAsync(h->id[c].p, old_id, size_t(keep) * 4, cudaMemcpyDeviceToDevice,
                             h->stream) != cudaSuccess ||
+            (h->reactive && old_massb &&
+             cudaMemcpyAsync(h->massb[c].p, old_massb, row, cudaMemcpyDeviceToDevice,
+                             h->stream) != cudaSuccess) ||
             (h->batch && old_rid &&
              cudaMemcpyAsync(h->rid[c].p, old_rid, size_t(keep) * 4, cudaMemcpyDeviceToDevice,
                              h->stream) != cudaSuccess) ||
@@ -807,7 +817,7 @@ int launch_sort_t(mtpt_handle* h, int c, int o, const View& vin) {
     k_gather<DIM, View, TANGENT><<<blocks, kBlock, 0, h->stream>>>(
         n, stride, h->perm.p, h->sortkey.p, h->start.p, h->pos[c].p, h->mass[c].p, h->id[o].p,
         h->pos[o].p, h->mass[o].p, h->cell.p, h->rec.p, h->corners.p, rid_out, vin, tan_in,
-        tan_out);
+        tan_out, h->reactive ? h->massb[c].p : nullptr, h->reactive ? h->massb[o].p : nullptr);
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -844,7 +854,7 @@ int launch_sort(mtpt_handle* h, int c, int o, const View& vin) {
     const bool fresh = h->fresh;
     h->fresh = false;
     if constexpr (!View::kBatch) {
-        if (fresh) {
+        if (fresh && !h->reactive) {      // (the records carry one species)
             if (h->tangent_on) return launch_sort_rec<DIM, true>(h, c, o, vin);
             return launch_sort_rec<DIM, false>(h, c, o, vin);
         }
@@ -869,6 +879,52 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
     k_exchange_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
         n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
         h->mass[c].p, nb);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
+}
+
+// Species B of a reaction run: its transfer with the weights of this step
+// (the row sums and neighbour lists of species A's passes), then the
+// reaction of both species on every particle (k_react).  B's masses move
+// from buffer o to c like A's.
+template <int DIM, class View>
+int launch_species_b(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
+                     int o, int c) {
+    const int blocks = grid_for(n);
+    cudaStream_t st = h->stream;
+    if (h->precision == MTPT_FP32W) {
+        k_split_mass<<<blocks, kBlock, 0, st>>>(n, h->massb[o].p, h->ex.p);
+        const NbList32 nb{h->nb32_e.p, h->nb32_e.p ? h->nb32_cap : 0};
+        MTPT_TIMED(h, "exchange_f32");
+        if (h->pair_block == 128)
+            k_exchange_f32<DIM, View, 128><<<int((n + 127) / 128), 128, 0, st>>>(
+                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->massb[o].p,
+                h->massb[c].p, nb);
+        else
+            k_exchange_f32<DIM, View, 256><<<int((n + 255) / 256), 256, 0, st>>>(
+                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->massb[o].p,
+                h->massb[c].p, nb);
+    } else {
+        MTPT_TIMED(h, "exchange_f64");
+        k_exchange_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
+            h->massb[o].p, h->massb[c].p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap});
+    }
+    MTPT_CUDA_TRY(cudaGetLastError());
+    // kp = k N / V (C = N M / V), from the run's box
+    const mtpt_params& p = h->reals[0].prm;
+    double vol = 1.0;
+    for (int a = 0; a < h->dim; ++a) vol *= p.hi[a] - p.lo[a];
+    const double kp = h->react_k * double(h->n) / vol;
+    {
+        MTPT_TIMED(h, "react");
+        if (h->precision == MTPT_FP32W)
+            k_react<false><<<blocks, kBlock, 0, st>>>(n, h->mass[c].p, h->massb[c].p, kp, p.dt,
+                                                      float(kp * p.dt));
+        else
+            k_react<true><<<blocks, kBlock, 0, st>>>(n, h->mass[c].p, h->massb[c].p, kp, p.dt,
+                                                     float(kp * p.dt));
+    }
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
 }
@@ -964,9 +1020,11 @@ int launch_step(mtpt_handle* h, int flags) {
         }
     }
     MTPT_CUDA_TRY(cudaGetLastError());
+    if (h->reactive) MTPT_TRY((launch_species_b<DIM, View>(h, n, stride, pos_s, vs, o, c)));
     // positions and ids live in o; the updated masses were written into c's
     // buffer: swap the mass pair so both sit at index o, then make o current.
     std::swap(h->mass[c], h->mass[o]);
+    if (h->reactive) std::swap(h->massb[c], h->massb[o]);
     h->cur = o;
     h->have_row_sums = true;
     return MTPT_OK;
@@ -997,6 +1055,7 @@ int capture_two_steps(mtpt_handle* h, int flags) {
     const int cur0 = h->cur;
     const bool rows0 = h->have_row_sums, fresh0 = h->fresh;
     DevBuf<double> mass0 = h->mass[0], mass1 = h->mass[1];
+    DevBuf<double> massb0 = h->massb[0], massb1 = h->massb[1];
     h->stream = h->capture_stream;
     MTPT_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = dispatch_step(h, flags);
@@ -1010,6 +1069,8 @@ int capture_two_steps(mtpt_handle* h, int flags) {
     h->fresh = fresh0;
     h->mass[0] = mass0;
     h->mass[1] = mass1;
+    h->massb[0] = massb0;
+    h->massb[1] = massb1;
     if (ec != cudaSuccess || rc != MTPT_OK || !graph) {
         (void)cudaGetLastError();
         if (graph) cudaGraphDestroy(graph);
@@ -1212,6 +1273,9 @@ int load_particles_body(mtpt_handle* h, const int64_t* counts, const double* pos
     h->have_particles = true;
     h->adj_ready = false;
     h->fresh = true;
+    // species B starts at zero on newly loaded particles
+    if (h->reactive && n > 0)
+        MTPT_CUDA_TRY(cudaMemsetAsync(h->massb[b].p, 0, size_t(n) * sizeof(double), h->stream));
     return MTPT_OK;
 }
 
@@ -1601,7 +1665,7 @@ extern "C" {
 
 int mtpt_adjoint_forward(mtpt_handle* h, int64_t nsteps, int64_t checkpoint_every) {
     if (!h || nsteps < 1 || checkpoint_every < 1) return MTPT_ERR_INVALID_ARG;
-    if (!h->have_particles || h->ntiles > 0) return MTPT_ERR_STATE;
+    if (!h->have_particles || h->ntiles > 0 || h->reactive) return MTPT_ERR_STATE;
     if (h->nreal != 1 || !h->any_transfer || !(h->reals[0].prm.D > 0.0)) return MTPT_ERR_INVALID_ARG;
     const int64_t n = h->n;
     const size_t cap = size_t(std::max<int64_t>(h->cap, 1));
@@ -1733,6 +1797,7 @@ int mtpt_destroy(mtpt_handle* h) {
     h->partial.release(); h->acc.release();
     h->nb_j.release(); h->nb_k.release(); h->nb_count.release();
     h->nb32_e.release();
+    h->massb[0].release(); h->massb[1].release();
     h->adj_nb_j.release(); h->adj_nb_k.release(); h->adj_nb_count.release();
     h->tile_counts.release(); h->tile_base.release(); h->tile_cursor.release();
     h->tile_native.release(); h->tile_flag.release(); h->tile_keep.release();
@@ -1848,6 +1913,8 @@ int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const
     }
     MTPT_CUDA_TRY(cudaEventRecord(h->in_free[slot], h->stream));
     MTPT_CUDA_TRY(cudaMemsetAsync(h->pair_counter.p, 0, sizeof(unsigned long long), h->stream));
+    if (h->reactive)                  // species B starts at zero on the new particles
+        MTPT_CUDA_TRY(cudaMemsetAsync(h->massb[f].p, 0, size_t(n) * sizeof(double), h->stream));
     h->in_next = 1 - slot;
     h->cur = f;
     h->step = 0;
@@ -2044,11 +2111,12 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
     // snapshot of the current state (the trials step it)
     const int64_t n = h->n;
     const int d = h->dim;
-    DevBuf<double> spos, smass;
+    DevBuf<double> spos, smass, smassb;
     DevBuf<uint32_t> sid, srid;
     auto free_snapshot = [&]() {
         spos.release();
         smass.release();
+        smassb.release();
         sid.release();
         srid.release();
     };
@@ -2056,6 +2124,7 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
         GrowAll g;
         g.want(spos, size_t(d) * size_t(std::max<int64_t>(n, 1)));
         g.want(smass, size_t(std::max<int64_t>(n, 1)));
+        if (h->reactive) g.want(smassb, size_t(std::max<int64_t>(n, 1)));
         g.want(sid, size_t(std::max<int64_t>(n, 1)));
         if (h->batch) g.want(srid, size_t(std::max<int64_t>(n, 1)));
         MTPT_TRY(g.commit());
@@ -2072,6 +2141,9 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
             MTPT_CUDA_TRY(cudaMemcpy2DAsync(spos.p, row, h->pos[c0].p, pitch, row, d,
                                             cudaMemcpyDeviceToDevice, h->stream));
             MTPT_CUDA_TRY(cudaMemcpyAsync(smass.p, h->mass[c0].p, row, cudaMemcpyDeviceToDevice, h->stream));
+            if (h->reactive)
+                MTPT_CUDA_TRY(cudaMemcpyAsync(smassb.p, h->massb[c0].p, row, cudaMemcpyDeviceToDevice,
+                                              h->stream));
             MTPT_CUDA_TRY(cudaMemcpyAsync(sid.p, h->id[c0].p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
             if (h->batch)
                 MTPT_CUDA_TRY(cudaMemcpyAsync(srid.p, h->rid[c0].p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
@@ -2081,6 +2153,9 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
             MTPT_CUDA_TRY(cudaMemcpy2DAsync(h->pos[c0].p, pitch, spos.p, row, row, d,
                                             cudaMemcpyDeviceToDevice, h->stream));
             MTPT_CUDA_TRY(cudaMemcpyAsync(h->mass[c0].p, smass.p, row, cudaMemcpyDeviceToDevice, h->stream));
+            if (h->reactive)
+                MTPT_CUDA_TRY(cudaMemcpyAsync(h->massb[c0].p, smassb.p, row, cudaMemcpyDeviceToDevice,
+                                              h->stream));
             MTPT_CUDA_TRY(cudaMemcpyAsync(h->id[c0].p, sid.p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
             if (h->batch)
                 MTPT_CUDA_TRY(cudaMemcpyAsync(h->rid[c0].p, srid.p, size_t(n) * 4, cudaMemcpyDeviceToDevice, h->stream));
@@ -2400,7 +2475,7 @@ int mtpt_tiling_factors(int32_t dim, const double* lo, const double* hi, int32_t
 
 int mtpt_set_tiling(mtpt_handle* h, const mtpt_tiling* t) {
     if (!h || !t) return MTPT_ERR_INVALID_ARG;
-    if (h->nreal != 1 || h->batch || h->have_particles) return MTPT_ERR_STATE;
+    if (h->nreal != 1 || h->batch || h->have_particles || h->reactive) return MTPT_ERR_STATE;
     RealHost& R = h->reals[0];
     const mtpt_params& p = R.prm;
     int64_t total = 1;
@@ -2493,6 +2568,54 @@ int mtpt_get_ids(mtpt_handle* h, uint32_t* out) {
     MTPT_CUDA_TRY(cudaMemcpyAsync(out, h->id[h->cur].p, size_t(h->n) * 4, cudaMemcpyDeviceToHost,
                                   h->stream));
     return read_status(h);
+}
+
+int mtpt_set_reaction(mtpt_handle* h, double k) {
+    if (!h) return MTPT_ERR_INVALID_ARG;
+    if (h->batch || h->nreal != 1 || h->ntiles > 0) return MTPT_ERR_STATE;
+    if (!(k >= 0.0) || !std::isfinite(k)) return MTPT_ERR_INVALID_ARG;
+    if (!h->reactive && h->cap > 0) {
+        GrowAll g;
+        for (int b = 0; b < 2; ++b) g.want(h->massb[b], size_t(h->cap));
+        MTPT_TRY(g.commit());
+        if (h->have_particles && h->n > 0)
+            MTPT_CUDA_TRY(cudaMemsetAsync(h->massb[h->cur].p, 0, size_t(h->n) * sizeof(double),
+                                          h->stream));
+    }
+    drop_graph(h);
+    h->reactive = true;
+    h->react_k = k;
+    h->adj_ready = false;
+    return MTPT_OK;
+}
+
+int mtpt_set_masses_b(mtpt_handle* h, const double* mass_b) {
+    if (!h || (!mass_b && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->reactive || !h->have_particles) return MTPT_ERR_STATE;
+    const int64_t n = h->n;
+    if (n == 0) return MTPT_OK;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(mass_b[i] >= 0.0) || !std::isfinite(mass_b[i]) ||
+            (h->precision == MTPT_FP32W && mass_b[i] > 1e30))
+            return MTPT_ERR_INVALID_ARG;
+    MTPT_TRY(ensure_out_tmp(h));
+    MTPT_CUDA_TRY(cudaMemcpyAsync(h->out_tmp.p, mass_b, size_t(n) * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->stream));
+    // to the current order: slot s holds the particle of input index id[s]
+    k_take_by_id<<<grid_for(n), kBlock, 0, h->stream>>>(int(n), h->id[h->cur].p, h->out_tmp.p,
+                                                        h->massb[h->cur].p);
+    MTPT_CUDA_TRY(cudaGetLastError());
+    MTPT_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return MTPT_OK;
+}
+
+int mtpt_get_masses_b(mtpt_handle* h, double* out) {
+    if (!h || (!out && h->n > 0)) return MTPT_ERR_INVALID_ARG;
+    if (!h->reactive || !h->have_particles) return MTPT_ERR_STATE;
+    if (h->n == 0) return MTPT_OK;
+    MTPT_TRY(ensure_out_tmp(h));
+    MTPT_TRY(unpermute_to(h, h->massb[h->cur].p, 1, h->out_tmp.p));
+    return copy_out_host(h, 1, out);
 }
 
 int mtpt_debug_fail_alloc(int64_t nth, int64_t* remaining) {

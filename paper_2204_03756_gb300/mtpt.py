@@ -43,7 +43,8 @@ EXPORTED = [
     "mtpt_adjoint_backward", "mtpt_status_string", "mtpt_check_word",
     "mtpt_set_particles_async", "mtpt_get_masses_async", "mtpt_tiling_factors",
     "mtpt_set_tiling", "mtpt_set_particles_tile", "mtpt_tile_pack", "mtpt_tile_transfer",
-    "mtpt_get_ids", "mtpt_debug_fail_alloc",
+    "mtpt_get_ids", "mtpt_debug_fail_alloc", "mtpt_set_reaction", "mtpt_set_masses_b",
+    "mtpt_get_masses_b",
 ]
 
 
@@ -174,6 +175,9 @@ def load():
     lib.mtpt_tile_transfer.argtypes = [vp, ctypes.c_int64, vp]
     lib.mtpt_get_ids.argtypes = [vp, vp]
     lib.mtpt_debug_fail_alloc.argtypes = [ctypes.c_int64, P(ctypes.c_int64)]
+    lib.mtpt_set_reaction.argtypes = [vp, ctypes.c_double]
+    lib.mtpt_set_masses_b.argtypes = [vp, vp]
+    lib.mtpt_get_masses_b.argtypes = [vp, vp]
     lib.mtpt_status_string.argtypes = [ctypes.c_int]
     lib.mtpt_status_string.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -521,6 +525,21 @@ def mtpt_get_ids(h, n: int) -> np.ndarray:
     return out
 
 
+def mtpt_set_reaction(h, k: float) -> None:
+    _check(load().mtpt_set_reaction(h, float(k)), "mtpt_set_reaction")
+
+
+def mtpt_set_masses_b(h, mass_b) -> None:
+    mass_b = np.ascontiguousarray(np.asarray(mass_b, dtype=np.float64).ravel())
+    _check(load().mtpt_set_masses_b(h, mass_b.ctypes.data), "mtpt_set_masses_b")
+
+
+def mtpt_get_masses_b(h, n: int) -> np.ndarray:
+    out = np.empty(n, dtype=np.float64)
+    _check(load().mtpt_get_masses_b(h, out.ctypes.data), "mtpt_get_masses_b")
+    return out
+
+
 def mtpt_debug_fail_alloc(nth: int) -> int:
     """Make the nth device allocation from now fail (0: off); returns how many
     the previous setting still had to go."""
@@ -581,6 +600,16 @@ class Simulation:
 
     def autotune(self, trial_steps: int = 4) -> dict:
         return mtpt_autotune(self.h, trial_steps)
+
+    def set_reaction(self, k: float, mass_b=None):
+        """Bimolecular reaction A + B -> 0 with rate constant k; species B's
+        masses (input order) when given, else zero."""
+        mtpt_set_reaction(self.h, k)
+        if mass_b is not None:
+            mtpt_set_masses_b(self.h, mass_b)
+
+    def masses_b(self) -> np.ndarray:
+        return mtpt_get_masses_b(self.h, self.n)
 
     def set_tuning(self, cell_scale: float = 1.0, pair_block: int = 256):
         mtpt_set_tuning(self.h, cell_scale, pair_block)

@@ -23,6 +23,10 @@ Workloads (sizes and parameters of the paper's test problem family, Sec. 2):
   steps.  The velocity is small so that over the run the particles carried
   into the downstream walls (where zero-flux reflection piles them up in a
   thin dense layer) stay a small fraction of the whole.
+* ``reaction_2d``    N = 4,000,000 in [0,2000]^2 (density 1), species A 1
+  where x < 1000, species B its complement, D = 1, kappa = 0.5, dt = 0.1,
+  A + B -> 0 with rate constant k = 1 (the reaction extension of Sec. 8),
+  1,000 steps: the two species meet along the line x = 1000.
 
 Every workload takes kappa = 0.5, beta = 1 and lambda = 3 (cutoff
 psi = 3 sqrt(4 D_MT dt)), and may be scaled down (``n`` with the box scaled
@@ -59,6 +63,7 @@ class Workload:
     seed: int = SEED_BASE
     mass_param: float = 0.0  # Heaviside split x, or Gaussian sigma
     v: tuple = (0.0, 0.0, 0.0)  # uniform velocity (advection)
+    react_k: float = 0.0     # rate constant of A + B -> 0 (0: no second species)
 
     def scaled(self, n: int) -> "Workload":
         """Same density and parameters with ``n`` particles: every box edge
@@ -85,6 +90,9 @@ WORKLOADS = {
     "advection_2d": Workload("advection_2d", 2, 4_000_000, (0.0, 0.0), (2000.0, 2000.0),
                              1.0, 0.5, 0.1, 1000, "heaviside_left", seed=SEED_BASE + 7,
                              mass_param=500.0, v=(0.1, 0.05, 0.0)),
+    "reaction_2d": Workload("reaction_2d", 2, 4_000_000, (0.0, 0.0), (2000.0, 2000.0),
+                            1.0, 0.5, 0.1, 1000, "heaviside_left", seed=SEED_BASE + 8,
+                            mass_param=1000.0, react_k=1.0),
 }
 
 
@@ -111,6 +119,12 @@ def masses(w: Workload, pos: np.ndarray) -> np.ndarray:
     if w.mass_kind == "ones":
         return np.ones(pos.shape[1], dtype=np.float64)
     raise ValueError(f"unknown mass kind {w.mass_kind!r}")
+
+
+def masses_b(w: Workload, pos: np.ndarray) -> np.ndarray:
+    """Species B of a reaction workload: the complement of A's Heaviside
+    initial condition (A on the left of the split, B on the right)."""
+    return 1.0 - masses(w, pos)
 
 
 def initial_state(w: Workload):
