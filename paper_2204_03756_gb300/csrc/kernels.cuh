@@ -1380,11 +1380,18 @@ struct FluxSum {
     float rs, two_beta;
     float2 ms;
     float acc = 0.0f, comp = 0.0f;
-    __device__ __forceinline__ void add(const float4& xj, float K, bool accept = true) {
-        const float W = __fdividef(two_beta * K, __fadd_rn(rs, xj.z));
-        const float dm = __fadd_rn(__fsub_rn(xj.x, ms.x), __fsub_rn(xj.y, ms.y));
+    // the pair's weight (shared by both species of a reaction run)
+    __device__ __forceinline__ float weight(const float4& xj, float K) const {
+        return __fdividef(two_beta * K, __fadd_rn(rs, xj.z));
+    }
+    // the flux of neighbour mass split mj under weight W
+    __device__ __forceinline__ void add_w(float2 mj, float W, bool accept = true) {
+        const float dm = __fadd_rn(__fsub_rn(mj.x, ms.x), __fsub_rn(mj.y, ms.y));
         // a rejected candidate (and the self pair) adds an exact zero
         neumaier_add(acc, comp, accept ? __fmul_rn(dm, W) : 0.0f);
+    }
+    __device__ __forceinline__ void add(const float4& xj, float K, bool accept = true) {
+        add_w(make_float2(xj.x, xj.y), weight(xj, K), accept);
     }
     // two binary64 additions per particle: acc + comp is exact in binary64
     __device__ __forceinline__ double delta() const {
@@ -1414,25 +1421,130 @@ __device__ __noinline__ float2 search_flux(uint32_t s, int64_t stride,
     return make_float2(g.acc, g.comp);
 }
 
+// ---------------------------------------------------------------------------
+// Bimolecular reaction A + B -> 0 (the extension Sec. 8 names; the model is
+// this library's reading).  After the transfer of both species with the same
+// weights, each particle reacts well mixed over dt: with concentrations
+// C = N M / V the rate law dC_A/dt = dC_B/dt = -k C_A C_B is
+// da/dt = db/dt = -kp a b on its masses, kp = k N / V, solved exactly over
+// dt.  With `big` the larger of a and b, x = kp (big - small) dt,
+// phi(x) = (1 - e^-x) / x (phi(0) = 1) and q = 1 + kp small dt phi(x):
+//   big' = big / q,   small' = small e^-x / q
+// (the closed form a(t) = D a / (a - b e^-kpDt), D = a - b, rearranged so
+// that neither D -> 0 nor the species in deficit loses digits).  A particle
+// with a negative mass of either species (sign bit set) does not react.
+// ---------------------------------------------------------------------------
+
+// The precision form's mass split of species B for its pass 2: the binary32
+// head/tail of mass_b[s] (species A's is in the particle record ex).
+__global__ void __launch_bounds__(kBlock)
+k_split_mass(int n, const double* __restrict__ mass_b, float2* __restrict__ exb) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float hi, lo;
+    split_double(mass_b[s], &hi, &lo);
+    exb[s] = make_float2(hi, lo);
+}
+
+// F64: binary64 throughout (exp, expm1 and IEEE division).  Otherwise (the
+// precision form) the two factors 1/q and e^-x / q in binary32 from the
+// binary32 heads of the masses (kpdt_f = kp dt rounded to binary32), each
+// applied to its binary64 mass with one binary64 multiply.
+template <bool F64>
+__device__ __forceinline__ void react_masses(double& ma, double& mb, double kp, double dt,
+                                             float kpdt_f) {
+    const double a = ma, b = mb;
+    const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
+    if ((ka | kb) < 0) return;                       // a negative mass: no reaction
+    const bool a_big = ka >= kb;                     // non-negative values order by their bits
+    const double big = a_big ? a : b, small = a_big ? b : a;
+    double nbig, nsmall;
+    if constexpr (F64) {
+        const double x = __dmul_rn(__dmul_rn(kp, __dsub_rn(big, small)), dt);
+        const double phi = x > 0.0 ? -expm1(-x) / x : 1.0;
+        const double q = __dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(kp, small), dt), phi));
+        nbig = big / q;
+        nsmall = __dmul_rn(small, exp(-x)) / q;
+    } else {
+        float bh, bl, sh, sl;
+        split_double(big, &bh, &bl);
+        split_double(small, &sh, &sl);
+        const float x = __fmul_rn(kpdt_f, __fsub_rn(bh, sh));
+        const float phi = x > 0.0f ? __fdiv_rn(-expm1f(-x), x) : 1.0f;
+        const float rq = __frcp_rn(__fmaf_rn(__fmul_rn(kpdt_f, sh), phi, 1.0f));
+        nbig = __dmul_rn(big, f32_to_f64(rq));
+        nsmall = __dmul_rn(small, f32_to_f64(__fmul_rn(expf(-x), rq)));
+    }
+    ma = a_big ? nbig : nsmall;
+    mb = a_big ? nsmall : nbig;
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(kBlock)
+k_react(int n, double* __restrict__ ma, double* __restrict__ mb, double kp, double dt,
+        float kpdt_f) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double a = ma[s], b = mb[s];
+    react_masses<F64>(a, b, kp, dt, kpdt_f);
+    ma[s] = a;
+    mb[s] = b;
+}
+
+// As search_flux, for both species of a reaction run (species B's mass split
+// in exb): {acc_A, comp_A, acc_B, comp_B}.
+template <int DIM, class View>
+__device__ __noinline__ float4 search_flux2(uint32_t s, int64_t stride,
+                                            const double* __restrict__ pos,
+                                            const float4* __restrict__ rec,
+                                            const uint32_t* __restrict__ cell,
+                                            const uint32_t* __restrict__ start, const View& v,
+                                            const float4* __restrict__ ex,
+                                            const float2* __restrict__ exb, float rs, float2 ms,
+                                            float2 msb, float two_beta) {
+    const RealParams& P = v.of_sorted(s);
+    const float na = -P.pp.a_log2e;
+    FluxSum a{rs, two_beta, ms}, b{rs, two_beta, msb};
+    scan_neighbours<DIM, true>(s, cell_arg<DIM>(cell, s), stride, rec, pos, start, P,
+                         [&](uint32_t j, float d2f, bool accept) {
+                             const float4 xj = __ldg(ex + j);
+                             const float W = a.weight(xj, ex2_approx(na * d2f));
+                             a.add_w(make_float2(xj.x, xj.y), W, accept);
+                             b.add_w(__ldg(exb + j), W, accept);
+                         });
+    return make_float4(a.acc, a.comp, b.acc, b.comp);
+}
+
 // Pass 2, precision form: each particle walks its neighbour list (the
 // accepted neighbours only, with pass 1's K), two entries at a time so two
 // gathers are in flight, or searches when it has none (no lists, or an
 // overflowing one).  Both add the same terms in the same order.
-template <int DIM, class View, int BLOCK>
+template <int DIM, class View, int BLOCK, bool TWO = false>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
                const __grid_constant__ View v, const float4* __restrict__ ex,
-               const double* __restrict__ mass, double* __restrict__ mass_out, NbList32 nb) {
+               const double* __restrict__ mass, double* __restrict__ mass_out, NbList32 nb,
+               const float2* __restrict__ exb = nullptr, const double* __restrict__ mass_b = nullptr,
+               double* __restrict__ mass_b_out = nullptr, double kp = 0.0, double dt = 0.0,
+               float kpdt_f = 0.0f) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const RealParams& P = v.of_sorted(uint32_t(s));
     if (!P.transfer) {
-        mass_out[s] = mass[s];
+        if constexpr (TWO) {
+            double a = mass[s], b = mass_b[s];
+            react_masses<false>(a, b, kp, dt, kpdt_f);
+            mass_out[s] = a;
+            mass_b_out[s] = b;
+        } else {
+            mass_out[s] = mass[s];
+        }
         return;
     }
     const float4 xs = ex[s];
     FluxSum f{xs.z, float(2.0 * P.pp.beta), make_float2(xs.x, xs.y)};   // beta folded into W
+    FluxSum g{xs.z, f.two_beta, TWO ? __ldg(exb + s) : make_float2(0.0f, 0.0f)};
     const uint32_t listed = nb.cap > 0 ? __float_as_uint(xs.w) : 0xffffffffu;
     if (listed <= uint32_t(nb.cap)) {
         const uint2* e = nb.e + s;
@@ -1440,20 +1552,52 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
         for (; k + 2 <= listed; k += 2, e += 2 * stride) {
             const uint2 q0 = __ldg(e), q1 = __ldg(e + stride);
             const float4 x0 = __ldg(ex + q0.x), x1 = __ldg(ex + q1.x);
-            f.add(x0, __uint_as_float(q0.y));
-            f.add(x1, __uint_as_float(q1.y));
+            if constexpr (TWO) {
+                const float2 b0 = __ldg(exb + q0.x), b1 = __ldg(exb + q1.x);
+                const float w0 = f.weight(x0, __uint_as_float(q0.y));
+                f.add_w(make_float2(x0.x, x0.y), w0);
+                g.add_w(b0, w0);
+                const float w1 = f.weight(x1, __uint_as_float(q1.y));
+                f.add_w(make_float2(x1.x, x1.y), w1);
+                g.add_w(b1, w1);
+            } else {
+                f.add(x0, __uint_as_float(q0.y));
+                f.add(x1, __uint_as_float(q1.y));
+            }
         }
         if (k < listed) {
             const uint2 q = __ldg(e);
-            f.add(__ldg(ex + q.x), __uint_as_float(q.y));
+            const float4 x = __ldg(ex + q.x);
+            if constexpr (TWO) {
+                const float w = f.weight(x, __uint_as_float(q.y));
+                f.add_w(make_float2(x.x, x.y), w);
+                g.add_w(__ldg(exb + q.x), w);
+            } else {
+                f.add(x, __uint_as_float(q.y));
+            }
         }
+    } else if constexpr (TWO) {
+        const float4 sum = search_flux2<DIM>(uint32_t(s), stride, pos, rec, cell, start, v, ex, exb,
+                                             f.rs, f.ms, g.ms, f.two_beta);
+        f.acc = sum.x;
+        f.comp = sum.y;
+        g.acc = sum.z;
+        g.comp = sum.w;
     } else {
         const float2 sum = search_flux<DIM>(uint32_t(s), stride, pos, rec, cell, start, v, ex,
                                             f.rs, f.ms, f.two_beta);
         f.acc = sum.x;
         f.comp = sum.y;
     }
-    mass_out[s] = __dadd_rn(mass[s], f.delta());
+    if constexpr (TWO) {
+        // both species' transfer, then the reaction on this particle
+        double a = __dadd_rn(mass[s], f.delta()), b = __dadd_rn(mass_b[s], g.delta());
+        react_masses<false>(a, b, kp, dt, kpdt_f);
+        mass_out[s] = a;
+        mass_b_out[s] = b;
+    } else {
+        mass_out[s] = __dadd_rn(mass[s], f.delta());
+    }
 }
 
 // Test support: every accepted ordered pair j != s as (id_s, id_j).
@@ -1478,67 +1622,6 @@ k_emit_pairs(int n, int64_t stride, const double* __restrict__ pos, const float4
                                   out_j[k] = id[j];
                               }
                           });
-}
-
-// ---------------------------------------------------------------------------
-// Bimolecular reaction A + B -> 0 (the extension Sec. 8 names; the model is
-// this library's reading).  After the transfer of both species with the same
-// weights, each particle reacts well mixed over dt: with concentrations
-// C = N M / V the rate law dC_A/dt = dC_B/dt = -k C_A C_B is
-// da/dt = db/dt = -kp a b on its masses, kp = k N / V, solved exactly over
-// dt.  With `big` the larger of a and b, x = kp (big - small) dt,
-// phi(x) = (1 - e^-x) / x (phi(0) = 1) and q = 1 + kp small dt phi(x):
-//   big' = big / q,   small' = small e^-x / q
-// (the closed form a(t) = D a / (a - b e^-kpDt), D = a - b, rearranged so
-// that neither D -> 0 nor the species in deficit loses digits).  A particle
-// with a negative mass of either species (sign bit set) does not react.
-// ---------------------------------------------------------------------------
-
-// The precision form's mass split for pass 2 of species B: ex[s].x/.y take
-// the binary32 head/tail of mass_b[s] (the row sum and the list length stay).
-__global__ void __launch_bounds__(kBlock)
-k_split_mass(int n, const double* __restrict__ mass_b, float4* __restrict__ ex) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    float hi, lo;
-    split_double(mass_b[s], &hi, &lo);
-    reinterpret_cast<float2*>(ex)[2 * s] = make_float2(hi, lo);
-}
-
-// F64: binary64 throughout (exp, expm1 and IEEE division).  Otherwise (the
-// precision form) the two factors 1/q and e^-x / q in binary32 from the
-// binary32 heads of the masses (kpdt_f = kp dt rounded to binary32), each
-// applied to its binary64 mass with one binary64 multiply.
-template <bool F64>
-__global__ void __launch_bounds__(kBlock)
-k_react(int n, double* __restrict__ ma, double* __restrict__ mb, double kp, double dt,
-        float kpdt_f) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const double a = ma[s], b = mb[s];
-    const long long ka = __double_as_longlong(a), kb = __double_as_longlong(b);
-    if ((ka | kb) < 0) return;                       // a negative mass: no reaction
-    const bool a_big = ka >= kb;                     // non-negative values order by their bits
-    const double big = a_big ? a : b, small = a_big ? b : a;
-    double nbig, nsmall;
-    if constexpr (F64) {
-        const double x = __dmul_rn(__dmul_rn(kp, __dsub_rn(big, small)), dt);
-        const double phi = x > 0.0 ? -expm1(-x) / x : 1.0;
-        const double q = __dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(kp, small), dt), phi));
-        nbig = big / q;
-        nsmall = __dmul_rn(small, exp(-x)) / q;
-    } else {
-        float bh, bl, sh, sl;
-        split_double(big, &bh, &bl);
-        split_double(small, &sh, &sl);
-        const float x = __fmul_rn(kpdt_f, __fsub_rn(bh, sh));
-        const float phi = x > 0.0f ? __fdiv_rn(-expm1f(-x), x) : 1.0f;
-        const float rq = __frcp_rn(__fmaf_rn(__fmul_rn(kpdt_f, sh), phi, 1.0f));
-        nbig = __dmul_rn(big, f32_to_f64(rq));
-        nsmall = __dmul_rn(small, f32_to_f64(__fmul_rn(expf(-x), rq)));
-    }
-    ma[s] = a_big ? nbig : nsmall;
-    mb[s] = a_big ? nsmall : nbig;
 }
 
 // ---------------------------------------------------------------------------

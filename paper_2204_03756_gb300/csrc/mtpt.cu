@@ -222,6 +222,7 @@ struct mtpt_handle {
     bool reactive = false;
     double react_k = 0.0;
     DevBuf<double> massb[2];
+    DevBuf<float2> exb;               // precision form: species B's mass split for pass 2
     DevBuf<float4> rec;
     DevBuf<float2> corners;
     DevBuf<int> corner_first;
@@ -647,6 +648,7 @@ int ensure_capacity(mtpt_handle* h, int64_t n, int64_t keep = 0) {
             g.want(h->pos[b], size_t(d) * cap);
             g.want(h->mass[b], size_t(cap));
             if (h->reactive) g.want(h->massb[b], size_t(cap));
+            if (h->reactive && b == 0 && h->precision == MTPT_FP32W) g.want(h->exb, size_t(cap));
             g.want(h->id[b], size_t(cap));
             if (h->batch) g.want(h->rid[b], size_t(cap));
         }
@@ -863,6 +865,16 @@ int launch_sort(mtpt_handle* h, int c, int o, const View& vin) {
     return launch_sort_t<DIM, View, false>(h, c, o, vin);
 }
 
+// The reaction's particle rate kp = k N / V (C = N M / V, V the run's box)
+// and the step dt.
+void reaction_rate(const mtpt_handle* h, double* kp, double* dt) {
+    const mtpt_params& p = h->reals[0].prm;
+    double vol = 1.0;
+    for (int a = 0; a < h->dim; ++a) vol *= p.hi[a] - p.lo[a];
+    *kp = h->react_k * double(h->n) / vol;
+    *dt = p.dt;
+}
+
 template <int DIM, class View, int BLOCK>
 int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
                      int o, int c) {
@@ -875,6 +887,18 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
             h->pair_counter.p,
             h->ntiles > 0 ? h->id[o].p : nullptr, nb);
     }
+    if (h->reactive) {
+        // species B's split, then one pass 2 for both species and the reaction
+        k_split_mass<<<grid_for(n), kBlock, 0, h->stream>>>(n, h->massb[o].p, h->exb.p);
+        double kp, dt;
+        reaction_rate(h, &kp, &dt);
+        MTPT_TIMED(h, "exchange_f32");
+        k_exchange_f32<DIM, View, BLOCK, true><<<blocks, BLOCK, 0, h->stream>>>(
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
+            h->mass[c].p, nb, h->exb.p, h->massb[o].p, h->massb[c].p, kp, dt, float(kp * dt));
+        MTPT_CUDA_TRY(cudaGetLastError());
+        return MTPT_OK;
+    }
     MTPT_TIMED(h, "exchange_f32");
     k_exchange_f32<DIM, View, BLOCK><<<blocks, BLOCK, 0, h->stream>>>(
         n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
@@ -883,47 +907,30 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
     return MTPT_OK;
 }
 
-// Species B of a reaction run: its transfer with the weights of this step
-// (the row sums and neighbour lists of species A's passes), then the
-// reaction of both species on every particle (k_react).  B's masses move
-// from buffer o to c like A's.
+// Species B of a binary64 reaction run: its transfer with the weights of
+// this step (the row sums and neighbour lists of species A's passes), then
+// the reaction on every particle (k_react).  B's masses move from buffer o
+// to c like A's.  (The precision form does both species and the reaction in
+// one pass 2: launch_pairs_f32.)
 template <int DIM, class View>
 int launch_species_b(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
                      int o, int c) {
+    if (h->precision == MTPT_FP32W) return MTPT_OK;
     const int blocks = grid_for(n);
     cudaStream_t st = h->stream;
-    if (h->precision == MTPT_FP32W) {
-        k_split_mass<<<blocks, kBlock, 0, st>>>(n, h->massb[o].p, h->ex.p);
-        const NbList32 nb{h->nb32_e.p, h->nb32_e.p ? h->nb32_cap : 0};
-        MTPT_TIMED(h, "exchange_f32");
-        if (h->pair_block == 128)
-            k_exchange_f32<DIM, View, 128><<<int((n + 127) / 128), 128, 0, st>>>(
-                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->massb[o].p,
-                h->massb[c].p, nb);
-        else
-            k_exchange_f32<DIM, View, 256><<<int((n + 255) / 256), 256, 0, st>>>(
-                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->massb[o].p,
-                h->massb[c].p, nb);
-    } else {
+    {
         MTPT_TIMED(h, "exchange_f64");
         k_exchange_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
             n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
             h->massb[o].p, h->massb[c].p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap});
     }
     MTPT_CUDA_TRY(cudaGetLastError());
-    // kp = k N / V (C = N M / V), from the run's box
-    const mtpt_params& p = h->reals[0].prm;
-    double vol = 1.0;
-    for (int a = 0; a < h->dim; ++a) vol *= p.hi[a] - p.lo[a];
-    const double kp = h->react_k * double(h->n) / vol;
+    double kp, dt;
+    reaction_rate(h, &kp, &dt);
     {
         MTPT_TIMED(h, "react");
-        if (h->precision == MTPT_FP32W)
-            k_react<false><<<blocks, kBlock, 0, st>>>(n, h->mass[c].p, h->massb[c].p, kp, p.dt,
-                                                      float(kp * p.dt));
-        else
-            k_react<true><<<blocks, kBlock, 0, st>>>(n, h->mass[c].p, h->massb[c].p, kp, p.dt,
-                                                     float(kp * p.dt));
+        k_react<true><<<blocks, kBlock, 0, st>>>(n, h->mass[c].p, h->massb[c].p, kp, dt,
+                                                 float(kp * dt));
     }
     MTPT_CUDA_TRY(cudaGetLastError());
     return MTPT_OK;
@@ -1797,7 +1804,7 @@ int mtpt_destroy(mtpt_handle* h) {
     h->partial.release(); h->acc.release();
     h->nb_j.release(); h->nb_k.release(); h->nb_count.release();
     h->nb32_e.release();
-    h->massb[0].release(); h->massb[1].release();
+    h->massb[0].release(); h->massb[1].release(); h->exb.release();
     h->adj_nb_j.release(); h->adj_nb_k.release(); h->adj_nb_count.release();
     h->tile_counts.release(); h->tile_base.release(); h->tile_cursor.release();
     h->tile_native.release(); h->tile_flag.release(); h->tile_keep.release();
@@ -2577,6 +2584,7 @@ int mtpt_set_reaction(mtpt_handle* h, double k) {
     if (!h->reactive && h->cap > 0) {
         GrowAll g;
         for (int b = 0; b < 2; ++b) g.want(h->massb[b], size_t(h->cap));
+        if (h->precision == MTPT_FP32W) g.want(h->exb, size_t(h->cap));
         MTPT_TRY(g.commit());
         if (h->have_particles && h->n > 0)
             MTPT_CUDA_TRY(cudaMemsetAsync(h->massb[h->cur].p, 0, size_t(h->n) * sizeof(double),
