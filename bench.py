@@ -80,13 +80,13 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # Valid only for the library source it was measured on: a different hash of
 # the CUDA sources and the header reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "b5186d182cdf"
+TRAFFIC_SOURCE_SHA1 = "a39d572a062a"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (88932096 + 28415488) / 4e6,
-    "scatter": (81774848 + 33553920) / 4e6,
-    "gather": (152971008 + 139163904) / 4e6,
-    "rowsum_f32": (237941760 + 292267264) / 4e6,
-    "exchange_f32": (389602560 + 28756480) / 4e6,
+    "walk_key": (88933632 + 28392704) / 4e6,
+    "scatter": (81759232 + 33905920) / 4e6,
+    "gather": (152973056 + 139597824) / 4e6,
+    "rowsum_f32": (238000384 + 292577280) / 4e6,
+    "exchange_f32": (389569280 + 28445952) / 4e6,
 }
 
 
@@ -97,7 +97,7 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 INSTR_PER_PARTICLE = {
     "walk_key": 43893462 / 4e6,
     "scatter": 4125000 / 4e6,
-    "gather": 38399212 / 4e6,
+    "gather": 38399201 / 4e6,
     "rowsum_f32": 183180239 / 4e6,
     "exchange_f32": 44836827 / 4e6,
 }
@@ -110,11 +110,11 @@ SMS, SCHEDULERS_PER_SM = 152, 4
 BINDING = {
     "exchange_f32": ("DRAM 55 % with long-scoreboard stalls on the list reads and the "
                      "neighbour-record gathers; issue 40 % at 20 of 32 active lanes"),
-    "rowsum_f32": "instruction issue: 72 % of issue slots at 18 of 32 active lanes; DRAM 32 %",
+    "rowsum_f32": "instruction issue: 74 % of issue slots at 18 of 32 active lanes; DRAM 32 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
-    "gather": "DRAM 64 % (payload reads through the permutation, cell-ordered writes)",
-    "scatter": "DRAM 43 % at 11 % issue (slot atomics, permutation and sort-key stores)",
+    "gather": "DRAM 63 % (payload reads through the permutation, cell-ordered writes)",
+    "scatter": "DRAM 42 % at 11 % issue (slot atomics, permutation and sort-key stores)",
     "walk_key": "binary64 pipe 80 % busy (x + sigma xi)",
 }
 
