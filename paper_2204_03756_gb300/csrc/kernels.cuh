@@ -1549,10 +1549,10 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
     if (listed <= uint32_t(nb.cap)) {
         const uint2* e = nb.e + s;
         uint32_t k = 0;
-        for (; k + 2 <= listed; k += 2, e += 2 * stride) {
-            const uint2 q0 = __ldg(e), q1 = __ldg(e + stride);
-            const float4 x0 = __ldg(ex + q0.x), x1 = __ldg(ex + q1.x);
-            if constexpr (TWO) {
+        if constexpr (TWO) {
+            for (; k + 2 <= listed; k += 2, e += 2 * stride) {
+                const uint2 q0 = __ldg(e), q1 = __ldg(e + stride);
+                const float4 x0 = __ldg(ex + q0.x), x1 = __ldg(ex + q1.x);
                 const float2 b0 = __ldg(exb + q0.x), b1 = __ldg(exb + q1.x);
                 const float w0 = f.weight(x0, __uint_as_float(q0.y));
                 f.add_w(make_float2(x0.x, x0.y), w0);
@@ -1560,21 +1560,28 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
                 const float w1 = f.weight(x1, __uint_as_float(q1.y));
                 f.add_w(make_float2(x1.x, x1.y), w1);
                 g.add_w(b1, w1);
-            } else {
-                f.add(x0, __uint_as_float(q0.y));
-                f.add(x1, __uint_as_float(q1.y));
             }
-        }
-        if (k < listed) {
-            const uint2 q = __ldg(e);
-            const float4 x = __ldg(ex + q.x);
-            if constexpr (TWO) {
+            if (k < listed) {
+                const uint2 q = __ldg(e);
+                const float4 x = __ldg(ex + q.x);
                 const float w = f.weight(x, __uint_as_float(q.y));
                 f.add_w(make_float2(x.x, x.y), w);
                 g.add_w(__ldg(exb + q.x), w);
-            } else {
-                f.add(x, __uint_as_float(q.y));
             }
+        } else {
+            // two entries per iteration, the next two list entries loaded
+            // while this pair's neighbour records are in flight
+            uint2 p0 = listed > 0u ? __ldg(e) : make_uint2(uint32_t(s), 0u);
+            uint2 p1 = listed > 1u ? __ldg(e + stride) : p0;
+            for (; k + 2 <= listed; k += 2, e += 2 * stride) {
+                const uint2 q0 = p0, q1 = p1;
+                const float4 x0 = __ldg(ex + q0.x), x1 = __ldg(ex + q1.x);
+                p0 = k + 2 < listed ? __ldg(e + 2 * stride) : q0;
+                p1 = k + 3 < listed ? __ldg(e + 3 * stride) : q1;
+                f.add(x0, __uint_as_float(q0.y));
+                f.add(x1, __uint_as_float(q1.y));
+            }
+            if (k < listed) f.add(__ldg(ex + p0.x), __uint_as_float(p0.y));   // p0 = entry k
         }
     } else if constexpr (TWO) {
         const float4 sum = search_flux2<DIM>(uint32_t(s), stride, pos, rec, cell, start, v, ex, exb,
