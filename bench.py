@@ -69,7 +69,7 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
         "rowsum_f64": x + r, "rowsum_f32": x + r,          # positions in, r out
         "exchange_f64": x + 8 + r + 8, "exchange_f32": x + 8 + r + 8,  # X, M, r in; M out
         "gather": 2 * (x + 8 + 4),         # state copied into cell order
-        "scatter": 8, "scan_tiles": 0, "scan_apply": 0,
+        "scatter": 8, "scan": 0,
     }
     return float(table.get(kernel, 0))
 

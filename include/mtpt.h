@@ -567,6 +567,19 @@ int mtpt_get_ids(mtpt_handle* h, uint32_t* out);
  * nothing. */
 int mtpt_debug_fail_alloc(int64_t nth, int64_t* remaining);
 
+/* Wait-limit test hook (no counterpart in the paper).  The cell-count scan of
+ * every step is one launch in which each tile of 16384 cells publishes its
+ * total and then waits, polling, for the totals of the tiles before it; after
+ * a bounded number of polls (tens of milliseconds) a tile stops waiting for
+ * one and sums that tile's counts directly, which gives the same result.
+ * From this call on, scans this process launches never publish tile `tile`
+ * (-1: off; launches already captured in a CUDA graph keep the setting they
+ * were captured with), so every tile after it runs out of polls.  *gave_up
+ * (may be NULL) receives how many times, on the current device since the
+ * library was loaded, a tile stopped waiting for an earlier one, after a
+ * device synchronisation.  MTPT_ERR_INVALID_ARG for tile < -1. */
+int mtpt_debug_scan_hold(int32_t tile, uint64_t* gave_up);
+
 /* Human-readable text of a status code (static storage).  Error reporting:
  * no counterpart in the paper. */
 const char* mtpt_status_string(int status);

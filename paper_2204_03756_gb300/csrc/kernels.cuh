@@ -59,7 +59,8 @@ __device__ __forceinline__ constexpr bool check(bool, uint32_t) { return true; }
 
 constexpr int kBlock = 256;
 constexpr int kScanThreads = 1024;
-constexpr int kScanTile = 4 * kScanThreads;   // cells per scan block
+constexpr int kScanPerThread = 16;                        // cells per scan thread
+constexpr int kScanTile = kScanPerThread * kScanThreads;  // cells per scan block
 
 struct Box {
     double lo[3], hi[3];
@@ -414,10 +415,14 @@ __global__ void k_iota(int n, uint32_t* __restrict__ id) {
 }
 
 // ---------------------------------------------------------------------------
-// Step 2a: exclusive prefix sum of the cell counts (two launches: per-tile
-// sums with the scan of the tile sums by the last tile, then per-tile scan
-// plus offset).  The
-// count array is padded with zeros to whole tiles, so start[n_cells] = n.
+// Step 2a: exclusive prefix sum of the cell counts in one launch.  Each block
+// scans a tile of 16 cells per thread, publishes the tile's total, and adds
+// the totals of all tiles before it, which every block publishes before it
+// waits on anyone (so no wait is chained behind another: the reduce-then-scan
+// pair of launches fused by single-pass publication, in the manner of D.
+// Merrill and M. Garland's decoupled look-back, NVIDIA technical report
+// NVR-2016-002).  The count array is padded with zeros to whole tiles, so
+// start[n_cells] = n.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
     __shared__ uint32_t warp_sums[32];
@@ -450,40 +455,87 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
     return excl;
 }
 
-// Per-tile sums of the counts; the last tile to finish (an atomic ticket,
-// nothing waits) then turns the tile sums into exclusive offsets in place,
-// resets the ticket, and advances the walk's step counter (device-resident,
-// so a captured graph of steps replays with the right counters) when
-// `advance` is set -- every kernel of the step that reads the counter has
-// completed by then.
+// A tile's published word: tag << 32 | total.  The tag is the launch's number
+// (ticket / tiles) mod 2^32 - 1, plus one: every launch rewrites every tile's
+// word, so a word still holding the previous launch's tag, or the zero the
+// host writes when the grid changes, is told apart from this launch's.
+constexpr unsigned long long kScanTagMod = 0xffffffffull;
+// Polls before a block stops waiting for an earlier tile's total and sums
+// that tile's counts itself (tens of milliseconds; the tiles it waits on took
+// their tickets first, so they are running: a safety net, not a path the
+// scan takes).
+constexpr int kScanWaitLimit = 1 << 17;
+__device__ unsigned long long g_scan_waits_given_up;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// state[0, ntiles) are the tiles' words, state[ntiles] the ticket (both zeroed
+// by the host whenever the grid changes).  The block of the last tile
+// advances the walk's step counter (device-resident, so a captured graph of
+// steps replays with the right counters) when `advance` is set: every kernel
+// of the step that reads it has completed.  A tile equal to `hold` never
+// publishes (a test hook: the tiles after it then run out of polls).
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_tiles(const uint4* __restrict__ count4, uint32_t* __restrict__ tile_sums, int ntiles,
-             unsigned int* __restrict__ ticket, unsigned long long* __restrict__ step_dev,
-             int advance) {
-    const uint4 v = count4[size_t(blockIdx.x) * kScanThreads + threadIdx.x];
-    uint32_t total;
-    block_exclusive_scan(v.x + v.y + v.z + v.w, &total);
-    __shared__ bool last;
+k_scan(const uint4* __restrict__ count4, uint4* __restrict__ start4,
+       unsigned long long* __restrict__ state, int ntiles,
+       unsigned long long* __restrict__ step_dev, int advance, int hold) {
+    constexpr int kVec = kScanPerThread / 4;
+    __shared__ uint32_t s_tile;
+    __shared__ unsigned long long s_tag;
     if (threadIdx.x == 0) {
-        tile_sums[blockIdx.x] = total;
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == unsigned(ntiles - 1);
+        // tiles in ticket order: a block only ever waits on blocks that started
+        const unsigned long long t = atomicAdd(state + ntiles, 1ull);
+        s_tile = uint32_t(t % unsigned(ntiles));
+        s_tag = (t / unsigned(ntiles)) % kScanTagMod + 1ull;
     }
     __syncthreads();
-    if (!last) return;
-    __threadfence();
-    uint32_t carry = 0;
-    for (int base = 0; base < ntiles; base += kScanThreads) {
-        const int t = base + threadIdx.x;
-        const uint32_t c = t < ntiles ? __ldcg(tile_sums + t) : 0u;   // other tiles' writes, via L2
-        uint32_t tot;
-        const uint32_t excl = block_exclusive_scan(c, &tot);
-        if (t < ntiles) tile_sums[t] = carry + excl;
-        carry += tot;
+    const uint32_t tile = s_tile;
+    const unsigned long long tag = s_tag;
+    // this thread's 16 consecutive cells
+    const size_t base = (size_t(tile) * kScanThreads + threadIdx.x) * kVec;
+    uint4 c[kVec];
+    uint32_t own = 0;
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+        c[k] = count4[base + k];
+        own += c[k].x + c[k].y + c[k].z + c[k].w;
     }
-    if (threadIdx.x == 0) {
-        *ticket = 0u;
-        if (advance) *step_dev += 1ull;
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan(own, &total);
+    if (threadIdx.x == 0 && int(tile) != hold) st_relaxed_u64(state + tile, (tag << 32) | total);
+    // the totals of every earlier tile, one word per thread at a time
+    uint32_t part = 0;
+    bool gave_up = false;
+    for (uint32_t p = threadIdx.x; p < tile; p += kScanThreads) {
+        unsigned long long w = ld_relaxed_u64(state + p);
+        for (int polls = 0; (w >> 32) != tag && polls < kScanWaitLimit; ++polls) {
+            __nanosleep(64);
+            w = ld_relaxed_u64(state + p);
+        }
+        if ((w >> 32) == tag) {
+            part += uint32_t(w);
+        } else {
+            gave_up = true;
+            const uint4* q = count4 + size_t(p) * (kScanTile / 4);
+            for (int k = 0; k < kScanTile / 4; ++k) part += q[k].x + q[k].y + q[k].z + q[k].w;
+        }
+    }
+    if (gave_up) atomicAdd(&g_scan_waits_given_up, 1ull);
+    uint32_t prefix;
+    block_exclusive_scan(part, &prefix);
+    if (advance && threadIdx.x == 0 && tile == uint32_t(ntiles - 1)) *step_dev += 1ull;
+    uint32_t e = prefix + excl;
+#pragma unroll
+    for (int k = 0; k < kVec; ++k) {
+        start4[base + k] = make_uint4(e, e + c[k].x, e + c[k].x + c[k].y, e + c[k].x + c[k].y + c[k].z);
+        e += c[k].x + c[k].y + c[k].z + c[k].w;
     }
 }
 
@@ -505,16 +557,6 @@ __global__ void k_fill_rid(int n, int nreal, const uint32_t* __restrict__ first,
         if (first[mid] <= uint32_t(i)) lo = mid; else hi = mid - 1;
     }
     rid[i] = uint32_t(lo);
-}
-
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_apply(const uint4* __restrict__ count4, const uint32_t* __restrict__ tile_offsets,
-             uint4* __restrict__ start4) {
-    const size_t k = size_t(blockIdx.x) * kScanThreads + threadIdx.x;
-    const uint4 v = count4[k];
-    uint32_t total;
-    const uint32_t excl = block_exclusive_scan(v.x + v.y + v.z + v.w, &total) + tile_offsets[blockIdx.x];
-    start4[k] = make_uint4(excl, excl + v.x, excl + v.x + v.y, excl + v.x + v.y + v.z);
 }
 
 // ---------------------------------------------------------------------------

@@ -213,7 +213,8 @@ struct mtpt_handle {
     DevBuf<uint32_t> id[2], rid[2];
     int cur = 0;
     // per-step scratch
-    DevBuf<uint32_t> key, perm, cell, count, start, tile_sums;
+    DevBuf<uint32_t> key, perm, cell, count, start;
+    DevBuf<unsigned long long> scan_state;   // scan tiles' words + the ticket
     DevBuf<double2> sortkey;          // (x, id | cell << 32) per slot (k_scatter)
     DevBuf<double2> sortrec;          // payload records per slot (k_scatter_rec)
     bool fresh = false;               // state loaded in input order, not yet sorted
@@ -694,10 +695,26 @@ int ensure_capacity(mtpt_handle* h, int64_t n, int64_t keep = 0) {
     return MTPT_OK;
 }
 
-// The cell-count scan's ticket: the word after the tile sums (zero between
-// scans; the last tile of each scan resets it).
-unsigned int* scan_ticket(mtpt_handle* h) {
-    return reinterpret_cast<unsigned int*>(h->tile_sums.p + h->n_cells_pad / kScanTile);
+// Zeroes the cell-count scan's tile words and ticket (a grid change moves
+// the ticket's launch numbering).
+int reset_scan(mtpt_handle* h, cudaStream_t st) {
+    const size_t words = size_t(h->n_cells_pad / kScanTile) + 1;
+    MTPT_CUDA_TRY(cudaMemsetAsync(h->scan_state.p, 0, words * sizeof(unsigned long long), st));
+    return MTPT_OK;
+}
+
+// Test hook of mtpt_debug_scan_hold: the scan tile that never publishes (-1: none).
+std::atomic<int> g_scan_hold{-1};
+
+// Exclusive prefix sum of the cell counts into start (one launch).
+int launch_scan(mtpt_handle* h, cudaStream_t st, bool advance) {
+    const int ntiles = int(h->n_cells_pad / kScanTile);
+    k_scan<<<ntiles, kScanThreads, 0, st>>>(reinterpret_cast<const uint4*>(h->count.p),
+                                            reinterpret_cast<uint4*>(h->start.p),
+                                            h->scan_state.p, ntiles, h->step_dev.p,
+                                            advance ? 1 : 0, g_scan_hold.load());
+    MTPT_CUDA_TRY(cudaGetLastError());
+    return MTPT_OK;
 }
 
 // The cell list's arrays for the current grid, grown all or nothing.
@@ -706,7 +723,7 @@ int ensure_cells(mtpt_handle* h) {
     GrowAll g;
     g.want(h->count, padded);
     g.want(h->start, padded);
-    g.want(h->tile_sums, padded / kScanTile + 1);   // + the scan's ticket
+    g.want(h->scan_state, padded / kScanTile + 1);   // + the scan's ticket
     g.want(h->corners, size_t(std::max(h->n_corners, 1)));
     if (h->nb_cap > 0) {
         const size_t slots = size_t(h->nb_cap) * size_t(h->cap);
@@ -719,8 +736,8 @@ int ensure_cells(mtpt_handle* h) {
     }
     if (g.grows()) drop_graph(h);
     MTPT_TRY(g.commit());
-    // the ticket sits after this grid's tile sums: zero it wherever that is now
-    MTPT_CUDA_TRY(cudaMemsetAsync(scan_ticket(h), 0, sizeof(unsigned int), h->stream));
+    // the scan's words for this grid's tiles
+    MTPT_TRY(reset_scan(h, h->stream));
     // counts start (and, after each scatter, end) at zero
     MTPT_CUDA_TRY(cudaMemsetAsync(h->count.p, 0, padded * sizeof(uint32_t), h->stream));
     return MTPT_OK;
@@ -989,18 +1006,9 @@ int launch_step(mtpt_handle* h, int flags) {
         return MTPT_OK;
     }
 
-    const int ntiles = int(h->n_cells_pad / kScanTile);
-    const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
     {
-        MTPT_TIMED(h, "scan_tiles");
-        k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p, ntiles,
-                                                      scan_ticket(h), h->step_dev.p,
-                                                      advance ? 1 : 0);
-    }
-    {
-        MTPT_TIMED(h, "scan_apply");
-        k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p,
-                                                      reinterpret_cast<uint4*>(h->start.p));
+        MTPT_TIMED(h, "scan");
+        MTPT_TRY(launch_scan(h, st, advance));
     }
     const bool split = h->precision == MTPT_FP32W;
     MTPT_TRY((launch_sort<DIM, View>(h, c, o, vin)));
@@ -1527,12 +1535,7 @@ int launch_emit(mtpt_handle* h, int64_t cap) {
     k_walk_key<DIM, View><<<blocks, kBlock, 0, h->stream>>>(n, stride, h->pos[c].p, h->id[c].p,
                                                             h->step_dev.p, 0, 1, vin, h->key.p,
                                                             h->count.p, h->status.p);
-    const int ntiles = int(h->n_cells_pad / kScanTile);
-    const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
-    k_scan_tiles<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p, ntiles,
-                                                         scan_ticket(h), h->step_dev.p, 0);
-    k_scan_apply<<<ntiles, kScanThreads, 0, h->stream>>>(count4, h->tile_sums.p,
-                                                         reinterpret_cast<uint4*>(h->start.p));
+    MTPT_TRY(launch_scan(h, h->stream, false));
     MTPT_TRY((launch_sort<DIM, View>(h, c, o, vin)));
     const View vs = make_view<View>(h, o, o);
     k_emit_pairs<DIM, View><<<blocks, kBlock, 0, h->stream>>>(
@@ -1632,13 +1635,7 @@ int launch_adjoint_step(mtpt_handle* h) {
         k_walk_key<DIM, SingleView, true><<<blocks, kBlock, 0, st>>>(
             n, stride, h->pos[c].p, h->id[c].p, h->step_dev.p, h->any_walk ? 1 : 0, 1, v,
             h->key.p, h->count.p, h->status.p, h->tan[c].p);
-    const int ntiles = int(h->n_cells_pad / kScanTile);
-    const uint4* count4 = reinterpret_cast<const uint4*>(h->count.p);
-    k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p, ntiles, scan_ticket(h),
-                                                  h->step_dev.p, 1);
-    k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(count4, h->tile_sums.p,
-                                                  reinterpret_cast<uint4*>(h->start.p));
-    MTPT_CUDA_TRY(cudaGetLastError());
+    MTPT_TRY(launch_scan(h, st, true));
     MTPT_TRY((launch_sort<DIM, SingleView>(h, c, o, v)));
     k_take_by_id<<<blocks, kBlock, 0, st>>>(n, h->id[o].p, h->lam_in.p, h->lam_s.p);
     const NbList<double2> adj_nb{h->adj_nb_j.p, h->adj_nb_k.p, h->adj_nb_count.p,
@@ -1792,7 +1789,7 @@ int mtpt_destroy(mtpt_handle* h) {
         h->rid[b].release();
     }
     h->key.release(); h->perm.release(); h->sortkey.release(); h->sortrec.release(); h->cell.release(); h->count.release();
-    h->start.release(); h->tile_sums.release(); h->rec.release(); h->corners.release();
+    h->start.release(); h->scan_state.release(); h->rec.release(); h->corners.release();
     h->corner_first.release(); h->id_first.release(); h->params_dev.release();
     h->r64.release(); h->ex.release(); h->out_tmp.release();
     h->exp_table.release();
@@ -2633,6 +2630,18 @@ int mtpt_debug_fail_alloc(int64_t nth, int64_t* remaining) {
     return MTPT_OK;
 }
 
+int mtpt_debug_scan_hold(int32_t tile, uint64_t* gave_up) {
+    if (tile < -1) return MTPT_ERR_INVALID_ARG;
+    g_scan_hold.store(tile);
+    if (gave_up) {
+        unsigned long long v = 0;
+        MTPT_CUDA_TRY(cudaDeviceSynchronize());
+        MTPT_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_scan_waits_given_up, sizeof(v)));
+        *gave_up = uint64_t(v);
+    }
+    return MTPT_OK;
+}
+
 const char* mtpt_status_string(int status) {
     switch (status) {
         case MTPT_OK: return "ok";
@@ -2685,7 +2694,8 @@ constexpr size_t kNoallocMaxCells = 4 * size_t(MTPT_NOALLOC_MAX_PARTICLES) + 64;
 constexpr size_t kNoallocMaxCellsPad = (kNoallocMaxCells + 1 + kScanTile - 1) / kScanTile * kScanTile;
 constexpr size_t kNoallocWorstBytes =
     kNoallocHeadBytes + 108 * size_t(MTPT_NOALLOC_MAX_PARTICLES) +
-    2 * sizeof(uint32_t) * kNoallocMaxCellsPad + sizeof(uint32_t) * (kNoallocMaxCellsPad / kScanTile) +
+    2 * sizeof(uint32_t) * kNoallocMaxCellsPad +
+    sizeof(unsigned long long) * (kNoallocMaxCellsPad / kScanTile + 1) +
     sizeof(float2) * (kNoallocMaxCells + 2) + 16 * 256;
 static_assert(kNoallocWorstBytes <= size_t(MTPT_NOALLOC_SCRATCH_BYTES),
               "the no-allocation scratch must hold the largest layout n allows");
@@ -2800,7 +2810,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     h.corners.p = cv.take<float2>(size_t(std::max(h.n_corners, 1)));
     h.count.p = cv.take<uint32_t>(cells_pad);
     h.start.p = cv.take<uint32_t>(cells_pad);
-    h.tile_sums.p = cv.take<uint32_t>(cells_pad / kScanTile + 1);   // + the scan's ticket
+    h.scan_state.p = cv.take<unsigned long long>(cells_pad / kScanTile + 1);   // + the ticket
     if (cv.overflow) return MTPT_ERR_TOO_LARGE;
 
     // The handle's buffer pairs: index 0 is the caller's state (positions are
@@ -2820,7 +2830,7 @@ extern "C" int mtpt_step_noalloc(const mtpt_params* params, int64_t n, uint64_t 
     // call's parameters, step and corner offsets, all from device-side work
     if (h.any_transfer) {
         MTPT_CUDA_TRY(cudaMemsetAsync(h.count.p, 0, cells_pad * sizeof(uint32_t), st));
-        MTPT_CUDA_TRY(cudaMemsetAsync(scan_ticket(&h), 0, sizeof(unsigned int), st));
+        MTPT_TRY(reset_scan(&h, st));
     }
     k_noalloc_init<<<1, 32, 0, st>>>(h.params[0], h.n_corners, (unsigned long long)step, head);
     MTPT_CUDA_TRY(cudaGetLastError());

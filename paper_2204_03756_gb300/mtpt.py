@@ -44,7 +44,7 @@ EXPORTED = [
     "mtpt_set_particles_async", "mtpt_get_masses_async", "mtpt_tiling_factors",
     "mtpt_set_tiling", "mtpt_set_particles_tile", "mtpt_tile_pack", "mtpt_tile_transfer",
     "mtpt_get_ids", "mtpt_debug_fail_alloc", "mtpt_set_reaction", "mtpt_set_masses_b",
-    "mtpt_get_masses_b",
+    "mtpt_get_masses_b", "mtpt_debug_scan_hold",
 ]
 
 
@@ -175,6 +175,7 @@ def load():
     lib.mtpt_tile_transfer.argtypes = [vp, ctypes.c_int64, vp]
     lib.mtpt_get_ids.argtypes = [vp, vp]
     lib.mtpt_debug_fail_alloc.argtypes = [ctypes.c_int64, P(ctypes.c_int64)]
+    lib.mtpt_debug_scan_hold.argtypes = [ctypes.c_int32, P(ctypes.c_uint64)]
     lib.mtpt_set_reaction.argtypes = [vp, ctypes.c_double]
     lib.mtpt_set_masses_b.argtypes = [vp, vp]
     lib.mtpt_get_masses_b.argtypes = [vp, vp]
@@ -546,6 +547,15 @@ def mtpt_debug_fail_alloc(nth: int) -> int:
     left = ctypes.c_int64()
     _check(load().mtpt_debug_fail_alloc(nth, ctypes.byref(left)), "mtpt_debug_fail_alloc")
     return int(left.value)
+
+
+def mtpt_debug_scan_hold(tile: int) -> int:
+    """Make the scans launched from now never publish scan tile `tile` (-1:
+    off); returns how many scan tiles on the current device have stopped
+    waiting for a tile before them so far (syncs the device)."""
+    gave_up = ctypes.c_uint64()
+    _check(load().mtpt_debug_scan_hold(tile, ctypes.byref(gave_up)), "mtpt_debug_scan_hold")
+    return int(gave_up.value)
 
 
 def mtpt_status_string(code: int) -> str:
