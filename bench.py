@@ -80,13 +80,13 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # Valid only for the library source it was measured on: a different hash of
 # the CUDA sources and the header reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "a39d572a062a"
+TRAFFIC_SOURCE_SHA1 = "130476ef0567"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (88933632 + 28392704) / 4e6,
-    "scatter": (81759232 + 33905920) / 4e6,
-    "gather": (152973056 + 139597824) / 4e6,
-    "rowsum_f32": (238000384 + 292577280) / 4e6,
-    "exchange_f32": (389569280 + 28445952) / 4e6,
+    "walk_key": (88936448 + 28718080) / 4e6,
+    "scatter": (81829888 + 34507776) / 4e6,
+    "gather": (152967680 + 139741184) / 4e6,
+    "rowsum_f32": (237576192 + 291190784) / 4e6,
+    "exchange_f32": (389564928 + 27121152) / 4e6,
 }
 
 
@@ -99,7 +99,7 @@ INSTR_PER_PARTICLE = {
     "scatter": 4125000 / 4e6,
     "gather": 38399201 / 4e6,
     "rowsum_f32": 183180239 / 4e6,
-    "exchange_f32": 44836827 / 4e6,
+    "exchange_f32": 49382305 / 4e6,
 }
 SMS, SCHEDULERS_PER_SM = 152, 4
 
@@ -108,13 +108,13 @@ SMS, SCHEDULERS_PER_SM = 152, 4
 # profiles/step_kernels_gaussian_2d_4M.md), reported beside the roofline
 # while the kernel source hash matches.
 BINDING = {
-    "exchange_f32": ("DRAM 55 % with long-scoreboard stalls on the list reads and the "
-                     "neighbour-record gathers; issue 40 % at 20 of 32 active lanes"),
-    "rowsum_f32": "instruction issue: 74 % of issue slots at 18 of 32 active lanes; DRAM 32 %",
+    "exchange_f32": ("DRAM 59 % with long-scoreboard stalls on the list reads and the "
+                     "neighbour-record gathers; issue 47 % at 21 of 32 active lanes"),
+    "rowsum_f32": "instruction issue: 72 % of issue slots at 18 of 32 active lanes; DRAM 31 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
     "gather": "DRAM 63 % (payload reads through the permutation, cell-ordered writes)",
-    "scatter": "DRAM 42 % at 11 % issue (slot atomics, permutation and sort-key stores)",
+    "scatter": "DRAM 43 % at 11 % issue (slot atomics, permutation and sort-key stores)",
     "walk_key": "binary64 pipe 80 % busy (x + sigma xi)",
 }
 
