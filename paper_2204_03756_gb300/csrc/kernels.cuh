@@ -11,7 +11,8 @@
 // Data layout (structure of arrays, `stride` = capacity >= n):
 //   pos[a * stride + s]  binary64 coordinates, particles in cell order
 //   mass[s], id[s]       binary64 mass, uint32 input index (keys the walk)
-//   cell[s]              linear cell index of particle s
+//   cell[s]              linear cell index of particle s (written and read in 3-d
+//                        only: below 3-d the record carries the cell coordinates)
 //   rec[s]               float4: binary32 offsets of the particle from its
 //                        cell's lower corner (x, y, z), and in .w the cell's
 //                        x index (a small integer, exact in binary32); in
@@ -671,7 +672,7 @@ k_gather(int n, int64_t stride, const uint32_t* __restrict__ perm,
     const uint32_t dst = b + rank;
     if (!check(dst < e, kChkGather)) return;
     id_out[dst] = my_id;
-    cell_out[dst] = c;
+    if constexpr (DIM == 3) cell_out[dst] = c;   // only the 3-d searches read it
     if constexpr (View::kBatch) rid_out[dst] = __ldg(v.rid_input + src);
     if (mass_b_out) mass_b_out[dst] = mass_b_in[src];   // second species (reactions)
     const RealParams& P = v.of_input(src);
@@ -779,7 +780,7 @@ k_gather_rec(int n, int64_t stride, const double2* __restrict__ recs,
     const uint32_t dst = b + rank;
     if (!check(dst < e, kChkGather)) return;
     id_out[dst] = my_id;
-    cell_out[dst] = c;
+    if constexpr (DIM == 3) cell_out[dst] = c;   // only the 3-d searches read it
     const RealParams& P = v.p;
     const double m = lane[DIM + 1];
     mass_out[dst] = m;
