@@ -68,6 +68,8 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
         "walk_key": 2 * x,                 # positions read + written
         "rowsum_f64": x + r, "rowsum_f32": x + r,          # positions in, r out
         "exchange_f64": x + 8 + r + 8, "exchange_f32": x + 8 + r + 8,  # X, M, r in; M out
+        # pass 2 and the next step's walk (walk-ahead): both kernels' bytes
+        "exchange_walk_f32": x + 8 + r + 8 + 2 * x,
         "gather": 2 * (x + 8 + 4),         # state copied into cell order
         "scatter": 8, "scan": 0,
     }

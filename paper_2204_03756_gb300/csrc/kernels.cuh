@@ -265,12 +265,66 @@ __device__ __forceinline__ uint32_t cell_of(const double* x, const Grid& g, bool
     return lin;
 }
 
-// With TANGENT, also carries the pathwise derivative of the positions with
-// respect to D (tan, same layout as pos): the walk adds dsigma/dD xi and a
-// mirror flips the sign, exactly as it maps the coordinate.  ADVECT compiles
-// the velocity term in (launched when some realisation has v != 0), so the
+// One particle's move of the random walk (Sec. 3: x + sigma xi per axis,
+// then the reflecting walls), in place on x[DIM].  With TANGENT, also
+// carries the pathwise derivative of the positions with respect to D (tan,
+// same layout as pos, particle i): the walk adds dsigma/dD xi and a mirror
+// flips the sign, exactly as it maps the coordinate.  ADVECT compiles the
+// velocity term in (launched when some realisation has v != 0), so the
 // binary64 pipe of a walk without one carries only its two operations per
 // axis.
+template <int DIM, bool TANGENT, bool ADVECT>
+__device__ __forceinline__ void walk_particle(const RealParams& P, uint32_t gen_id, uint64_t step,
+                                              double* x, double* __restrict__ tan, int64_t stride,
+                                              int i) {
+    const float4 z4 = normals4(P.seed, gen_id, step);
+    const float z[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const double za = f32_to_f64(z[a]);
+        // move sigma xi, or v dt + sigma xi with a velocity on this axis
+        double disp = __dmul_rn(P.sigma, za);
+        if constexpr (ADVECT) {
+            if (P.advect & (1u << a)) disp = __dadd_rn(P.vdt[a], disp);
+        }
+        double xv = __dadd_rn(x[a], disp);
+        const long long k = order_key(xv);
+        // strictly inside in the integer order => inside in binary64, no
+        // mirror needed; anything else (walls, outside, NaN) takes the
+        // binary64 reflection
+        if constexpr (TANGENT) {
+            double sign = 1.0;
+            if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
+                xv = reflect_parity(xv, P.box.lo[a], P.box.hi[a], &sign);
+            const double t = __fma_rn(P.dsigma_dD, za, tan[a * stride + i]);
+            tan[a * stride + i] = __dmul_rn(sign, t);
+        } else {
+            if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
+                xv = reflect(xv, P.box.lo[a], P.box.hi[a]);
+        }
+        x[a] = xv;
+    }
+}
+
+// The particle's cell (global index) into *key_out and its cell count; a
+// coordinate that is not finite sets the status bit.
+template <int DIM>
+__device__ __forceinline__ void key_particle(const RealParams& P, const double* x,
+                                             uint32_t* __restrict__ status,
+                                             uint32_t* __restrict__ key_out,
+                                             uint32_t* __restrict__ count) {
+    bool bad = false;
+    const uint32_t c = P.cell_base + cell_of<DIM>(x, P.g, &bad);
+    if (bad) atomicOr(status, kStatusNonFinite);
+    if (!check(c - P.cell_base < uint32_t(P.g.n[0]) * uint32_t(P.g.n[1]) * uint32_t(P.g.n[2]),
+               kChkCell))
+        return;
+    *key_out = c;
+    atomicAdd(&count[c], 1u);
+}
+
+// Step 1 over all particles, in place: the walk (with do_walk) and the
+// cell keys and counts of the counting sort (with do_key).
 template <int DIM, class View, bool TANGENT = false, bool ADVECT = false>
 __global__ void __launch_bounds__(kBlock)
 k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __restrict__ id,
@@ -286,45 +340,11 @@ k_walk_key(int n, int64_t stride, double* __restrict__ pos, const uint32_t* __re
 #pragma unroll
     for (int a = 0; a < DIM; ++a) x[a] = pos[a * stride + i];
     if (do_walk && P.walk) {
-        const float4 z4 = normals4(P.seed, id[i] - P.id_offset, step);
-        const float z[4] = {z4.x, z4.y, z4.z, z4.w};
+        walk_particle<DIM, TANGENT, ADVECT>(P, id[i] - P.id_offset, step, x, tan, stride, i);
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            const double za = f32_to_f64(z[a]);
-            // move sigma xi, or v dt + sigma xi with a velocity on this axis
-            double disp = __dmul_rn(P.sigma, za);
-            if constexpr (ADVECT) {
-                if (P.advect & (1u << a)) disp = __dadd_rn(P.vdt[a], disp);
-            }
-            double xv = __dadd_rn(x[a], disp);
-            const long long k = order_key(xv);
-            // strictly inside in the integer order => inside in binary64, no
-            // mirror needed; anything else (walls, outside, NaN) takes the
-            // binary64 reflection
-            if constexpr (TANGENT) {
-                double sign = 1.0;
-                if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
-                    xv = reflect_parity(xv, P.box.lo[a], P.box.hi[a], &sign);
-                const double t = __fma_rn(P.dsigma_dD, za, tan[a * stride + i]);
-                tan[a * stride + i] = __dmul_rn(sign, t);
-            } else {
-                if (!(k > P.box.lo_key[a] && k < P.box.hi_key[a]))
-                    xv = reflect(xv, P.box.lo[a], P.box.hi[a]);
-            }
-            x[a] = xv;
-            pos[a * stride + i] = xv;
-        }
+        for (int a = 0; a < DIM; ++a) pos[a * stride + i] = x[a];
     }
-    if (do_key) {
-        bool bad = false;
-        const uint32_t c = P.cell_base + cell_of<DIM>(x, P.g, &bad);
-        if (bad) atomicOr(status, kStatusNonFinite);
-        if (!check(c - P.cell_base < uint32_t(P.g.n[0]) * uint32_t(P.g.n[1]) * uint32_t(P.g.n[2]),
-                   kChkCell))
-            return;
-        key[i] = c;
-        atomicAdd(&count[c], 1u);
-    }
+    if (do_key) key_particle<DIM>(P, x, status, key + i, count);
 }
 
 // Check of host-loaded input in its device copy (positions dim x n with
@@ -1562,7 +1582,37 @@ __device__ __noinline__ float4 search_flux2(uint32_t s, int64_t stride,
 // accepted neighbours only, with pass 1's K), two entries at a time so two
 // gathers are in flight, or searches when it has none (no lists, or an
 // overflowing one).  Both add the same terms in the same order.
-template <int DIM, class View, int BLOCK, bool TWO = false>
+// The next step's walk done at the end of pass 2 (walk-ahead, for the steps of
+// one call that another step follows): particle s of this step's cell order
+// keeps its index, and its walked position, its id, cell key and cell count
+// go to the other buffer pair, which the next step's sort then reads as its
+// input order.  The walk is latency-tolerant arithmetic (binary64 pipe,
+// generator) and pass 2 waits on memory, so the two overlap in one kernel.
+struct WalkAhead {
+    const uint32_t* id_in;              // this step's ids (cell order)
+    double* pos_next;                   // walked positions, same index
+    uint32_t* id_next;                  // the ids, same index
+    uint32_t* key;                      // cell keys of the next sort
+    uint32_t* count;                    // cell counts of the next sort
+    uint32_t* status;
+    const unsigned long long* step_dev; // the walk's step counter, already advanced
+};
+
+template <int DIM>
+__device__ __forceinline__ void walk_ahead(const RealParams& P, int s, int64_t stride,
+                                           const double* __restrict__ pos, const WalkAhead& wa) {
+    double x[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = pos[a * stride + s];
+    const uint32_t idv = wa.id_in[s];
+    if (P.walk) walk_particle<DIM, false, false>(P, idv - P.id_offset, *wa.step_dev, x, nullptr, stride, s);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) wa.pos_next[a * stride + s] = x[a];
+    wa.id_next[s] = idv;
+    key_particle<DIM>(P, x, wa.status, wa.key + s, wa.count);
+}
+
+template <int DIM, class View, int BLOCK, bool TWO = false, bool WALK = false>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
@@ -1570,7 +1620,7 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
                const double* __restrict__ mass, double* __restrict__ mass_out, NbList32 nb,
                const float2* __restrict__ exb = nullptr, const double* __restrict__ mass_b = nullptr,
                double* __restrict__ mass_b_out = nullptr, double kp = 0.0, double dt = 0.0,
-               float kpdt_f = 0.0f) {
+               float kpdt_f = 0.0f, const WalkAhead wa = WalkAhead{}) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const RealParams& P = v.of_sorted(uint32_t(s));
@@ -1583,6 +1633,7 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
         } else {
             mass_out[s] = mass[s];
         }
+        if constexpr (WALK) walk_ahead<DIM>(P, s, stride, pos, wa);
         return;
     }
     const float4 xs = ex[s];
@@ -1648,6 +1699,7 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
     } else {
         mass_out[s] = __dadd_rn(mass[s], f.delta());
     }
+    if constexpr (WALK) walk_ahead<DIM>(P, s, stride, pos, wa);
 }
 
 // Test support: every accepted ordered pair j != s as (id_s, id_j).

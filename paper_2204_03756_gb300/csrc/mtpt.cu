@@ -273,6 +273,13 @@ struct mtpt_handle {
     cudaGraphExec_t graph = nullptr;
     int graph_cur = -1, graph_flags = -1;
     const double* graph_mass0 = nullptr;
+    // one walk-ahead middle step, per current buffer (a call's last step
+    // swaps the pairs, so consecutive calls alternate between the two)
+    cudaGraphExec_t graph_mid[2] = {nullptr, nullptr};
+    const double* graph_mid_mass0[2] = {nullptr, nullptr};
+    // the next step's walk has been done (by the previous step's pass 2):
+    // its positions, ids, keys and counts sit in buffer `cur`
+    bool walked_ahead = false;
     cudaStream_t capture_stream = nullptr;
     // split domain: this handle's tile and its pack / keep buffers
     TileGeom tile{};
@@ -352,6 +359,11 @@ void drop_graph(mtpt_handle* h) {
     h->graph_cur = -1;
     h->graph_flags = -1;
     h->graph_mass0 = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (h->graph_mid[k]) cudaGraphExecDestroy(h->graph_mid[k]);
+        h->graph_mid[k] = nullptr;
+        h->graph_mid_mass0[k] = nullptr;
+    }
 }
 
 int validate_params(const mtpt_params* p) {
@@ -894,7 +906,7 @@ void reaction_rate(const mtpt_handle* h, double* kp, double* dt) {
 
 template <int DIM, class View, int BLOCK>
 int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s, const View& vs,
-                     int o, int c) {
+                     int o, int c, bool walk_ahead) {
     const int blocks = int((n + BLOCK - 1) / BLOCK);
     const NbList32 nb{h->nb32_e.p, h->nb32_e.p ? h->nb32_cap : 0};
     {
@@ -913,6 +925,17 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
         k_exchange_f32<DIM, View, BLOCK, true><<<blocks, BLOCK, 0, h->stream>>>(
             n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
             h->mass[c].p, nb, h->exb.p, h->massb[o].p, h->massb[c].p, kp, dt, float(kp * dt));
+        MTPT_CUDA_TRY(cudaGetLastError());
+        return MTPT_OK;
+    }
+    if (walk_ahead) {
+        // pass 2 plus the next step's walk into buffer c (see WalkAhead)
+        const WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
+                           h->status.p, h->step_dev.p};
+        MTPT_TIMED(h, "exchange_walk_f32");
+        k_exchange_f32<DIM, View, BLOCK, false, true><<<blocks, BLOCK, 0, h->stream>>>(
+            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
+            h->mass[c].p, nb, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0f, wa);
         MTPT_CUDA_TRY(cudaGetLastError());
         return MTPT_OK;
     }
@@ -957,7 +980,9 @@ int launch_species_b(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
 // lives on the device and advances inside the step, so the same launches can
 // be captured once and replayed.
 template <int DIM, class View>
-int launch_step(mtpt_handle* h, int flags) {
+int launch_step(mtpt_handle* h, int flags, bool walk_ahead) {
+    // only the precision form's single-species pass 2 walks ahead
+    walk_ahead = walk_ahead && h->precision == MTPT_FP32W && !h->reactive && !View::kBatch;
     const int n = int(h->n);
     if (n == 0) {
         // an empty handle (e.g. a tile without particles) keeps its walk's
@@ -975,7 +1000,7 @@ int launch_step(mtpt_handle* h, int flags) {
     const bool transfer = (flags & MTPT_DO_TRANSFER) && h->any_transfer;
     const int c = h->cur, o = 1 - h->cur;
     const View vin = make_view<View>(h, c, c);
-    if (walk || transfer) {
+    if ((walk || transfer) && !h->walked_ahead) {
         MTPT_TIMED(h, "walk_key");
         if (h->tangent_on) {
             if (h->any_advect)
@@ -1029,52 +1054,69 @@ int launch_step(mtpt_handle* h, int flags) {
             h->mass[o].p, h->mass[c].p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap});
     } else {
         if (h->pair_block == 128) {
-            MTPT_TRY((launch_pairs_f32<DIM, View, 128>(h, n, stride, pos_s, vs, o, c)));
+            MTPT_TRY((launch_pairs_f32<DIM, View, 128>(h, n, stride, pos_s, vs, o, c, walk_ahead)));
         } else {
-            MTPT_TRY((launch_pairs_f32<DIM, View, 256>(h, n, stride, pos_s, vs, o, c)));
+            MTPT_TRY((launch_pairs_f32<DIM, View, 256>(h, n, stride, pos_s, vs, o, c, walk_ahead)));
         }
     }
     MTPT_CUDA_TRY(cudaGetLastError());
+    h->have_row_sums = true;
+    if (walk_ahead) {
+        // pass 2 wrote the masses and the next step's walked positions, ids,
+        // keys and counts into buffer c, which stays current
+        h->walked_ahead = true;
+        return MTPT_OK;
+    }
+    h->walked_ahead = false;
     if (h->reactive) MTPT_TRY((launch_species_b<DIM, View>(h, n, stride, pos_s, vs, o, c)));
     // positions and ids live in o; the updated masses were written into c's
     // buffer: swap the mass pair so both sit at index o, then make o current.
     std::swap(h->mass[c], h->mass[o]);
     if (h->reactive) std::swap(h->massb[c], h->massb[o]);
     h->cur = o;
-    h->have_row_sums = true;
     return MTPT_OK;
 }
 
-int dispatch_step(mtpt_handle* h, int flags) {
+int dispatch_step(mtpt_handle* h, int flags, bool walk_ahead = false) {
     if (h->batch) {
         switch (h->dim) {
-            case 1: return launch_step<1, BatchView>(h, flags);
-            case 2: return launch_step<2, BatchView>(h, flags);
-            default: return launch_step<3, BatchView>(h, flags);
+            case 1: return launch_step<1, BatchView>(h, flags, false);
+            case 2: return launch_step<2, BatchView>(h, flags, false);
+            default: return launch_step<3, BatchView>(h, flags, false);
         }
     }
     switch (h->dim) {
-        case 1: return launch_step<1, SingleView>(h, flags);
-        case 2: return launch_step<2, SingleView>(h, flags);
-        default: return launch_step<3, SingleView>(h, flags);
+        case 1: return launch_step<1, SingleView>(h, flags, walk_ahead);
+        case 2: return launch_step<2, SingleView>(h, flags, walk_ahead);
+        default: return launch_step<3, SingleView>(h, flags, walk_ahead);
     }
 }
 
-// Captures two consecutive steps (the buffer pairs swap every step, so two
-// steps return them to the starting arrangement) into an executable graph.
-int capture_two_steps(mtpt_handle* h, int flags) {
-    drop_graph(h);
+// Captures steps into an executable graph: two consecutive plain steps (the
+// buffer pairs swap every step, so two steps return them to the starting
+// arrangement), or, with walk_ahead, one middle step of a walk-ahead run
+// (entered with the walk done, it leaves it done for the next step and swaps
+// nothing).
+int capture_steps(mtpt_handle* h, int flags, bool walk_ahead) {
+    if (walk_ahead) {
+        cudaGraphExec_t& old = h->graph_mid[h->cur];
+        if (old) cudaGraphExecDestroy(old);
+        old = nullptr;
+    } else {
+        if (h->graph) cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     if (!h->capture_stream)
         MTPT_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     const cudaStream_t user = h->stream;
     const int cur0 = h->cur;
-    const bool rows0 = h->have_row_sums, fresh0 = h->fresh;
+    const bool rows0 = h->have_row_sums, fresh0 = h->fresh, ahead0 = h->walked_ahead;
     DevBuf<double> mass0 = h->mass[0], mass1 = h->mass[1];
     DevBuf<double> massb0 = h->massb[0], massb1 = h->massb[1];
     h->stream = h->capture_stream;
     MTPT_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = dispatch_step(h, flags);
-    if (rc == MTPT_OK) rc = dispatch_step(h, flags);
+    int rc = dispatch_step(h, flags, walk_ahead);
+    if (rc == MTPT_OK && !walk_ahead) rc = dispatch_step(h, flags);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
     // capture only recorded the launches: restore the host bookkeeping
@@ -1082,6 +1124,7 @@ int capture_two_steps(mtpt_handle* h, int flags) {
     h->cur = cur0;
     h->have_row_sums = rows0;
     h->fresh = fresh0;
+    h->walked_ahead = ahead0;
     h->mass[0] = mass0;
     h->mass[1] = mass1;
     h->massb[0] = massb0;
@@ -1098,6 +1141,11 @@ int capture_two_steps(mtpt_handle* h, int flags) {
         (void)cudaGetLastError();
         return MTPT_ERR_CUDA;
     }
+    if (walk_ahead) {
+        h->graph_mid[cur0] = exec;
+        h->graph_mid_mass0[cur0] = h->mass[0].p;
+        return MTPT_OK;
+    }
     h->graph = exec;
     h->graph_cur = cur0;
     h->graph_flags = flags;
@@ -1105,8 +1153,35 @@ int capture_two_steps(mtpt_handle* h, int flags) {
     return MTPT_OK;
 }
 
+// Whether a call's steps can run with walk-ahead (all but the last step's
+// pass 2 also walk the particles for the step after): the precision form of
+// one plain realisation (no batch, tile, reaction, advection or tangent),
+// stepping with both the walk and the transfer.
+bool walk_ahead_ok(const mtpt_handle* h, int flags) {
+    return h->precision == MTPT_FP32W && !h->batch && h->ntiles == 0 && !h->reactive &&
+           !h->tangent_on && !h->any_advect && h->any_walk && h->any_transfer && h->n > 0 &&
+           flags == (MTPT_DO_WALK | MTPT_DO_TRANSFER);
+}
+
 int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {
     const bool use_graph = nsteps >= kGraphMinSteps && !h->timing && !h->tangent_on && h->n > 0;
+    if (nsteps >= 2 && walk_ahead_ok(h, flags)) {
+        // first step (walk, and the record sort after a host load), the middle
+        // steps (replayed from a one-step graph), a last step without walk-ahead
+        MTPT_TRY(dispatch_step(h, flags, true));
+        int64_t middle = nsteps - 2;
+        if (use_graph && middle > 0) {
+            // (walk-ahead runs only with both flags, so the flags need no key)
+            const int k = h->cur;
+            if (!h->graph_mid[k] || h->graph_mid_mass0[k] != h->mass[0].p)
+                MTPT_TRY(capture_steps(h, flags, true));
+            for (; middle > 0; --middle) MTPT_CUDA_TRY(cudaGraphLaunch(h->graph_mid[k], h->stream));
+        }
+        for (; middle > 0; --middle) MTPT_TRY(dispatch_step(h, flags, true));
+        MTPT_TRY(dispatch_step(h, flags, false));
+        h->step += uint64_t(nsteps);
+        return MTPT_OK;
+    }
     int64_t done = 0;
     if (use_graph && h->fresh) {          // the record sort stays out of the graph
         MTPT_TRY(dispatch_step(h, flags));
@@ -1115,7 +1190,7 @@ int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {
     if (use_graph) {
         if (!h->graph || h->graph_cur != h->cur || h->graph_flags != flags ||
             h->graph_mass0 != h->mass[0].p)
-            MTPT_TRY(capture_two_steps(h, flags));
+            MTPT_TRY(capture_steps(h, flags, false));
         for (; done + 2 <= nsteps; done += 2) MTPT_CUDA_TRY(cudaGraphLaunch(h->graph, h->stream));
         // an even number of steps leaves the buffers where they started; a
         // transfer step leaves row sums behind
@@ -1285,6 +1360,7 @@ int load_particles_body(mtpt_handle* h, const int64_t* counts, const double* pos
     MTPT_CUDA_TRY(cudaMemsetAsync(h->pair_counter.p, 0, sizeof(unsigned long long), h->stream));
     MTPT_TRY(set_step_dev(h, 0));
     h->have_row_sums = false;
+    h->walked_ahead = false;
     h->have_particles = true;
     h->adj_ready = false;
     h->fresh = true;
@@ -1545,6 +1621,7 @@ int launch_emit(mtpt_handle* h, int64_t cap) {
     // the gathered copy in o is the same state in cell order: make it current
     h->cur = o;
     h->have_row_sums = false;
+    h->walked_ahead = false;
     return MTPT_OK;
 }
 
@@ -1743,6 +1820,7 @@ int mtpt_adjoint_backward(mtpt_handle* h, const double* gmass_dev, double* gmass
     if (rc == MTPT_OK) rc = snapshot(h, final_slot, false);
     if (rc == MTPT_OK) rc = set_step_dev(h, h->adj_step0 + uint64_t(T));
     h->have_row_sums = false;
+    h->walked_ahead = false;
     if (rc != MTPT_OK) return rc;
     MTPT_CUDA_TRY(cudaMemcpyAsync(gmass0_dev, h->lam_in.p, size_t(n) * sizeof(double),
                                   cudaMemcpyDeviceToDevice, h->stream));
@@ -1923,6 +2001,7 @@ int mtpt_set_particles_async(mtpt_handle* h, int64_t n, const double* pos, const
     h->cur = f;
     h->step = 0;
     h->have_row_sums = false;
+    h->walked_ahead = false;
     h->adj_ready = false;
     h->fresh = true;
     return MTPT_OK;
@@ -2097,6 +2176,7 @@ int mtpt_set_tuning(mtpt_handle* h, const mtpt_tuning* t) {
             return rc;
         }
         h->have_row_sums = false;
+        h->walked_ahead = false;
     }
     return MTPT_OK;
 }
@@ -2226,6 +2306,7 @@ int mtpt_autotune(mtpt_handle* h, int32_t trial_steps, mtpt_tuning* chosen) {
             rc2 = MTPT_ERR_CUDA;
     }
     h->have_row_sums = false;
+    h->walked_ahead = false;
     h->timing = timing0;
     free_snapshot();
     if (rc == MTPT_OK) rc = rc2;
@@ -2294,6 +2375,7 @@ int tile_install_t(mtpt_handle* h, int64_t n_keep, const double* keep, int64_t n
     h->fresh = true;
     h->have_particles = true;
     h->have_row_sums = false;
+    h->walked_ahead = false;
     return MTPT_OK;
 }
 
@@ -2377,6 +2459,7 @@ int tile_transfer_t(mtpt_handle* h, int64_t n_recv, const double* recv) {
     h->n = int64_t(natives);
     h->reals[0].n = h->n;
     h->have_row_sums = false;
+    h->walked_ahead = false;
     if (flag) return MTPT_ERR_INVALID_ARG;
     return status_code(h, st);
 }

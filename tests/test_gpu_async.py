@@ -172,7 +172,10 @@ def test_pipeline_on_a_user_stream_with_timing_and_a_one_member_batch():
             sim.masses_async(out)
         sim.sync()
         stats = mtpt.mtpt_timing_read(sim.h)
-        assert stats["load_input"][0] == 3 and stats["exchange_f32"][0] == 6
+        # six pass-2 launches: each call's first step walks ahead for its second
+        assert stats["load_input"][0] == 3
+        assert stats["exchange_f32"][0] == 3 and stats["exchange_walk_f32"][0] == 3
+        assert stats["walk_key"][0] == 3
     for r, o in zip(ref, outs):
         assert np.array_equal(o.numpy(), r)
     outs_b = [np.empty(w.n) for _ in ref]
