@@ -82,13 +82,14 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # Valid only for the library source it was measured on: a different hash of
 # the CUDA sources and the header reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "130476ef0567"
+TRAFFIC_SOURCE_SHA1 = "5a89093490da"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (88936448 + 28718080) / 4e6,
-    "scatter": (81829888 + 34507776) / 4e6,
-    "gather": (152967680 + 139741184) / 4e6,
-    "rowsum_f32": (237576192 + 291190784) / 4e6,
-    "exchange_f32": (389564928 + 27121152) / 4e6,
+    "walk_key": (88931584 + 31843840) / 4e6,
+    "scatter": (81828096 + 35095808) / 4e6,
+    "gather": (152936448 + 124399360) / 4e6,
+    "rowsum_f32": (238032384 + 292266752) / 4e6,
+    "exchange_f32": (389628160 + 27271936) / 4e6,
+    "exchange_walk_f32": (478562816 + 117270528) / 4e6,
 }
 
 
@@ -97,11 +98,12 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 # issue rate, against the issue peak of 4 warp instructions per clock per SM
 # (one per scheduler).
 INSTR_PER_PARTICLE = {
-    "walk_key": 43893462 / 4e6,
+    "walk_key": 43906125 / 4e6,
     "scatter": 4125000 / 4e6,
-    "gather": 38399201 / 4e6,
+    "gather": 38024199 / 4e6,
     "rowsum_f32": 183180239 / 4e6,
-    "exchange_f32": 49382305 / 4e6,
+    "exchange_f32": 49384119 / 4e6,
+    "exchange_walk_f32": 92400743 / 4e6,
 }
 SMS, SCHEDULERS_PER_SM = 152, 4
 
@@ -110,13 +112,15 @@ SMS, SCHEDULERS_PER_SM = 152, 4
 # profiles/step_kernels_gaussian_2d_4M.md), reported beside the roofline
 # while the kernel source hash matches.
 BINDING = {
-    "exchange_f32": ("DRAM 59 % with long-scoreboard stalls on the list reads and the "
-                     "neighbour-record gathers; issue 47 % at 21 of 32 active lanes"),
-    "rowsum_f32": "instruction issue: 72 % of issue slots at 18 of 32 active lanes; DRAM 31 %",
+    "exchange_f32": ("DRAM 58 % with long-scoreboard stalls on the list reads and the "
+                     "neighbour-record gathers; issue 46 % at 21 of 32 active lanes"),
+    "exchange_walk_f32": ("DRAM 58 % and binary64 pipe 51 % (pass 2's update and the next "
+                          "step's x + sigma xi); issue 59 % at 26 of 32 active lanes"),
+    "rowsum_f32": "instruction issue: 71 % of issue slots at 18 of 32 active lanes; DRAM 31 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
-    "gather": "DRAM 63 % (payload reads through the permutation, cell-ordered writes)",
-    "scatter": "DRAM 43 % at 11 % issue (slot atomics, permutation and sort-key stores)",
+    "gather": "DRAM 62 % (payload reads through the permutation, cell-ordered writes)",
+    "scatter": "DRAM 42 % at 10 % issue (slot atomics, permutation and sort-key stores)",
     "walk_key": "binary64 pipe 80 % busy (x + sigma xi)",
 }
 
