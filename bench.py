@@ -82,7 +82,7 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # Valid only for the library source it was measured on: a different hash of
 # the CUDA sources and the header reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "5a89093490da"
+TRAFFIC_SOURCE_SHA1 = "01a316170fd5"   # 5a89093490da + header comments
 TRAFFIC_BYTES_PER_PARTICLE = {
     "walk_key": (88931584 + 31843840) / 4e6,
     "scatter": (81828096 + 35095808) / 4e6,

@@ -202,9 +202,12 @@ int mtpt_get_realisation_info(mtpt_handle* h, int32_t k, mtpt_info* out);
  * walls, every pair within psi of Eq. "cutoff", the simplified kernel that
  * follows Eq. "kernel", the normalisation W_ij = K_ij / (1/2 (column sum +
  * row sum)), and M_i(t + dt) = M_i(t) + delta_i with delta_i of
- * Eq. "changemass", all M_j taken at time t.  Enqueued on the stream; returns the launch status.  Calls of
- * four or more steps capture two steps as a CUDA graph on first use and
- * replay it (same results as step-by-step launches). */
+ * Eq. "changemass", all M_j taken at time t.  Enqueued on the stream;
+ * returns the launch status.  Calls of four or more steps replay a CUDA graph
+ * captured on first use; in the precision form of a plain handle, the mass
+ * transfer of every step of a call but its last also walks the particles for
+ * the next step (one kernel instead of two).  Either way the results equal
+ * step-by-step launches bit for bit. */
 int mtpt_step(mtpt_handle* h, int64_t nsteps);
 
 /* As mtpt_step with a subset of the step: flags is a combination of
