@@ -1339,14 +1339,47 @@ k_rowsum_f64(int n, int64_t stride, const double* __restrict__ pos, const float4
     add_pair_count(counted ? cnt : 0u, pair_counter);
 }
 
+// The next step's walk done at the end of pass 2 (walk-ahead, for the steps of
+// one call that another step follows): particle s of this step's cell order
+// keeps its index, and its walked position, its id, cell key and cell count
+// go to the other buffer pair, which the next step's sort then reads as its
+// input order.  The walk is latency-tolerant arithmetic (binary64 pipe,
+// generator) and pass 2 waits on memory, so the two overlap in one kernel.
+struct WalkAhead {
+    const uint32_t* id_in;              // this step's ids (cell order)
+    double* pos_next;                   // walked positions, same index
+    uint32_t* id_next;                  // the ids, same index
+    uint32_t* key;                      // cell keys of the next sort
+    uint32_t* count;                    // cell counts of the next sort
+    uint32_t* status;
+    const unsigned long long* step_dev; // the walk's step counter, already advanced
+};
+
+// WALK selects the walk-ahead instance of a pass-2 kernel: 0 none, 1 the
+// walk, 2 the walk with the advection term.
+template <int DIM, int WALK>
+__device__ __forceinline__ void walk_ahead(const RealParams& P, int s, int64_t stride,
+                                           const double* __restrict__ pos, const WalkAhead& wa) {
+    double x[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = pos[a * stride + s];
+    const uint32_t idv = wa.id_in[s];
+    if (P.walk)
+        walk_particle<DIM, false, WALK == 2>(P, idv - P.id_offset, *wa.step_dev, x, nullptr, stride, s);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) wa.pos_next[a * stride + s] = x[a];
+    wa.id_next[s] = idv;
+    key_particle<DIM>(P, x, wa.status, wa.key + s, wa.count);
+}
+
 // Pass 2, binary64 form: M'_s = M_s + beta sum_j (M_j - M_s) 2 K_sj / (r_s + r_j).
-template <int DIM, class View>
+template <int DIM, class View, int WALK = 0>
 __global__ void __launch_bounds__(kBlock)
 k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
                const double* __restrict__ exp_table, const __grid_constant__ View v,
                const double* __restrict__ r, const double* __restrict__ mass,
-               double* __restrict__ mass_out, NbList64 nb) {
+               double* __restrict__ mass_out, NbList64 nb, const WalkAhead wa = WalkAhead{}) {
     __shared__ double table[kExpTable];
     __shared__ SegShared<kWarpsPerBlock, double, false> seg;
     for (int t = threadIdx.x; t < kExpTable; t += blockDim.x) table[t] = exp_table[t];
@@ -1378,6 +1411,9 @@ k_exchange_f64(int n, int64_t stride, const double* __restrict__ pos, const floa
             [&](double f) { acc = __dadd_rn(acc, f); });
     }
     if (s < n) mass_out[s] = valid ? __dadd_rn(mass[s], __dmul_rn(P.pp.beta, acc)) : mass[s];
+    if constexpr (WALK > 0) {
+        if (s < n) walk_ahead<DIM, WALK>(P, s, stride, pos, wa);
+    }
 }
 
 // Pass 1, precision form: binary32 kernel exp2(-a log2(e) d2f) with the
@@ -1582,37 +1618,7 @@ __device__ __noinline__ float4 search_flux2(uint32_t s, int64_t stride,
 // accepted neighbours only, with pass 1's K), two entries at a time so two
 // gathers are in flight, or searches when it has none (no lists, or an
 // overflowing one).  Both add the same terms in the same order.
-// The next step's walk done at the end of pass 2 (walk-ahead, for the steps of
-// one call that another step follows): particle s of this step's cell order
-// keeps its index, and its walked position, its id, cell key and cell count
-// go to the other buffer pair, which the next step's sort then reads as its
-// input order.  The walk is latency-tolerant arithmetic (binary64 pipe,
-// generator) and pass 2 waits on memory, so the two overlap in one kernel.
-struct WalkAhead {
-    const uint32_t* id_in;              // this step's ids (cell order)
-    double* pos_next;                   // walked positions, same index
-    uint32_t* id_next;                  // the ids, same index
-    uint32_t* key;                      // cell keys of the next sort
-    uint32_t* count;                    // cell counts of the next sort
-    uint32_t* status;
-    const unsigned long long* step_dev; // the walk's step counter, already advanced
-};
-
-template <int DIM>
-__device__ __forceinline__ void walk_ahead(const RealParams& P, int s, int64_t stride,
-                                           const double* __restrict__ pos, const WalkAhead& wa) {
-    double x[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) x[a] = pos[a * stride + s];
-    const uint32_t idv = wa.id_in[s];
-    if (P.walk) walk_particle<DIM, false, false>(P, idv - P.id_offset, *wa.step_dev, x, nullptr, stride, s);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) wa.pos_next[a * stride + s] = x[a];
-    wa.id_next[s] = idv;
-    key_particle<DIM>(P, x, wa.status, wa.key + s, wa.count);
-}
-
-template <int DIM, class View, int BLOCK, bool TWO = false, bool WALK = false>
+template <int DIM, class View, int BLOCK, bool TWO = false, int WALK = 0>
 __global__ void __launch_bounds__(BLOCK, 2048 / BLOCK)
 k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const float4* __restrict__ rec,
                const uint32_t* __restrict__ cell, const uint32_t* __restrict__ start,
@@ -1633,7 +1639,7 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
         } else {
             mass_out[s] = mass[s];
         }
-        if constexpr (WALK) walk_ahead<DIM>(P, s, stride, pos, wa);
+        if constexpr (WALK > 0) walk_ahead<DIM, WALK>(P, s, stride, pos, wa);
         return;
     }
     const float4 xs = ex[s];
@@ -1699,7 +1705,7 @@ k_exchange_f32(int n, int64_t stride, const double* __restrict__ pos, const floa
     } else {
         mass_out[s] = __dadd_rn(mass[s], f.delta());
     }
-    if constexpr (WALK) walk_ahead<DIM>(P, s, stride, pos, wa);
+    if constexpr (WALK > 0) walk_ahead<DIM, WALK>(P, s, stride, pos, wa);
 }
 
 // Test support: every accepted ordered pair j != s as (id_s, id_j).

@@ -933,9 +933,14 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
         const WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
                            h->status.p, h->step_dev.p};
         MTPT_TIMED(h, "exchange_walk_f32");
-        k_exchange_f32<DIM, View, BLOCK, false, true><<<blocks, BLOCK, 0, h->stream>>>(
-            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
-            h->mass[c].p, nb, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0f, wa);
+        if (h->any_advect)
+            k_exchange_f32<DIM, View, BLOCK, false, 2><<<blocks, BLOCK, 0, h->stream>>>(
+                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
+                h->mass[c].p, nb, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0f, wa);
+        else
+            k_exchange_f32<DIM, View, BLOCK, false, 1><<<blocks, BLOCK, 0, h->stream>>>(
+                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
+                h->mass[c].p, nb, nullptr, nullptr, nullptr, 0.0, 0.0, 0.0f, wa);
         MTPT_CUDA_TRY(cudaGetLastError());
         return MTPT_OK;
     }
@@ -981,8 +986,8 @@ int launch_species_b(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
 // be captured once and replayed.
 template <int DIM, class View>
 int launch_step(mtpt_handle* h, int flags, bool walk_ahead) {
-    // only the precision form's single-species pass 2 walks ahead
-    walk_ahead = walk_ahead && h->precision == MTPT_FP32W && !h->reactive && !View::kBatch;
+    // a single species of one plain realisation walks ahead
+    walk_ahead = walk_ahead && !h->reactive && !View::kBatch;
     const int n = int(h->n);
     if (n == 0) {
         // an empty handle (e.g. a tile without particles) keeps its walk's
@@ -1048,10 +1053,26 @@ int launch_step(mtpt_handle* h, int flags, bool walk_ahead) {
                 h->pair_counter.p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap},
                 h->ntiles > 0 ? h->id[o].p : nullptr);
         }
-        MTPT_TIMED(h, "exchange_f64");
-        k_exchange_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
-            n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
-            h->mass[o].p, h->mass[c].p, NbList64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap});
+        const NbList64 nb64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap};
+        if (walk_ahead) {
+            // pass 2 plus the next step's walk into buffer c (see WalkAhead)
+            const WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
+                               h->status.p, h->step_dev.p};
+            MTPT_TIMED(h, "exchange_walk_f64");
+            if (h->any_advect)
+                k_exchange_f64<DIM, View, 2><<<blocks, kBlock, 0, st>>>(
+                    n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs,
+                    h->r64.p, h->mass[o].p, h->mass[c].p, nb64, wa);
+            else
+                k_exchange_f64<DIM, View, 1><<<blocks, kBlock, 0, st>>>(
+                    n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs,
+                    h->r64.p, h->mass[o].p, h->mass[c].p, nb64, wa);
+        } else {
+            MTPT_TIMED(h, "exchange_f64");
+            k_exchange_f64<DIM, View><<<blocks, kBlock, 0, st>>>(
+                n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, h->exp_table.p, vs, h->r64.p,
+                h->mass[o].p, h->mass[c].p, nb64);
+        }
     } else {
         if (h->pair_block == 128) {
             MTPT_TRY((launch_pairs_f32<DIM, View, 128>(h, n, stride, pos_s, vs, o, c, walk_ahead)));
@@ -1154,13 +1175,12 @@ int capture_steps(mtpt_handle* h, int flags, bool walk_ahead) {
 }
 
 // Whether a call's steps can run with walk-ahead (all but the last step's
-// pass 2 also walk the particles for the step after): the precision form of
-// one plain realisation (no batch, tile, reaction, advection or tangent),
-// stepping with both the walk and the transfer.
+// pass 2 also walk the particles for the step after): one plain realisation
+// (no batch, tile, reaction or tangent) stepping with both the walk and the
+// transfer.
 bool walk_ahead_ok(const mtpt_handle* h, int flags) {
-    return h->precision == MTPT_FP32W && !h->batch && h->ntiles == 0 && !h->reactive &&
-           !h->tangent_on && !h->any_advect && h->any_walk && h->any_transfer && h->n > 0 &&
-           flags == (MTPT_DO_WALK | MTPT_DO_TRANSFER);
+    return !h->batch && h->ntiles == 0 && !h->reactive && !h->tangent_on && h->any_walk &&
+           h->any_transfer && h->n > 0 && flags == (MTPT_DO_WALK | MTPT_DO_TRANSFER);
 }
 
 int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {

@@ -1,6 +1,7 @@
-"""Walk-ahead in multi-step calls of the precision form: the pass 2 of every
-step but a call's last also does the next step's walk (the walk of Sec. 3,
-then the next counting sort's keys), writing into the other buffer pair.  A
+"""Walk-ahead in multi-step calls of a plain handle: the pass 2 of every step
+but a call's last also does the next step's walk (the walk of Sec. 3, with
+the advection term of Sec. 8 when there is a velocity, then the next
+counting sort's keys), writing into the other buffer pair, in both forms.  A
 call of n steps must equal n calls of one step, which never walk ahead, bit
 for bit -- positions, masses, pair count and step counter -- through the
 first step's record sort after a host load, the one-step graph replayed for
@@ -38,18 +39,25 @@ def _same(a, b):
             and a[3] == b[3])
 
 
-def _case(dim, n, L, seed=21):
+def _case(dim, n, L, seed=21, form=FP32W, v=None):
     rng = np.random.default_rng(100 + dim)
     pos = rng.uniform(0.0, L, size=(dim, n))
     mass = (pos[0] < L / 2).astype(np.float64) + 0.25 * rng.uniform(size=n)
+    extra = {} if v is None else {"v": v}
     p = mtpt.Params(dim=dim, D=1.0, kappa=0.5, dt=0.1, lo=(0.0,) * dim, hi=(L,) * dim,
-                    seed=seed, precision=FP32W)
+                    seed=seed, precision=form, **extra)
     return p, pos, mass
 
 
-@pytest.mark.parametrize("dim,n,L", [(1, 3000, 1500.0), (2, 40000, 150.0), (3, 30000, 30.0)])
-def test_calls_of_many_steps_equal_single_steps(dim, n, L):
-    p, pos, mass = _case(dim, n, L)
+CASES = [(1, 3000, 1500.0, FP32W, None), (2, 40000, 150.0, FP32W, None),
+         (3, 30000, 30.0, FP32W, None), (2, 30000, 130.0, mtpt.MTPT_FP64, None),
+         (3, 20000, 26.0, mtpt.MTPT_FP64, None), (2, 30000, 130.0, FP32W, (0.7, -0.4)),
+         (2, 20000, 110.0, mtpt.MTPT_FP64, (0.0, 1.3))]
+
+
+@pytest.mark.parametrize("dim,n,L,form,v", CASES)
+def test_calls_of_many_steps_equal_single_steps(dim, n, L, form, v):
+    p, pos, mass = _case(dim, n, L, form=form, v=v)
     with mtpt.Simulation(p, pos, mass) as a, mtpt.Simulation(p, pos, mass) as b:
         for k in CALLS:
             a.step(k)
