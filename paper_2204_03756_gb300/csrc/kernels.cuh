@@ -1353,6 +1353,8 @@ struct WalkAhead {
     uint32_t* count;                    // cell counts of the next sort
     uint32_t* status;
     const unsigned long long* step_dev; // the walk's step counter, already advanced
+    const uint32_t* rid_in = nullptr;   // a batch: realisation of each particle (cell order)
+    uint32_t* rid_next = nullptr;       // a batch: the same, same index
 };
 
 // WALK selects the walk-ahead instance of a pass-2 kernel: 0 none, 1 the
@@ -1369,6 +1371,7 @@ __device__ __forceinline__ void walk_ahead(const RealParams& P, int s, int64_t s
 #pragma unroll
     for (int a = 0; a < DIM; ++a) wa.pos_next[a * stride + s] = x[a];
     wa.id_next[s] = idv;
+    if (wa.rid_next) wa.rid_next[s] = wa.rid_in[s];
     key_particle<DIM>(P, x, wa.status, wa.key + s, wa.count);
 }
 

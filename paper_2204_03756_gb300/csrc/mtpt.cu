@@ -930,8 +930,12 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
     }
     if (walk_ahead) {
         // pass 2 plus the next step's walk into buffer c (see WalkAhead)
-        const WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
-                           h->status.p, h->step_dev.p};
+        WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
+                     h->status.p, h->step_dev.p};
+        if (View::kBatch) {
+            wa.rid_in = h->rid[o].p;
+            wa.rid_next = h->rid[c].p;
+        }
         MTPT_TIMED(h, "exchange_walk_f32");
         if (h->any_advect)
             k_exchange_f32<DIM, View, BLOCK, false, 2><<<blocks, BLOCK, 0, h->stream>>>(
@@ -986,8 +990,8 @@ int launch_species_b(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
 // be captured once and replayed.
 template <int DIM, class View>
 int launch_step(mtpt_handle* h, int flags, bool walk_ahead) {
-    // a single species of one plain realisation walks ahead
-    walk_ahead = walk_ahead && !h->reactive && !View::kBatch;
+    // a single species walks ahead
+    walk_ahead = walk_ahead && !h->reactive;
     const int n = int(h->n);
     if (n == 0) {
         // an empty handle (e.g. a tile without particles) keeps its walk's
@@ -1056,8 +1060,12 @@ int launch_step(mtpt_handle* h, int flags, bool walk_ahead) {
         const NbList64 nb64{h->nb_j.p, h->nb_k.p, h->nb_count.p, h->nb_cap};
         if (walk_ahead) {
             // pass 2 plus the next step's walk into buffer c (see WalkAhead)
-            const WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
-                               h->status.p, h->step_dev.p};
+            WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
+                         h->status.p, h->step_dev.p};
+            if (View::kBatch) {
+                wa.rid_in = h->rid[o].p;
+                wa.rid_next = h->rid[c].p;
+            }
             MTPT_TIMED(h, "exchange_walk_f64");
             if (h->any_advect)
                 k_exchange_f64<DIM, View, 2><<<blocks, kBlock, 0, st>>>(
@@ -1101,9 +1109,9 @@ int launch_step(mtpt_handle* h, int flags, bool walk_ahead) {
 int dispatch_step(mtpt_handle* h, int flags, bool walk_ahead = false) {
     if (h->batch) {
         switch (h->dim) {
-            case 1: return launch_step<1, BatchView>(h, flags, false);
-            case 2: return launch_step<2, BatchView>(h, flags, false);
-            default: return launch_step<3, BatchView>(h, flags, false);
+            case 1: return launch_step<1, BatchView>(h, flags, walk_ahead);
+            case 2: return launch_step<2, BatchView>(h, flags, walk_ahead);
+            default: return launch_step<3, BatchView>(h, flags, walk_ahead);
         }
     }
     switch (h->dim) {
@@ -1175,12 +1183,12 @@ int capture_steps(mtpt_handle* h, int flags, bool walk_ahead) {
 }
 
 // Whether a call's steps can run with walk-ahead (all but the last step's
-// pass 2 also walk the particles for the step after): one plain realisation
-// (no batch, tile, reaction or tangent) stepping with both the walk and the
-// transfer.
+// pass 2 also walk the particles for the step after): a plain handle or a
+// batch (not a tile, a reaction or the adjoint's tangent run) stepping with
+// both the walk and the transfer.
 bool walk_ahead_ok(const mtpt_handle* h, int flags) {
-    return !h->batch && h->ntiles == 0 && !h->reactive && !h->tangent_on && h->any_walk &&
-           h->any_transfer && h->n > 0 && flags == (MTPT_DO_WALK | MTPT_DO_TRANSFER);
+    return h->ntiles == 0 && !h->reactive && !h->tangent_on && h->any_walk && h->any_transfer &&
+           h->n > 0 && flags == (MTPT_DO_WALK | MTPT_DO_TRANSFER);
 }
 
 int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {

@@ -1,13 +1,13 @@
-"""Walk-ahead in multi-step calls of a plain handle: the pass 2 of every step
-but a call's last also does the next step's walk (the walk of Sec. 3, with
-the advection term of Sec. 8 when there is a velocity, then the next
-counting sort's keys), writing into the other buffer pair, in both forms.  A
-call of n steps must equal n calls of one step, which never walk ahead, bit
-for bit -- positions, masses, pair count and step counter -- through the
-first step's record sort after a host load, the one-step graph replayed for
-the middle steps (one per buffer parity, so consecutive calls alternate),
-reloads between calls and list overflow, in 1-, 2- and 3-d; and the oracle
-still agrees."""
+"""Walk-ahead in multi-step calls of a plain handle or a batch: the pass 2 of
+every step but a call's last also does the next step's walk (the walk of
+Sec. 3, with the advection term of Sec. 8 when there is a velocity, then the
+next counting sort's keys), writing into the other buffer pair, in both
+forms.  A call of n steps must equal n calls of one step, which never walk
+ahead, bit for bit -- positions, masses, pair count and step counter --
+through the first step's record sort after a host load, the one-step graph
+replayed for the middle steps (one per buffer parity, so consecutive calls
+alternate), reloads between calls, list overflow and batches, in 1-, 2- and
+3-d; and the oracle still agrees."""
 import numpy as np
 import pytest
 
@@ -111,3 +111,22 @@ def test_pipelined_loads_between_walk_ahead_calls():
             for _ in range(6):
                 b.step(1)
             assert _same(_state(a), _state(b))
+
+
+@pytest.mark.parametrize("form", [FP32W, mtpt.MTPT_FP64])
+def test_batch_calls_of_many_steps_equal_single_steps(form):
+    from paper_2204_03756_gb300 import workloads
+    from gpu_helpers import params_of
+    e = workloads.ensemble(nreal=4, n_min=400, n_max=8000, steps=10)
+    params = [params_of(w, precision=form, kappa=kappa)
+              for w, kappa in zip(e.members, (0.5, 0.2, 0.5, 1.0))]
+    pos, mass = workloads.ensemble_state(e)
+    with mtpt.Batch(params, e.counts, pos, mass) as a, \
+            mtpt.Batch(params, e.counts, pos, mass) as b:
+        for k in (5, 2, 8, 1, 6):
+            a.step(k)
+            for _ in range(k):
+                b.step(1)
+            assert np.array_equal(a.positions(), b.positions()), k
+            assert np.array_equal(a.masses(), b.masses()), k
+            assert a.info()["pair_count"] == b.info()["pair_count"], k
