@@ -918,9 +918,30 @@ int launch_pairs_f32(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
     }
     if (h->reactive) {
         // species B's split, then one pass 2 for both species and the reaction
+        // (a reaction runs on a plain handle only: batches refuse it)
         k_split_mass<<<grid_for(n), kBlock, 0, h->stream>>>(n, h->massb[o].p, h->exb.p);
         double kp, dt;
         reaction_rate(h, &kp, &dt);
+        if constexpr (!View::kBatch) {
+            if (walk_ahead) {
+                // and the next step's walk into buffer c (see WalkAhead)
+                const WalkAhead wa{h->id[o].p, h->pos[c].p, h->id[c].p, h->key.p, h->count.p,
+                                   h->status.p, h->step_dev.p};
+                MTPT_TIMED(h, "exchange_walk_f32");
+                if (h->any_advect)
+                    k_exchange_f32<DIM, View, BLOCK, true, 2><<<blocks, BLOCK, 0, h->stream>>>(
+                        n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p,
+                        h->mass[o].p, h->mass[c].p, nb, h->exb.p, h->massb[o].p, h->massb[c].p,
+                        kp, dt, float(kp * dt), wa);
+                else
+                    k_exchange_f32<DIM, View, BLOCK, true, 1><<<blocks, BLOCK, 0, h->stream>>>(
+                        n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p,
+                        h->mass[o].p, h->mass[c].p, nb, h->exb.p, h->massb[o].p, h->massb[c].p,
+                        kp, dt, float(kp * dt), wa);
+                MTPT_CUDA_TRY(cudaGetLastError());
+                return MTPT_OK;
+            }
+        }
         MTPT_TIMED(h, "exchange_f32");
         k_exchange_f32<DIM, View, BLOCK, true><<<blocks, BLOCK, 0, h->stream>>>(
             n, stride, pos_s, h->rec.p, h->cell.p, h->start.p, vs, h->ex.p, h->mass[o].p,
@@ -990,8 +1011,9 @@ int launch_species_b(mtpt_handle* h, int n, int64_t stride, const double* pos_s,
 // be captured once and replayed.
 template <int DIM, class View>
 int launch_step(mtpt_handle* h, int flags, bool walk_ahead) {
-    // a single species walks ahead
-    walk_ahead = walk_ahead && !h->reactive;
+    // a reaction walks ahead in the precision form, whose pass 2 does both
+    // species and the reaction (the binary64 form runs species B after it)
+    walk_ahead = walk_ahead && (!h->reactive || (h->precision == MTPT_FP32W && !View::kBatch));
     const int n = int(h->n);
     if (n == 0) {
         // an empty handle (e.g. a tile without particles) keeps its walk's
@@ -1184,11 +1206,12 @@ int capture_steps(mtpt_handle* h, int flags, bool walk_ahead) {
 
 // Whether a call's steps can run with walk-ahead (all but the last step's
 // pass 2 also walk the particles for the step after): a plain handle or a
-// batch (not a tile, a reaction or the adjoint's tangent run) stepping with
-// both the walk and the transfer.
+// batch (not a tile, a binary64 reaction or the adjoint's tangent run)
+// stepping with both the walk and the transfer.
 bool walk_ahead_ok(const mtpt_handle* h, int flags) {
-    return h->ntiles == 0 && !h->reactive && !h->tangent_on && h->any_walk && h->any_transfer &&
-           h->n > 0 && flags == (MTPT_DO_WALK | MTPT_DO_TRANSFER);
+    return h->ntiles == 0 && (!h->reactive || h->precision == MTPT_FP32W) && !h->tangent_on &&
+           h->any_walk && h->any_transfer && h->n > 0 &&
+           flags == (MTPT_DO_WALK | MTPT_DO_TRANSFER);
 }
 
 int run_steps(mtpt_handle* h, int64_t nsteps, int flags) {
