@@ -1056,16 +1056,6 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Compensated summation of positive terms (Kahan): s - c carries the sum,
-// four additions per term.  Used for the row sums, whose terms are all
-// positive.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
 // Compensated summation of mixed-sign terms (Kahan-Babuska / Neumaier):
 // s + c carries the sum to about twice binary32 precision whatever the order
 // of magnitudes.  Used for the flux sums.
@@ -1445,7 +1435,9 @@ k_rowsum_f32(int n, int64_t stride, const double* __restrict__ pos, const float4
             uint2* lp = nb.e + s;          // slot `listed` of s
             scan_neighbours<DIM, true>(uint32_t(s), cell_arg<DIM>(cell, s), stride, rec, pos, start, P,
                                  [&](uint32_t j, float d2f, bool accept) {
-                                     // Kahan step, kept only for accepted pairs
+                                     // compensated (Kahan) step for positive terms:
+                                     // rsum - rc carries the sum; kept only for
+                                     // accepted pairs
                                      const float K = ex2_approx(na * d2f);
                                      const float y = __fsub_rn(K, rc);
                                      const float t = __fadd_rn(rsum, y);
