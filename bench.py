@@ -82,14 +82,14 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # Valid only for the library source it was measured on: a different hash of
 # the CUDA sources and the header reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "01a316170fd5"   # 5a89093490da + header comments
+TRAFFIC_SOURCE_SHA1 = "e5836a015aa0"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (88931584 + 31843840) / 4e6,
-    "scatter": (81828096 + 35095808) / 4e6,
-    "gather": (152936448 + 124399360) / 4e6,
-    "rowsum_f32": (238032384 + 292266752) / 4e6,
-    "exchange_f32": (389628160 + 27271936) / 4e6,
-    "exchange_walk_f32": (478562816 + 117270528) / 4e6,
+    "walk_key": (88933888 + 31825664) / 4e6,
+    "scatter": (81831168 + 35118592) / 4e6,
+    "gather": (152934912 + 124552704) / 4e6,
+    "rowsum_f32": (238012928 + 292361472) / 4e6,
+    "exchange_f32": (389627648 + 27205120) / 4e6,
+    "exchange_walk_f32": (478511104 + 117244416) / 4e6,
 }
 
 
@@ -100,10 +100,10 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 INSTR_PER_PARTICLE = {
     "walk_key": 43906125 / 4e6,
     "scatter": 4125000 / 4e6,
-    "gather": 38024199 / 4e6,
+    "gather": 38024193 / 4e6,
     "rowsum_f32": 183180239 / 4e6,
     "exchange_f32": 49384119 / 4e6,
-    "exchange_walk_f32": 92400743 / 4e6,
+    "exchange_walk_f32": 93525743 / 4e6,
 }
 SMS, SCHEDULERS_PER_SM = 152, 4
 
@@ -114,9 +114,9 @@ SMS, SCHEDULERS_PER_SM = 152, 4
 BINDING = {
     "exchange_f32": ("DRAM 58 % with long-scoreboard stalls on the list reads and the "
                      "neighbour-record gathers; issue 46 % at 21 of 32 active lanes"),
-    "exchange_walk_f32": ("DRAM 58 % and binary64 pipe 51 % (pass 2's update and the next "
-                          "step's x + sigma xi); issue 59 % at 26 of 32 active lanes"),
-    "rowsum_f32": "instruction issue: 71 % of issue slots at 18 of 32 active lanes; DRAM 31 %",
+    "exchange_walk_f32": ("DRAM 59 % and binary64 pipe 52 % (pass 2's update and the next "
+                          "step's x + sigma xi); issue 61 % at 26 of 32 active lanes"),
+    "rowsum_f32": "instruction issue: 74 % of issue slots at 18 of 32 active lanes; DRAM 32 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
     "gather": "DRAM 62 % (payload reads through the permutation, cell-ordered writes)",
