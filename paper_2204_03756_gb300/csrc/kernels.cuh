@@ -878,9 +878,11 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 
 // Binary32 x difference of candidate o from particle me (cells cx_o - cx_me
 // apart, |cx_o - cx_me| <= reach <= 2, so the shift is a power-of-two multiple
-// of wx and exact): changes sign exactly when the pair swaps.
+// of wx and exact, and one fused multiply-add rounds exactly as the sum of the
+// rounded offset difference and the shift would): changes sign exactly when
+// the pair swaps.
 __device__ __forceinline__ float dx_f32(const float4& me, const float4& o, float wx) {
-    return __fadd_rn(__fsub_rn(o.x, me.x), __fmul_rn(__fsub_rn(o.w, me.w), wx));
+    return __fmaf_rn(__fsub_rn(o.w, me.w), wx, __fsub_rn(o.x, me.x));
 }
 
 template <int DIM>
