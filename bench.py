@@ -82,14 +82,14 @@ def _algo_bytes_per_particle(kernel: str, dim: int, form: str) -> float:
 # Valid only for the library source it was measured on: a different hash of
 # the CUDA sources and the header reports traffic as null.
 TRAFFIC_DIM = 2
-TRAFFIC_SOURCE_SHA1 = "e5836a015aa0"
+TRAFFIC_SOURCE_SHA1 = "fd2803d8f07e"
 TRAFFIC_BYTES_PER_PARTICLE = {
-    "walk_key": (88933888 + 31825664) / 4e6,
-    "scatter": (81831168 + 35118592) / 4e6,
-    "gather": (152934912 + 124552704) / 4e6,
-    "rowsum_f32": (238012928 + 292361472) / 4e6,
-    "exchange_f32": (389627648 + 27205120) / 4e6,
-    "exchange_walk_f32": (478511104 + 117244416) / 4e6,
+    "walk_key": (88933632 + 31892736) / 4e6,
+    "scatter": (81824512 + 34699776) / 4e6,
+    "gather": (152929792 + 124269312) / 4e6,
+    "rowsum_f32": (238171904 + 292427776) / 4e6,
+    "exchange_f32": (389639424 + 26841344) / 4e6,
+    "exchange_walk_f32": (478508544 + 117244416) / 4e6,
 }
 
 
@@ -100,9 +100,9 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 INSTR_PER_PARTICLE = {
     "walk_key": 43906125 / 4e6,
     "scatter": 4125000 / 4e6,
-    "gather": 38024193 / 4e6,
-    "rowsum_f32": 183180239 / 4e6,
-    "exchange_f32": 49384119 / 4e6,
+    "gather": 38024198 / 4e6,
+    "rowsum_f32": 178884629 / 4e6,
+    "exchange_f32": 49384081 / 4e6,
     "exchange_walk_f32": 93525743 / 4e6,
 }
 SMS, SCHEDULERS_PER_SM = 152, 4
@@ -116,7 +116,7 @@ BINDING = {
                      "neighbour-record gathers; issue 46 % at 21 of 32 active lanes"),
     "exchange_walk_f32": ("DRAM 59 % and binary64 pipe 52 % (pass 2's update and the next "
                           "step's x + sigma xi); issue 61 % at 26 of 32 active lanes"),
-    "rowsum_f32": "instruction issue: 74 % of issue slots at 18 of 32 active lanes; DRAM 32 %",
+    "rowsum_f32": "instruction issue: 72 % of issue slots at 18 of 32 active lanes; DRAM 32 %",
     "rowsum_f64": "binary64 pipe 86 % busy",
     "exchange_f64": "binary64 pipe 86 % busy",
     "gather": "DRAM 62 % (payload reads through the permutation, cell-ordered writes)",
