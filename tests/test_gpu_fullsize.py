@@ -5,7 +5,9 @@ size), sampled realisations of the full 512-member ensemble (realisations are
 independent, so the oracle runs each sampled one on its own), and the
 adjoint's full-size gradient checked through properties that hold at any
 size: linearity in the masses and a binary64 finite difference in D
-(with the pair set and the bins checked unchanged across it)."""
+(with the pair set and the bins checked unchanged across it); and the 2-d
+workload run for its full 1000 steps in one call against 1000 single-step
+calls."""
 import numpy as np
 import pytest
 
@@ -119,3 +121,24 @@ def _bins(w, x, nb):
     ix = np.clip(((x[0] - w.lo[0]) / (w.hi[0] - w.lo[0]) * nb[0]).astype(int), 0, nb[0] - 1)
     iy = np.clip(((x[1] - w.lo[1]) / (w.hi[1] - w.lo[1]) * nb[1]).astype(int), 0, nb[1] - 1)
     return ix * nb[1] + iy
+
+
+def test_full_length_run_in_one_call_equals_single_steps():
+    """The 4e6-particle 2-d workload for its full 1000 steps: one call (the
+    walk-ahead path, its middle steps replayed from a graph) equals 1000
+    calls of one step bit for bit, and the precision form's exactly
+    antisymmetric fluxes keep the total mass to binary64 rounding."""
+    w = workloads.get("gaussian_2d")
+    assert w.steps == 1000
+    pos, mass = workloads.initial_state(w)
+    p = params_of(w, precision=mtpt.MTPT_FP32W)
+    with mtpt.Simulation(p, pos, mass) as a:
+        a.step(w.steps)
+        xa, ma, ia = a.positions(), a.masses(), a.info()
+    with mtpt.Simulation(p, pos, mass) as b:
+        for _ in range(w.steps):
+            b.step(1)
+        xb, mb, ib = b.positions(), b.masses(), b.info()
+    assert np.array_equal(xa, xb) and np.array_equal(ma, mb)
+    assert ia["step"] == ib["step"] == w.steps and ia["pair_count"] == ib["pair_count"]
+    assert abs(ma.sum() - mass.sum()) <= 1e-12 * mass.sum()
