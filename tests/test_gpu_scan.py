@@ -69,3 +69,28 @@ def test_the_hook_checks_its_argument():
     with pytest.raises(mtpt.MtptError) as e:
         mtpt.mtpt_debug_scan_hold(-2)
     assert e.value.code == mtpt.MTPT_ERR_INVALID_ARG
+
+
+def test_a_scan_of_several_block_waves_keeps_parity():
+    """A sparse box whose cell grid hits its cap (4 n + 64 cells): about 300
+    scan tiles, nearly two waves of the one-block-per-SM scan, so tiles of the
+    second wave read totals published by blocks that have already finished.  Two
+    steps against the oracle: positions and pair count exact, masses within
+    tolerance."""
+    import oracle as O
+    from gpu_helpers import TOL, oracle_params, rel_err
+    n, L = 1_200_000, 12_000.0
+    rng = np.random.default_rng(77)
+    pos = rng.uniform(0.0, L, size=(2, n))
+    mass = rng.uniform(0.0, 1.0, n)
+    p = mtpt.Params(dim=2, D=1.0, kappa=0.5, dt=0.1, lo=(0.0, 0.0), hi=(L, L), seed=9,
+                    precision=mtpt.MTPT_FP32W)
+    with mtpt.Simulation(p, pos, mass) as sim:
+        cells = sim.info()["cells"]
+        assert _tiles(cells) > 152        # more tiles than one scan block per SM
+        sim.step(2)
+        x, m, info = sim.positions(), sim.masses(), sim.info()
+    xr, mr, npairs = O.run(oracle_params(p), pos, mass, 2)
+    assert np.array_equal(x, xr)
+    assert info["pair_count"] == npairs and npairs > 0
+    assert rel_err(m, mr) <= TOL[mtpt.MTPT_FP32W]
